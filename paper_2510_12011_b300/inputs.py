@@ -1,0 +1,225 @@
+"""Seeded synthetic inputs for the monodomain hot path.
+
+This module generates *inputs only*: node coordinates, tetrahedral connectivity, per-element
+fibre directions, region ids, stimulus node sets and the parameter sets of the workloads.
+It holds none of the method's arithmetic (no element matrices, no assembly, no solver, no
+ionic model), so both the CUDA path and the FP64 oracle may draw their inputs from it.
+
+Meshes are structured cuboid slabs split into tetrahedra, the geometry the paper uses for
+its idealised cube meshes and its N-version benchmark (Section 3.1.2, Table 3; Section 3.3).
+Every hexahedral cell is cut into six tetrahedra along its (0,0,0)-(1,1,1) diagonal (the
+Kuhn/Freudenthal split: one tetrahedron per ordering of the three axes), which gives a
+conforming mesh.  Optional node jitter uses SplitMix64 (Steele, Lea & Flood 2014) as a
+counter-based generator: draw number c of seed s is mix(s + (c+1) * 0x9E3779B97F4A7C15).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Counter-based SplitMix64: output number ``counters`` of the stream seeded ``seed``."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (counters.astype(np.uint64) + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of SplitMix64 outputs."""
+    return (splitmix64(seed, counters) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+# The six tetrahedra of one hex cell, as corner offsets (dx, dy, dz).  Axis ordering
+# (a, b, c) walks (0,0,0) -> e_a -> e_a+e_b -> (1,1,1); odd orderings swap the last two
+# vertices so that every tetrahedron is positively oriented.
+def _kuhn_corners():
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    even = {(0, 1, 2), (1, 2, 0), (2, 0, 1)}
+    out = []
+    for p in perms:
+        v = [np.zeros(3, dtype=int)]
+        for ax in p:
+            nxt = v[-1].copy()
+            nxt[ax] = 1
+            v.append(nxt)
+        if p not in even:
+            v[2], v[3] = v[3], v[2]
+        out.append([tuple(int(c) for c in x) for x in v])
+    return out
+
+
+KUHN_CORNERS = _kuhn_corners()
+
+
+@dataclass
+class Mesh:
+    """A tetrahedral mesh: coordinates in mm, 0-based connectivity, unit fibres per element."""
+    xyz: np.ndarray          # (n, 3) float64, mm
+    tets: np.ndarray         # (n_tets, 4) int32
+    fibres: np.ndarray       # (n_tets, 3) float64, unit
+    region: np.ndarray       # (n_tets,) int32
+    lattice: np.ndarray      # (n, 3) int32 lattice indices (i, j, k) of each node
+    shape: tuple             # (nx, ny, nz) nodes per axis
+    h: float
+
+    @property
+    def n_nodes(self) -> int:
+        return self.xyz.shape[0]
+
+    @property
+    def n_tets(self) -> int:
+        return self.tets.shape[0]
+
+
+def slab_mesh(lx: float, ly: float, lz: float, h: float, jitter: float = 0.0, seed: int = 0,
+              fibre: str = "x") -> Mesh:
+    """Cuboid [0,lx]x[0,ly]x[0,lz] (mm) with node spacing h, six tetrahedra per cell.
+
+    jitter: each node coordinate moves by U(-jitter*h, +jitter*h) drawn from SplitMix64 with
+    counter 3*node+axis; a coordinate that lies on a face of the box normal to that axis is
+    not moved, so the box stays a box.  With jitter <= 0.15 every tetrahedron keeps a positive
+    volume (its smallest height, h/sqrt(2), shrinks by at most 0.3*sqrt(2)*h).
+    fibre: "x" for (1,0,0) everywhere; "rotating" for f = (cos a, sin a, 0) with the angle a
+    going linearly from -60 deg at z=0 to +60 deg at z=lz, taken at the element centroid.
+    """
+    nx = int(round(lx / h)) + 1
+    ny = int(round(ly / h)) + 1
+    nz = int(round(lz / h)) + 1
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lat = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.int32)
+    xyz = lat.astype(np.float64) * h
+    n = lat.shape[0]
+    if jitter > 0.0:
+        c = np.arange(3 * n, dtype=np.uint64).reshape(n, 3)
+        d = (2.0 * uniform01(seed, c) - 1.0) * (jitter * h)
+        dims = np.array([nx, ny, nz])
+        on_face = (lat == 0) | (lat == dims - 1)
+        d[on_face] = 0.0
+        xyz = xyz + d
+
+    def nid(ii, jj, kk):
+        return ii + nx * (jj + ny * kk)
+
+    ci, cj, ck = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), np.arange(nz - 1), indexing="ij")
+    # cell order: i fastest, then j, then k
+    ci = ci.transpose(2, 1, 0).ravel()
+    cj = cj.transpose(2, 1, 0).ravel()
+    ck = ck.transpose(2, 1, 0).ravel()
+    tets = np.empty((ci.size, 6, 4), dtype=np.int64)
+    for t, corners in enumerate(KUHN_CORNERS):
+        for v, (dx, dy, dz) in enumerate(corners):
+            tets[:, t, v] = nid(ci + dx, cj + dy, ck + dz)
+    tets = tets.reshape(-1, 4).astype(np.int32)
+
+    if fibre == "x":
+        fib = np.zeros((tets.shape[0], 3))
+        fib[:, 0] = 1.0
+    elif fibre == "rotating":
+        zc = xyz[tets, 2].mean(axis=1)
+        a = np.deg2rad(-60.0 + 120.0 * zc / lz)
+        fib = np.stack([np.cos(a), np.sin(a), np.zeros_like(a)], axis=1)
+    else:
+        raise ValueError(f"unknown fibre rule {fibre!r}")
+    region = np.zeros(tets.shape[0], dtype=np.int32)
+    return Mesh(xyz=xyz, tets=tets, fibres=fib, region=region, lattice=lat,
+                shape=(nx, ny, nz), h=h)
+
+
+def corner_nodes(mesh: Mesh, size_mm: float) -> np.ndarray:
+    """Nodes whose unjittered lattice position lies in the corner cube [0, size_mm]^3."""
+    lim = size_mm / mesh.h + 1e-9
+    sel = np.all(mesh.lattice.astype(np.float64) <= lim, axis=1)
+    return np.nonzero(sel)[0].astype(np.int32)
+
+
+@dataclass
+class MSParams:
+    """Mitchell-Schaeffer two-variable model, mapped to mV (v = (V - v_min)/(v_max - v_min))."""
+    tau_in: float = 0.3
+    tau_out: float = 6.0
+    tau_open: float = 120.0
+    tau_close: float = 150.0
+    v_gate: float = 0.13
+    v_min: float = -80.0
+    v_max: float = 20.0
+
+    def as_array(self) -> np.ndarray:
+        return np.array([self.tau_in, self.tau_out, self.tau_open, self.tau_close,
+                         self.v_gate, self.v_min, self.v_max], dtype=np.float64)
+
+
+@dataclass
+class Stimulus:
+    nodes: np.ndarray
+    start: float        # ms
+    duration: float     # ms
+    intensity: float    # uA/mm^2
+
+
+@dataclass
+class Workload:
+    """One monodomain run: mesh, tissue constants, time stepping, solver and stimuli."""
+    name: str
+    mesh: Mesh
+    sigma_l: float            # S/m
+    sigma_t: float            # S/m
+    chi: float                # 1/mm
+    cm: float                 # uF/mm^2
+    theta: float
+    dt: float                 # ms
+    t_end: float              # ms
+    model: str                # "ms" or "tp06"
+    ms: MSParams = field(default_factory=MSParams)
+    stimuli: list = field(default_factory=list)
+    atol: float = 0.0
+    rtol: float = 1e-10
+    max_iter: int = 1000
+    v_threshold: float = 0.0  # mV, activation threshold
+
+    @property
+    def n_steps(self) -> int:
+        return int(round(self.t_end / self.dt))
+
+
+def slab_small_ms() -> Workload:
+    """10x4x2 mm slab at h=0.5 mm (945 nodes, 3840 tets), fibres along x, Mitchell-Schaeffer,
+    dt=0.01 ms for 50 ms, 2 ms corner stimulus at 50 uA/cm^2 = 0.5 uA/mm^2, PCG rel tol 1e-10."""
+    m = slab_mesh(10.0, 4.0, 2.0, 0.5)
+    st = [Stimulus(corner_nodes(m, 1.0), 0.0, 2.0, 0.5)]
+    # chi = 1400 /cm = 140 /mm; Cm = 1 uF/cm^2 = 0.01 uF/mm^2
+    return Workload("slab10x4x2_h0.5_ms", m, 0.17, 0.019, 140.0, 0.01, 0.5, 0.01, 50.0, "ms",
+                    stimuli=st, atol=0.0, rtol=1e-10, max_iter=1000)
+
+
+def slab_large(model: str = "ms") -> Workload:
+    """40x16x6 mm slab at h=0.2 mm (504,711 nodes, 2,880,000 tets), jitter U(+-0.15h) seed 1,
+    fibres rotating -60..+60 deg through the depth, dt=0.02 ms for 100 ms, 1 mm corner stimulus
+    (2 ms at 0.5 uA/mm^2).  Solver tolerances are the paper's recommended a_tol = r_tol = 1e-5
+    with at most 100 iterations (Section 3.2, Listing 1)."""
+    m = slab_mesh(40.0, 16.0, 6.0, 0.2, jitter=0.15, seed=1, fibre="rotating")
+    st = [Stimulus(corner_nodes(m, 1.0), 0.0, 2.0, 0.5)]
+    return Workload(f"slab40x16x6_h0.2_{model}", m, 0.17, 0.019, 140.0, 0.01, 0.5, 0.02, 100.0,
+                    model, stimuli=st, atol=1e-5, rtol=1e-5, max_iter=100)
+
+
+def slab_custom(lx, ly, lz, h, jitter=0.0, seed=0, fibre="x", dt=0.01, model="ms",
+                stim_mm=1.0, rtol=1e-10, atol=0.0, max_iter=1000, t_end=10.0) -> Workload:
+    """A slab workload of any size with the small-slab tissue constants (used for sweeps)."""
+    m = slab_mesh(lx, ly, lz, h, jitter=jitter, seed=seed, fibre=fibre)
+    st = [Stimulus(corner_nodes(m, stim_mm), 0.0, 2.0, 0.5)]
+    return Workload(f"slab{lx:g}x{ly:g}x{lz:g}_h{h:g}_{model}", m, 0.17, 0.019, 140.0, 0.01, 0.5,
+                    dt, t_end, model, stimuli=st, atol=atol, rtol=rtol, max_iter=max_iter)
+
+
+def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Seeded uniform vector for operator tests."""
+    return lo + (hi - lo) * uniform01(seed, np.arange(n, dtype=np.uint64))
