@@ -1,0 +1,199 @@
+/*
+ * tc.h - C ABI of the B300 monodomain hot path (TorchCor, arXiv 2510.12011).
+ *
+ * The library advances the operator-split monodomain P1-FEM scheme of Section 2.2:
+ *   per step k -> k+1
+ *     (a1) ionic update u^{k+1} = f(V^k, u^k), I_ion(V^k, u^{k+1})            Eq. 2, row 1
+ *     (a2) b = chi M (Cm V^k - dt I_ion + dt I_stim) - (1 - theta) dt K V^k     after Eq. 3
+ *     (a3,a4) Jacobi-PCG solve of (chi Cm M + theta dt K) V^{k+1} = b           Algorithm 1
+ *          from the extrapolated guess 2 V^k - V^{k-1}                         end of Sec. 2.2
+ *     (a5) activation time: first upward crossing of a threshold (LAT)         Section 2.1
+ * on one GPU with hand-written sm_103a kernels.  Units follow Table 1: mm, ms, mV,
+ * uA/mm^2 (currents), uF/mm^2 (Cm), 1/mm (chi), S/m (conductivities); with these units the
+ * diffusion term needs no conversion factor.
+ *
+ * Conventions for every call
+ *   - Every call returns tc_status; TC_OK is 0, errors are negative.  On error,
+ *     tc_last_error() returns a message for the calling thread; no call aborts the process.
+ *   - Input arrays are host pointers unless a name says "dev"; they are copied before the
+ *     call returns, and the caller keeps ownership of them.
+ *   - Handles are owned by the library and released only by *_destroy; destroying NULL is
+ *     a no-op.  A handle may be used by one thread at a time.
+ *   - Node numbering in and out of the library is the caller's.  The library reorders nodes
+ *     internally (reverse Cuthill-McKee, then SELL-C-sigma row sorting, Section 2.2: "RCM")
+ *     and undoes the order on every read.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TC_OK = 0,
+  TC_ERR_ARG = -1,      /* null pointer, size out of range, bad enum value            */
+  TC_ERR_MESH = -2,     /* degenerate tetrahedron, node index out of range             */
+  TC_ERR_STATE = -3,    /* call made in the wrong order / on a mismatched object       */
+  TC_ERR_CUDA = -4,     /* a CUDA runtime call failed (message has the CUDA error)     */
+  TC_ERR_NOMEM = -5,    /* host or device allocation failed                            */
+  TC_ERR_TIMEOUT = -6,  /* a device-side wait hit its iteration limit                  */
+  TC_ERR_NAN = -7       /* a non-finite value appeared in the solver                   */
+} tc_status;
+
+typedef enum { TC_MODEL_MS = 0, TC_MODEL_TP06 = 1 } tc_model;
+typedef enum { TC_FP64 = 0, TC_FP32 = 1 } tc_precision;
+typedef enum { TC_OP_M = 0, TC_OP_K = 1, TC_OP_A = 2 } tc_operator;
+/* Fields for tc_read_state / tc_write_state.  TC_FIELD_STATE + j is ionic state j. */
+typedef enum { TC_FIELD_V = 0, TC_FIELD_V_PREV = 1, TC_FIELD_STATE = 16 } tc_field;
+
+typedef struct tc_mesh tc_mesh;
+typedef struct tc_sim tc_sim;
+
+/* Statistics of one tc_step call (filled when the pointer is not NULL). */
+typedef struct {
+  int64_t steps;          /* time steps made by this call                               */
+  int64_t step_index;     /* index k of the next step after the call                    */
+  int64_t cg_iterations;  /* A-products made inside the PCG loops, summed over the steps  */
+  int32_t max_iterations; /* largest PCG iteration count of one step                    */
+  int32_t not_converged;  /* steps whose PCG stopped at max_iter (Algorithm 1 just stops) */
+  double last_znorm;      /* ||z|| when the last step's PCG stopped                      */
+  double last_z0norm;     /* ||z_0|| of the last step's PCG                              */
+} tc_step_stats;
+
+/* Accumulated device time per kernel while profiling is on (tc_set_profiling). */
+typedef struct {
+  double ionic_ms;        int64_t ionic_launches;
+  double pcg_ms;          int64_t pcg_launches;
+  int64_t pcg_iterations; /* iterations inside the profiled PCG launches                */
+} tc_profile;
+
+/* ---- mesh ------------------------------------------------------------------------- */
+
+/* tc_mesh_create: copy a tetrahedral mesh (Section 2.1: points, connectivity, fibres).
+ *   xyz     [n_nodes][3] node coordinates in mm
+ *   tets    [n_tets][4]  0-based node indices; either orientation is accepted
+ *   fibres  [n_tets][3]  fibre direction per element (normalised here), or NULL for (1,0,0)
+ *   region  [n_tets]     region id per element in [0, n_regions), or NULL for all 0
+ * Errors: TC_ERR_ARG (null/size), TC_ERR_MESH (index out of range, zero-length fibre,
+ * |det J| <= 1e-12 * (longest edge)^3, i.e. a degenerate element). */
+tc_status tc_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                         const double* fibres, const int32_t* region, tc_mesh** out);
+void tc_mesh_destroy(tc_mesh* mesh);
+
+/* Number of stored entries of M, K and A (one shared pattern: every node pair of an element). */
+tc_status tc_mesh_nnz(const tc_mesh* mesh, int64_t* nnz);
+
+/* tc_mesh_matrices: host-side P1 assembly, returned in the caller's node order as CSR with
+ * sorted column indices (Section 2.2: "M and K ... are sparse").  Per element:
+ *   M_e[i][j] = vol (1 + delta_ij) / 20,  K_e[i][j] = vol grad(l_i)^T sigma_e grad(l_j),
+ *   sigma_e = sigma_t I + (sigma_l - sigma_t) f f^T  (Section 2.1, conductivity from fibres).
+ * sigma_l, sigma_t: [n_regions] conductivities in S/m.  Outputs (caller-allocated):
+ * row_ptr [n+1], col [nnz], m_val [nnz], k_val [nnz]; any of the four may be NULL.
+ * Runs on the host only; needs no GPU. */
+tc_status tc_mesh_matrices(const tc_mesh* mesh, const double* sigma_l, const double* sigma_t,
+                           int32_t n_regions, int64_t* row_ptr, int32_t* col, double* m_val,
+                           double* k_val);
+
+/* tc_mesh_ordering: the internal node order the device path uses (host only).
+ * perm[new] = old for the nodes; slice_width receives ceil(n/32) SELL slice widths if not NULL. */
+tc_status tc_mesh_ordering(const tc_mesh* mesh, int32_t sell_sigma, int32_t* perm,
+                           int32_t* slice_width);
+
+/* ---- simulation ------------------------------------------------------------------- */
+
+/* tc_assemble: assemble M, K and A = chi Cm M + theta dt K (Eq. 3), build the Jacobi
+ * preconditioner diag(A) (Section 2.2), reorder and upload everything to the current CUDA
+ * device, and allocate the state.  The simulation starts at step 0 with the ionic model's
+ * resting state (set by tc_set_ionic) and V^{-1} = V^0.
+ *   sigma_l, sigma_t [n_regions] S/m; chi 1/mm; cm uF/mm^2; theta in [0,1]; dt ms > 0
+ *   precision: TC_FP64 (all arithmetic in double) or TC_FP32 (matrix/ionic in float, PCG
+ *   dot products and alpha/beta recurrences in double)
+ *   cuda_stream: a cudaStream_t to run on, or NULL for the legacy default stream.
+ * Errors: TC_ERR_ARG, TC_ERR_MESH, TC_ERR_CUDA, TC_ERR_NOMEM. */
+tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* sigma_t,
+                      int32_t n_regions, double chi, double cm, double theta, double dt,
+                      int32_t precision, void* cuda_stream, tc_sim** out);
+void tc_sim_destroy(tc_sim* sim);
+
+tc_status tc_sim_size(const tc_sim* sim, int64_t* n_nodes, int64_t* nnz, int64_t* padded_nnz,
+                      int32_t* n_blocks);
+
+/* tc_set_ionic: choose the ionic model and reset the state to init_state (NULL = the model's
+ * resting state; otherwise [n_states][n_nodes] in caller order, V excluded).
+ * TC_MODEL_MS (Mitchell-Schaeffer in mV; 1 state h): params = {tau_in, tau_out, tau_open,
+ *   tau_close, v_gate, v_min, v_max} (ms, ms, ms, ms, -, mV, mV); n_params = 7.
+ *   v = (V - v_min)/(v_max - v_min); I_ion = -Cm (v_max - v_min)(h v^2 (1-v)/tau_in - v/tau_out);
+ *   gate by Rush-Larsen: v < v_gate -> (h_inf, tau) = (1, tau_open), else (0, tau_close).
+ * TC_MODEL_TP06 (ten Tusscher-Panfilov 2006; 18 states): params = {cell type} with
+ *   0 = endo, 1 = mid-myocardial, 2 = epi; n_params = 1.
+ * Sets V^0 = V^{-1} = the model's resting potential, resets activation times and the step
+ * index to 0.  Must be called before tc_step.  Errors: TC_ERR_ARG, TC_ERR_CUDA. */
+tc_status tc_set_ionic(tc_sim* sim, int32_t model, const double* params, int32_t n_params,
+                       const double* init_state);
+
+/* tc_add_stimulus: any number of stimuli (Section 2.1).  The nodes receive I_stim += intensity
+ * (uA/mm^2) during steps k with k0 <= k < k0 + nk, k0 = round(start/dt), nk = round(duration/dt)
+ * (round half to even); I_stim enters b as chi M dt I_stim.  Errors: TC_ERR_ARG (index range). */
+tc_status tc_add_stimulus(tc_sim* sim, const int32_t* nodes, int64_t n, double start_ms,
+                          double duration_ms, double intensity);
+
+/* tc_set_solver: PCG tolerances (Algorithm 1): stop when ||z|| < atol or ||z||/||z_0|| < rtol,
+ * z = D^{-1} r, 2-norms; at most max_iter iterations (reaching it is not an error). */
+tc_status tc_set_solver(tc_sim* sim, double atol, double rtol, int32_t max_iter);
+
+/* tc_set_activation_threshold: threshold (mV) of the activation-time capture; default 0 mV
+ * (LAT: "first becomes positive").  Only before the first step. */
+tc_status tc_set_activation_threshold(tc_sim* sim, double v_threshold);
+
+/* tc_step: advance n_steps >= 0 time steps on the simulation's stream and wait for them.
+ * Errors: TC_ERR_STATE (no ionic model), TC_ERR_TIMEOUT (a device wait hit its limit; the
+ * state is then undefined), TC_ERR_NAN, TC_ERR_CUDA. */
+tc_status tc_step(tc_sim* sim, int64_t n_steps, tc_step_stats* stats);
+
+/* tc_read_state / tc_write_state: copy one field to/from a host array of n = n_nodes doubles
+ * in caller node order (TC_FIELD_V = V^k, TC_FIELD_V_PREV = V^{k-1},
+ * TC_FIELD_STATE + j = ionic state j). */
+tc_status tc_read_state(const tc_sim* sim, int32_t field, double* host_dst, int64_t n);
+tc_status tc_write_state(tc_sim* sim, int32_t field, const double* host_src, int64_t n);
+
+/* tc_activation_times: per node, the first time (ms) V crossed v_threshold upwards, linearly
+ * interpolated within the step; 0 if V^0 >= threshold; -1 if never.  v_threshold must equal the
+ * capture threshold (TC_ERR_STATE otherwise). */
+tc_status tc_activation_times(const tc_sim* sim, double v_threshold, double* host_dst, int64_t n);
+
+/* tc_get_step_index / tc_set_step_index: the step counter k (for checkpoint/restart). */
+tc_status tc_get_step_index(const tc_sim* sim, int64_t* k);
+tc_status tc_set_step_index(tc_sim* sim, int64_t k);
+
+/* tc_apply_operator: y = Op x with Op in {M, K, A} using the device SELL-C-sigma kernel
+ * (the SpMV of Algorithm 1).  x, y: host arrays [n_nodes] in caller order. */
+tc_status tc_apply_operator(tc_sim* sim, int32_t op, const double* x, double* y, int64_t n);
+
+/* tc_apply_operator_dev: the same on device arrays in the INTERNAL node order (no copies,
+ * asynchronous on the simulation's stream).  x_dev, y_dev: n_nodes doubles (TC_FP64) or
+ * floats (TC_FP32), 16-byte aligned. */
+tc_status tc_apply_operator_dev(tc_sim* sim, int32_t op, const void* x_dev, void* y_dev);
+
+/* Profiling: when on, tc_step records CUDA events around every launch on the simulation's
+ * stream and accumulates their durations; tc_get_profile reads and tc_reset_profile clears. */
+tc_status tc_set_profiling(tc_sim* sim, int32_t on);
+tc_status tc_get_profile(const tc_sim* sim, tc_profile* out);
+tc_status tc_reset_profile(tc_sim* sim);
+
+/* tc_set_wait_limit: iteration limit of every device-side wait of the PCG kernel's grid
+ * barrier (default 1<<26 polls).  A tiny limit makes the barrier give up and tc_step return
+ * TC_ERR_TIMEOUT with the GPU context intact (used to test the timeout path). */
+tc_status tc_set_wait_limit(tc_sim* sim, int64_t polls);
+
+/* Thread-local message of the last error ("" if none). */
+const char* tc_last_error(void);
+/* Library version string. */
+const char* tc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */

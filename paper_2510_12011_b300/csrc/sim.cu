@@ -1,0 +1,682 @@
+// Device-side simulation object and the C ABI calls that touch the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "tc_internal.h"
+
+using namespace tc;
+
+namespace {
+
+constexpr int kPcgThreads = 512;
+constexpr int kIonicThreads = 256;
+
+struct Dev {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tc_sim {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0, nnz = 0, nslices = 0, padded = 0;
+  int precision = TC_FP64;
+  std::vector<int32_t> perm, inv;   // perm[new] = old
+  int num_sms = 0, blocks_per_sm = 2, nblocks = 0;
+  // device arrays
+  int32_t *slice_ptr = nullptr, *col = nullptr, *blk_slice = nullptr;
+  double *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
+  double* V[3] = {nullptr, nullptr, nullptr};
+  int iv = 0;   // V[iv] = V^k, V[(iv+2)%3] = V^{k-1}, V[(iv+1)%3] = V^{k+1}
+  double *state = nullptr, *g1 = nullptr, *g2 = nullptr;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *act = nullptr;
+  double *partA = nullptr, *partB = nullptr;
+  GridBar* bar = nullptr;
+  int* err = nullptr;
+  DevStats* stats = nullptr;
+  int32_t *stim_off = nullptr, *stim_ids = nullptr;
+  StimDev* stims = nullptr;
+  std::vector<std::vector<int32_t>> stim_nodes;   // per stimulus, internal indices
+  std::vector<StimDev> stim_host;
+  bool stim_dirty = false;
+  // parameters
+  double chi = 0, cm = 0, theta = 0, dt = 0;
+  double atol = 0.0, rtol = 1e-10;
+  int max_iter = 1000;
+  double thr = 0.0;
+  bool thr_locked = false;
+  int model = -1;
+  int n_states = 0;
+  double ms[7] = {0};
+  long long k = 0;
+  long long wait_limit = 1ll << 26;
+  // profiling
+  bool prof = false;
+  tc_profile prof_acc{};
+  std::vector<cudaEvent_t> evpool;
+  std::vector<Dev> allocs;
+  double* pinned = nullptr;   // n doubles of page-locked staging for host reads/writes
+};
+
+namespace {
+
+tc_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? TC_ERR_NOMEM : TC_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(x)                                   \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x);  \
+  } while (0)
+
+template <class T>
+tc_status dalloc(tc_sim* s, T** out, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  s->allocs.push_back({p, bytes});
+  *out = static_cast<T*>(p);
+  return TC_OK;
+}
+
+#define TRY(x)                      \
+  do {                              \
+    tc_status st_ = (x);            \
+    if (st_ != TC_OK) return st_;   \
+  } while (0)
+
+int64_t round_half_even(double x) { return (int64_t)std::nearbyint(x); }
+
+tc_status upload_stimuli(tc_sim* s) {
+  std::vector<std::vector<int32_t>> per_node(s->n);
+  for (size_t sid = 0; sid < s->stim_nodes.size(); ++sid)
+    for (int32_t i : s->stim_nodes[sid]) per_node[i].push_back((int32_t)sid);
+  std::vector<int32_t> off(s->n + 1, 0), ids;
+  for (int64_t i = 0; i < s->n; ++i) {
+    off[i + 1] = off[i] + (int32_t)per_node[i].size();
+    ids.insert(ids.end(), per_node[i].begin(), per_node[i].end());
+  }
+  if (s->stim_ids) cudaFree(s->stim_ids), s->stim_ids = nullptr;
+  if (s->stims) cudaFree(s->stims), s->stims = nullptr;
+  CUDA_TRY(cudaMalloc(&s->stim_ids, std::max<size_t>(ids.size(), 1) * sizeof(int32_t)));
+  CUDA_TRY(cudaMalloc(&s->stims, std::max<size_t>(s->stim_host.size(), 1) * sizeof(StimDev)));
+  CUDA_TRY(cudaMemcpyAsync(s->stim_off, off.data(), off.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s->stream));
+  if (!ids.empty())
+    CUDA_TRY(cudaMemcpyAsync(s->stim_ids, ids.data(), ids.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s->stream));
+  if (!s->stim_host.empty())
+    CUDA_TRY(cudaMemcpyAsync(s->stims, s->stim_host.data(), s->stim_host.size() * sizeof(StimDev),
+                             cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->stim_dirty = false;
+  return TC_OK;
+}
+
+tc_status set_partition(tc_sim* s) {
+  int bps = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pcg_step_kernel<kPcgThreads>,
+                                                         kPcgThreads, 0));
+  if (bps < 1) return fail(TC_ERR_CUDA, "PCG kernel cannot be resident on an SM");
+  const int per_sm = std::min(bps, std::max(1, s->blocks_per_sm));
+  const int64_t max_blocks = (int64_t)per_sm * s->num_sms;
+  constexpr int kWarps = kPcgThreads / 32;
+  const int64_t want = (s->nslices + kWarps - 1) / kWarps;   // at least one slice per warp
+  s->nblocks = (int)std::max<int64_t>(1, std::min(max_blocks, want));
+  std::vector<int32_t> bs(s->nblocks + 1);
+  for (int b = 0; b <= s->nblocks; ++b) bs[b] = (int32_t)((s->nslices * (int64_t)b) / s->nblocks);
+  if (s->blk_slice) cudaFree(s->blk_slice), s->blk_slice = nullptr;
+  CUDA_TRY(cudaMalloc(&s->blk_slice, bs.size() * sizeof(int32_t)));
+  CUDA_TRY(cudaMemcpy(s->blk_slice, bs.data(), bs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (s->partA) cudaFree(s->partA), s->partA = nullptr;
+  if (s->partB) cudaFree(s->partB), s->partB = nullptr;
+  CUDA_TRY(cudaMalloc(&s->partA, s->nblocks * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&s->partB, 2 * s->nblocks * sizeof(double)));
+  return TC_OK;
+}
+
+tc_status to_internal(const tc_sim* s, const double* host, std::vector<double>& out) {
+  out.resize(s->n);
+  for (int64_t i = 0; i < s->n; ++i) out[i] = host[s->perm[i]];
+  return TC_OK;
+}
+
+cudaEvent_t pooled_event(tc_sim* s, size_t idx) {
+  while (s->evpool.size() <= idx) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    s->evpool.push_back(e);
+  }
+  return s->evpool[idx];
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* sigma_t,
+                      int32_t n_regions, double chi, double cm, double theta, double dt,
+                      int32_t precision, void* cuda_stream, tc_sim** out) {
+  clear_error();
+  if (!out) return fail(TC_ERR_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (!mesh) return fail(TC_ERR_ARG, "mesh must not be NULL");
+  if (!(chi > 0) || !(cm > 0) || !(dt > 0) || !(theta >= 0.0 && theta <= 1.0) ||
+      !std::isfinite(chi) || !std::isfinite(cm) || !std::isfinite(dt))
+    return fail(TC_ERR_ARG, "need chi > 0, cm > 0, dt > 0 and 0 <= theta <= 1");
+  if (precision != TC_FP64)
+    return fail(TC_ERR_ARG, "precision " + std::to_string(precision) + " is not available");
+  std::vector<double> mv, kv;
+  try {
+    TRY(assemble_mk(*mesh, sigma_l, sigma_t, n_regions, mv, kv));
+  } catch (const std::bad_alloc&) {
+    return fail(TC_ERR_NOMEM, "out of host memory");
+  }
+  tc_sim* s = new (std::nothrow) tc_sim();
+  if (!s) return fail(TC_ERR_NOMEM, "out of host memory");
+  auto bail = [&](tc_status st) {
+    tc_sim_destroy(s);
+    return st;
+  };
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  s->chi = chi;
+  s->cm = cm;
+  s->theta = theta;
+  s->dt = dt;
+  s->precision = precision;
+  s->n = mesh->n;
+  const Csr& pat = mesh->pattern;
+  s->nnz = pat.row_ptr[mesh->n];
+  Sell sell;
+  try {
+    node_ordering(pat, 1, s->perm);
+    tc_status st = build_sell(pat, s->perm, sell);
+    if (st != TC_OK) return bail(st);
+  } catch (const std::bad_alloc&) {
+    return bail(fail(TC_ERR_NOMEM, "out of host memory"));
+  }
+  s->inv.resize(s->n);
+  for (int64_t i = 0; i < s->n; ++i) s->inv[s->perm[i]] = (int32_t)i;
+  s->nslices = sell.nslices;
+  s->padded = sell.padded;
+  // A = chi Cm M + theta dt K, entry by entry (Eq. 3)
+  const double c1 = chi * cm, c2 = theta * dt;
+  std::vector<double> av(s->nnz);
+  for (int64_t q = 0; q < s->nnz; ++q) {
+    volatile double t1 = c1 * mv[q];   // two roundings and an add, as the definition reads
+    volatile double t2 = c2 * kv[q];
+    av[q] = t1 + t2;
+  }
+  std::vector<double> hM(sell.padded), hK(sell.padded), hA(sell.padded), hdinv(s->n);
+  for (int64_t e = 0; e < sell.padded; ++e) {
+    const int64_t q = sell.src[e];
+    hM[e] = q >= 0 ? mv[q] : 0.0;
+    hK[e] = q >= 0 ? kv[q] : 0.0;
+    hA[e] = q >= 0 ? av[q] : 0.0;
+  }
+  for (int64_t i = 0; i < s->n; ++i) {
+    const int32_t o = s->perm[i];
+    const int32_t* cb = &pat.col[pat.row_ptr[o]];
+    const int64_t len = pat.row_ptr[o + 1] - pat.row_ptr[o];
+    const int64_t d = std::lower_bound(cb, cb + len, o) - cb;
+    hdinv[i] = 1.0 / av[pat.row_ptr[o] + d];
+  }
+  cudaError_t ce = cudaGetDevice(&s->device);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
+  ce = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceGetAttribute"));
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+  if (!coop) return bail(fail(TC_ERR_CUDA, "device does not support cooperative launches"));
+  tc_status st = TC_OK;
+  const int64_t n = s->n;
+#define ALLOC(ptr, cnt)                        \
+  do {                                         \
+    st = dalloc(s, &(ptr), (size_t)(cnt));     \
+    if (st != TC_OK) return bail(st);          \
+  } while (0)
+  ALLOC(s->slice_ptr, s->nslices + 1);
+  ALLOC(s->col, sell.padded);
+  ALLOC(s->vM, sell.padded);
+  ALLOC(s->vK, sell.padded);
+  ALLOC(s->vA, sell.padded);
+  ALLOC(s->dinv, n);
+  for (int j = 0; j < 3; ++j) ALLOC(s->V[j], n);
+  ALLOC(s->g1, n);
+  ALLOC(s->g2, n);
+  ALLOC(s->r, n);
+  ALLOC(s->z, n);
+  ALLOC(s->p, n);
+  ALLOC(s->q, n);
+  ALLOC(s->act, n);
+  ALLOC(s->bar, 1);
+  ALLOC(s->err, 1);
+  ALLOC(s->stats, 1);
+  ALLOC(s->stim_off, n + 1);
+#undef ALLOC
+#define H2D(dst, src, cnt)                                                                     \
+  do {                                                                                         \
+    ce = cudaMemcpy(dst, src, (size_t)(cnt) * sizeof(*(src)), cudaMemcpyHostToDevice);         \
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpy"));                           \
+  } while (0)
+  H2D(s->slice_ptr, sell.slice_ptr.data(), s->nslices + 1);
+  H2D(s->col, sell.col.data(), sell.padded);
+  H2D(s->vM, hM.data(), sell.padded);
+  H2D(s->vK, hK.data(), sell.padded);
+  H2D(s->vA, hA.data(), sell.padded);
+  H2D(s->dinv, hdinv.data(), n);
+#undef H2D
+  ce = cudaMemset(s->bar, 0, sizeof(GridBar));
+  if (ce == cudaSuccess) ce = cudaMemset(s->err, 0, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMemset(s->stats, 0, sizeof(DevStats));
+  if (ce == cudaSuccess) ce = cudaMemset(s->stim_off, 0, (n + 1) * sizeof(int32_t));
+  if (ce == cudaSuccess) ce = cudaMemset(s->act, 0, n * sizeof(double));
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
+  ce = cudaMallocHost(&s->pinned, n * sizeof(double));
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMallocHost"));
+  st = set_partition(s);
+  if (st != TC_OK) return bail(st);
+  st = upload_stimuli(s);
+  if (st != TC_OK) return bail(st);
+  *out = s;
+  return TC_OK;
+}
+
+void tc_sim_destroy(tc_sim* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  if (s->stream || true) cudaStreamSynchronize(s->stream);
+  for (auto& d : s->allocs) cudaFree(d.p);
+  if (s->blk_slice) cudaFree(s->blk_slice);
+  if (s->partA) cudaFree(s->partA);
+  if (s->partB) cudaFree(s->partB);
+  if (s->stim_ids) cudaFree(s->stim_ids);
+  if (s->stims) cudaFree(s->stims);
+  if (s->state) cudaFree(s->state);
+  for (cudaEvent_t e : s->evpool) cudaEventDestroy(e);
+  if (s->pinned) cudaFreeHost(s->pinned);
+  delete s;
+}
+
+tc_status tc_sim_size(const tc_sim* s, int64_t* n_nodes, int64_t* nnz, int64_t* padded_nnz,
+                      int32_t* n_blocks) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  if (n_nodes) *n_nodes = s->n;
+  if (nnz) *nnz = s->nnz;
+  if (padded_nnz) *padded_nnz = s->padded;
+  if (n_blocks) *n_blocks = s->nblocks;
+  return TC_OK;
+}
+
+tc_status tc_set_ionic(tc_sim* s, int32_t model, const double* params, int32_t n_params,
+                       const double* init_state) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  CUDA_TRY(cudaSetDevice(s->device));
+  if (model != TC_MODEL_MS)
+    return fail(TC_ERR_ARG, "ionic model " + std::to_string(model) + " is not available");
+  if (!params || n_params != 7) return fail(TC_ERR_ARG, "Mitchell-Schaeffer needs 7 parameters");
+  const double* p = params;
+  if (!(p[0] > 0 && p[1] > 0 && p[2] > 0 && p[3] > 0 && p[6] > p[5]))
+    return fail(TC_ERR_ARG, "Mitchell-Schaeffer needs positive time constants and v_max > v_min");
+  std::copy(p, p + 7, s->ms);
+  s->model = model;
+  s->n_states = 1;
+  if (s->state) cudaFree(s->state), s->state = nullptr;
+  CUDA_TRY(cudaMalloc(&s->state, s->n * sizeof(double)));
+  std::vector<double> h(s->n, 1.0);
+  if (init_state) TRY(to_internal(s, init_state, h));
+  CUDA_TRY(cudaMemcpy(s->state, h.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<double> v0(s->n, s->ms[5]);
+  s->iv = 0;
+  CUDA_TRY(cudaMemcpy(s->V[0], v0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->V[2], v0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<double> a0(s->n, s->ms[5] >= s->thr ? 0.0 : -1.0);
+  CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  s->k = 0;
+  return TC_OK;
+}
+
+tc_status tc_add_stimulus(tc_sim* s, const int32_t* nodes, int64_t n, double start_ms,
+                          double duration_ms, double intensity) {
+  clear_error();
+  if (!s || (!nodes && n > 0) || n < 0) return fail(TC_ERR_ARG, "bad stimulus arguments");
+  if (!(start_ms >= 0) || !(duration_ms >= 0) || !std::isfinite(intensity))
+    return fail(TC_ERR_ARG, "stimulus start/duration must be >= 0 and intensity finite");
+  std::vector<int32_t> in;
+  in.reserve(n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (nodes[i] < 0 || nodes[i] >= s->n)
+      return fail(TC_ERR_ARG, "stimulus node index " + std::to_string(nodes[i]) + " out of range");
+    in.push_back(s->inv[nodes[i]]);
+  }
+  std::sort(in.begin(), in.end());
+  in.erase(std::unique(in.begin(), in.end()), in.end());
+  StimDev d{};
+  d.k0 = round_half_even(start_ms / s->dt);
+  d.nk = round_half_even(duration_ms / s->dt);
+  d.amp = intensity;
+  s->stim_nodes.push_back(std::move(in));
+  s->stim_host.push_back(d);
+  CUDA_TRY(cudaSetDevice(s->device));
+  return upload_stimuli(s);
+}
+
+tc_status tc_set_solver(tc_sim* s, double atol, double rtol, int32_t max_iter) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  if (!(atol >= 0) || !(rtol >= 0) || max_iter < 0)
+    return fail(TC_ERR_ARG, "need atol >= 0, rtol >= 0, max_iter >= 0");
+  s->atol = atol;
+  s->rtol = rtol;
+  s->max_iter = max_iter;
+  return TC_OK;
+}
+
+tc_status tc_set_activation_threshold(tc_sim* s, double v) {
+  clear_error();
+  if (!s || !std::isfinite(v)) return fail(TC_ERR_ARG, "bad threshold");
+  if (s->thr_locked) return fail(TC_ERR_STATE, "threshold is fixed once stepping has started");
+  s->thr = v;
+  if (s->model >= 0) {
+    CUDA_TRY(cudaSetDevice(s->device));
+    std::vector<double> vcur(s->n), a0(s->n);
+    CUDA_TRY(cudaMemcpy(vcur.data(), s->V[s->iv], s->n * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < s->n; ++i) a0[i] = vcur[i] >= v ? 0.0 : -1.0;
+    CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return TC_OK;
+}
+
+tc_status tc_set_wait_limit(tc_sim* s, int64_t polls) {
+  clear_error();
+  if (!s || polls < 1) return fail(TC_ERR_ARG, "need polls >= 1");
+  s->wait_limit = polls;
+  return TC_OK;
+}
+
+tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
+  clear_error();
+  if (!s || n_steps < 0) return fail(TC_ERR_ARG, "bad tc_step arguments");
+  if (s->model < 0) return fail(TC_ERR_STATE, "tc_set_ionic must be called before tc_step");
+  CUDA_TRY(cudaSetDevice(s->device));
+  s->thr_locked = true;
+  DevStats zero{};
+  CUDA_TRY(cudaMemcpyAsync(s->stats, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+  CUDA_TRY(cudaMemsetAsync(s->bar, 0, sizeof(GridBar), s->stream));
+  const double range = s->ms[6] - s->ms[5];
+  MSConst mc;
+  mc.vmin = s->ms[5];
+  mc.inv_range = 1.0 / range;
+  mc.range = range;
+  mc.vgate = s->ms[4];
+  mc.inv_tau_in = 1.0 / s->ms[0];
+  mc.inv_tau_out = 1.0 / s->ms[1];
+  mc.dec_open = std::exp(-s->dt / s->ms[2]);
+  mc.dec_close = std::exp(-s->dt / s->ms[3]);
+  const int ion_blocks = (int)((s->n + kIonicThreads - 1) / kIonicThreads);
+  size_t ev = 0;
+  std::vector<std::pair<size_t, int>> prof_pairs;
+  for (int64_t st = 0; st < n_steps; ++st) {
+    double* Vc = s->V[s->iv];
+    double* Vp = s->V[(s->iv + 2) % 3];
+    double* Vn = s->V[(s->iv + 1) % 3];
+    IonicArgs ia;
+    ia.n = s->n;
+    ia.V = Vc;
+    ia.Vp = Vp;
+    ia.h = s->state;
+    ia.g1 = s->g1;
+    ia.g2 = s->g2;
+    ia.x0 = Vn;
+    ia.stim_off = s->stim_off;
+    ia.stim_ids = s->stim_ids;
+    ia.stims = s->stims;
+    ia.k = s->k;
+    ia.chi = s->chi;
+    ia.cm = s->cm;
+    ia.dt = s->dt;
+    ia.theta = s->theta;
+    ia.ms = mc;
+    if (s->prof) {
+      cudaEvent_t e = pooled_event(s, ev);
+      if (!e) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
+      cudaEventRecord(e, s->stream);
+      prof_pairs.push_back({ev++, 0});
+    }
+    ionic_ms_kernel<<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
+    CUDA_TRY(cudaGetLastError());
+    PcgArgs pa;
+    pa.n = s->n;
+    pa.slice_ptr = s->slice_ptr;
+    pa.col = s->col;
+    pa.vM = s->vM;
+    pa.vK = s->vK;
+    pa.vA = s->vA;
+    pa.dinv = s->dinv;
+    pa.blk_slice = s->blk_slice;
+    pa.g1 = s->g1;
+    pa.g2 = s->g2;
+    pa.x = Vn;
+    pa.Vcur = Vc;
+    pa.r = s->r;
+    pa.z = s->z;
+    pa.p = s->p;
+    pa.q = s->q;
+    pa.act = s->act;
+    pa.partA = s->partA;
+    pa.partB = s->partB;
+    pa.bar = s->bar;
+    pa.err = s->err;
+    pa.stats = s->stats;
+    pa.atol = s->atol;
+    pa.rtol = s->rtol;
+    pa.max_iter = s->max_iter;
+    pa.wait_limit = s->wait_limit;
+    pa.t_k = (double)s->k * s->dt;
+    pa.dt = s->dt;
+    pa.thr = s->thr;
+    if (s->prof) {
+      cudaEvent_t e = pooled_event(s, ev);
+      cudaEventRecord(e, s->stream);
+      ev++;
+    }
+    void* args[] = {&pa};
+    CUDA_TRY(cudaLaunchCooperativeKernel((const void*)pcg_step_kernel<kPcgThreads>, s->nblocks,
+                                         kPcgThreads, args, 0, s->stream));
+    if (s->prof) {
+      cudaEvent_t e = pooled_event(s, ev);
+      cudaEventRecord(e, s->stream);
+      ev++;
+    }
+    s->iv = (s->iv + 1) % 3;
+    s->k += 1;
+  }
+  DevStats ds{};
+  int herr = 0;
+  CUDA_TRY(cudaMemcpyAsync(&ds, s->stats, sizeof(ds), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (s->prof) {
+    for (auto& pp : prof_pairs) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, s->evpool[pp.first], s->evpool[pp.first + 1]);
+      cudaEventElapsedTime(&b, s->evpool[pp.first + 1], s->evpool[pp.first + 2]);
+      s->prof_acc.ionic_ms += a;
+      s->prof_acc.ionic_launches += 1;
+      s->prof_acc.pcg_ms += b;
+      s->prof_acc.pcg_launches += 1;
+    }
+    s->prof_acc.pcg_iterations += ds.iters_total;
+  }
+  if (stats) {
+    stats->steps = n_steps;
+    stats->step_index = s->k;
+    stats->cg_iterations = ds.iters_total;
+    stats->max_iterations = ds.max_iters;
+    stats->not_converged = ds.not_conv;
+    stats->last_znorm = ds.last_zn;
+    stats->last_z0norm = ds.last_z0n;
+  }
+  if (herr & kErrTimeout) return fail(TC_ERR_TIMEOUT, "a grid barrier wait hit its limit");
+  if (herr & kErrNan) return fail(TC_ERR_NAN, "non-finite value in the PCG solve");
+  return TC_OK;
+}
+
+static double* field_ptr(const tc_sim* s, int32_t field) {
+  if (field == TC_FIELD_V) return s->V[s->iv];
+  if (field == TC_FIELD_V_PREV) return s->V[(s->iv + 2) % 3];
+  if (field >= TC_FIELD_STATE && field < TC_FIELD_STATE + s->n_states)
+    return s->state + (size_t)(field - TC_FIELD_STATE) * s->n;
+  return nullptr;
+}
+
+tc_status tc_read_state(const tc_sim* s, int32_t field, double* dst, int64_t n) {
+  clear_error();
+  if (!s || !dst) return fail(TC_ERR_ARG, "null argument");
+  if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
+  if (s->model < 0) return fail(TC_ERR_STATE, "no ionic model set");
+  const double* src = field_ptr(s, field);
+  if (!src) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
+  CUDA_TRY(cudaSetDevice(s->device));
+  double* tmp = s->pinned;
+  CUDA_TRY(cudaMemcpyAsync(tmp, src, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = tmp[i];
+  return TC_OK;
+}
+
+tc_status tc_write_state(tc_sim* s, int32_t field, const double* src, int64_t n) {
+  clear_error();
+  if (!s || !src) return fail(TC_ERR_ARG, "null argument");
+  if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
+  if (s->model < 0) return fail(TC_ERR_STATE, "no ionic model set");
+  double* dst = field_ptr(s, field);
+  if (!dst) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
+  CUDA_TRY(cudaSetDevice(s->device));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));   // the staging buffer may still feed a copy
+  double* tmp = s->pinned;
+  for (int64_t i = 0; i < s->n; ++i) tmp[i] = src[s->perm[i]];
+  CUDA_TRY(cudaMemcpyAsync(dst, tmp, s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TC_OK;
+}
+
+tc_status tc_activation_times(const tc_sim* s, double v_threshold, double* dst, int64_t n) {
+  clear_error();
+  if (!s || !dst) return fail(TC_ERR_ARG, "null argument");
+  if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
+  if (v_threshold != s->thr)
+    return fail(TC_ERR_STATE, "activation times were captured for another threshold");
+  CUDA_TRY(cudaSetDevice(s->device));
+  double* tmp = s->pinned;
+  CUDA_TRY(cudaMemcpyAsync(tmp, s->act, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = tmp[i];
+  return TC_OK;
+}
+
+tc_status tc_get_step_index(const tc_sim* s, int64_t* k) {
+  clear_error();
+  if (!s || !k) return fail(TC_ERR_ARG, "null argument");
+  *k = s->k;
+  return TC_OK;
+}
+
+tc_status tc_set_step_index(tc_sim* s, int64_t k) {
+  clear_error();
+  if (!s || k < 0) return fail(TC_ERR_ARG, "bad step index");
+  s->k = k;
+  return TC_OK;
+}
+
+static const double* op_values(const tc_sim* s, int32_t op) {
+  return op == TC_OP_M ? s->vM : op == TC_OP_K ? s->vK : op == TC_OP_A ? s->vA : nullptr;
+}
+
+tc_status tc_apply_operator_dev(tc_sim* s, int32_t op, const void* x_dev, void* y_dev) {
+  clear_error();
+  if (!s || !x_dev || !y_dev) return fail(TC_ERR_ARG, "null argument");
+  const double* val = op_values(s, op);
+  if (!val) return fail(TC_ERR_ARG, "unknown operator");
+  if (((uintptr_t)x_dev | (uintptr_t)y_dev) & 15) return fail(TC_ERR_ARG, "x/y must be 16-byte aligned");
+  CUDA_TRY(cudaSetDevice(s->device));
+  const int threads = 256;
+  const int64_t warps_needed = s->nslices;
+  const int64_t blocks = std::min<int64_t>((warps_needed * 32 + threads - 1) / threads,
+                                           (int64_t)s->num_sms * 8);
+  spmv_sell_kernel<<<(int)std::max<int64_t>(blocks, 1), threads, 0, s->stream>>>(
+      s->n, s->nslices, s->slice_ptr, s->col, val, static_cast<const double*>(x_dev),
+      static_cast<double*>(y_dev));
+  CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
+tc_status tc_apply_operator(tc_sim* s, int32_t op, const double* x, double* y, int64_t n) {
+  clear_error();
+  if (!s || !x || !y) return fail(TC_ERR_ARG, "null argument");
+  if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
+  if (!op_values(s, op)) return fail(TC_ERR_ARG, "unknown operator");
+  CUDA_TRY(cudaSetDevice(s->device));
+  std::vector<double> xi;
+  to_internal(s, x, xi);
+  double *dx = nullptr, *dy = nullptr;
+  CUDA_TRY(cudaMalloc(&dx, s->n * sizeof(double)));
+  cudaError_t e = cudaMalloc(&dy, s->n * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(dx);
+    return cuda_fail(e, "cudaMalloc");
+  }
+  std::vector<double> yi(s->n);
+  e = cudaMemcpyAsync(dx, xi.data(), s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  tc_status st = TC_OK;
+  if (e == cudaSuccess) st = tc_apply_operator_dev(s, op, dx, dy);
+  if (e == cudaSuccess && st == TC_OK)
+    e = cudaMemcpyAsync(yi.data(), dy, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(dx);
+  cudaFree(dy);
+  if (e != cudaSuccess) return cuda_fail(e, "tc_apply_operator");
+  if (st != TC_OK) return st;
+  for (int64_t i = 0; i < s->n; ++i) y[s->perm[i]] = yi[i];
+  return TC_OK;
+}
+
+tc_status tc_set_profiling(tc_sim* s, int32_t on) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  s->prof = on != 0;
+  return TC_OK;
+}
+
+tc_status tc_get_profile(const tc_sim* s, tc_profile* out) {
+  clear_error();
+  if (!s || !out) return fail(TC_ERR_ARG, "null argument");
+  *out = s->prof_acc;
+  return TC_OK;
+}
+
+tc_status tc_reset_profile(tc_sim* s) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  s->prof_acc = tc_profile{};
+  return TC_OK;
+}
+
+const char* tc_version(void) { return "tc_b300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+"""Python binding of the C ABI in include/tc.h (argument marshalling only).
+
+Every computation runs in libtc_b300.so; if the library cannot be loaded this module raises
+instead of falling back to anything else.  Arrays are numpy (host) arrays; device pointers are
+plain integers (e.g. ``torch.Tensor.data_ptr()``), streams are ``cudaStream_t`` integers (e.g.
+``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TC_OK, TC_ERR_ARG, TC_ERR_MESH, TC_ERR_STATE = 0, -1, -2, -3
+TC_ERR_CUDA, TC_ERR_NOMEM, TC_ERR_TIMEOUT, TC_ERR_NAN = -4, -5, -6, -7
+TC_MODEL_MS, TC_MODEL_TP06 = 0, 1
+TC_FP64, TC_FP32 = 0, 1
+TC_OP_M, TC_OP_K, TC_OP_A = 0, 1, 2
+TC_FIELD_V, TC_FIELD_V_PREV, TC_FIELD_STATE = 0, 1, 16
+
+_STATUS_NAMES = {0: "TC_OK", -1: "TC_ERR_ARG", -2: "TC_ERR_MESH", -3: "TC_ERR_STATE",
+                 -4: "TC_ERR_CUDA", -5: "TC_ERR_NOMEM", -6: "TC_ERR_TIMEOUT", -7: "TC_ERR_NAN"}
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class StepStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("step_index", C.c_int64), ("cg_iterations", C.c_int64),
+                ("max_iterations", C.c_int32), ("not_converged", C.c_int32),
+                ("last_znorm", C.c_double), ("last_z0norm", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Profile(C.Structure):
+    _fields_ = [("ionic_ms", C.c_double), ("ionic_launches", C.c_int64),
+                ("pcg_ms", C.c_double), ("pcg_launches", C.c_int64),
+                ("pcg_iterations", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+_SIGS = {
+    "tc_mesh_create": [_D, C.c_int64, _I32, C.c_int64, _D, _I32, C.POINTER(_P)],
+    "tc_mesh_nnz": [_P, _I64],
+    "tc_mesh_matrices": [_P, _D, _D, C.c_int32, _I64, _I32, _D, _D],
+    "tc_mesh_ordering": [_P, C.c_int32, _I32, _I32],
+    "tc_assemble": [_P, _D, _D, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
+                    C.c_int32, _P, C.POINTER(_P)],
+    "tc_sim_size": [_P, _I64, _I64, _I64, _I32],
+    "tc_set_ionic": [_P, C.c_int32, _D, C.c_int32, _D],
+    "tc_add_stimulus": [_P, _I32, C.c_int64, C.c_double, C.c_double, C.c_double],
+    "tc_set_solver": [_P, C.c_double, C.c_double, C.c_int32],
+    "tc_set_activation_threshold": [_P, C.c_double],
+    "tc_step": [_P, C.c_int64, C.POINTER(StepStats)],
+    "tc_read_state": [_P, C.c_int32, _D, C.c_int64],
+    "tc_write_state": [_P, C.c_int32, _D, C.c_int64],
+    "tc_activation_times": [_P, C.c_double, _D, C.c_int64],
+    "tc_get_step_index": [_P, _I64],
+    "tc_set_step_index": [_P, C.c_int64],
+    "tc_apply_operator": [_P, C.c_int32, _D, _D, C.c_int64],
+    "tc_apply_operator_dev": [_P, C.c_int32, _P, _P],
+    "tc_set_profiling": [_P, C.c_int32],
+    "tc_get_profile": [_P, C.POINTER(Profile)],
+    "tc_reset_profile": [_P],
+    "tc_set_wait_limit": [_P, C.c_int64],
+}
+_VOID = {"tc_mesh_destroy": [_P], "tc_sim_destroy": [_P]}
+_STR = {"tc_last_error": [], "tc_version": []}
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the in-tree libtc_b300.so and declare its signatures."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            path = _build.build()
+        L = C.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        for name, args in _VOID.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None
+        for name, args in _STR.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS) + list(_VOID) + list(_STR)
+
+
+def _check(status):
+    if status != TC_OK:
+        raise TcError(status, lib().tc_last_error().decode())
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Mesh:
+    """tc_mesh: a copied tetrahedral mesh (coordinates mm, 0-based tets, unit fibres)."""
+
+    def __init__(self, xyz, tets, fibres=None, region=None):
+        xyz = _f64(xyz).reshape(-1, 3)
+        tets = _i32(tets).reshape(-1, 4)
+        fib = None if fibres is None else _f64(fibres).reshape(-1, 3)
+        reg = None if region is None else _i32(region)
+        h = _P()
+        _check(lib().tc_mesh_create(_d(xyz), xyz.shape[0], tets.ctypes.data_as(_I32), tets.shape[0],
+                                    None if fib is None else _d(fib),
+                                    None if reg is None else reg.ctypes.data_as(_I32), C.byref(h)))
+        self._h = h
+        self.n_nodes = xyz.shape[0]
+        self.n_tets = tets.shape[0]
+
+    @classmethod
+    def from_inputs(cls, m):
+        return cls(m.xyz, m.tets, m.fibres, m.region)
+
+    @property
+    def nnz(self):
+        v = C.c_int64()
+        _check(lib().tc_mesh_nnz(self._h, C.byref(v)))
+        return v.value
+
+    def matrices(self, sigma_l, sigma_t):
+        """Host-assembled (row_ptr, col, M values, K values) in the caller's node order."""
+        sl = _f64(np.atleast_1d(sigma_l))
+        st = _f64(np.atleast_1d(sigma_t))
+        nnz = self.nnz
+        rp = np.empty(self.n_nodes + 1, dtype=np.int64)
+        col = np.empty(nnz, dtype=np.int32)
+        mv = np.empty(nnz)
+        kv = np.empty(nnz)
+        _check(lib().tc_mesh_matrices(self._h, _d(sl), _d(st), sl.size, rp.ctypes.data_as(_I64),
+                                      col.ctypes.data_as(_I32), _d(mv), _d(kv)))
+        return rp, col, mv, kv
+
+    def ordering(self, sell_sigma=1):
+        perm = np.empty(self.n_nodes, dtype=np.int32)
+        sw = np.empty((self.n_nodes + 31) // 32, dtype=np.int32)
+        _check(lib().tc_mesh_ordering(self._h, sell_sigma, perm.ctypes.data_as(_I32),
+                                      sw.ctypes.data_as(_I32)))
+        return perm, sw
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tc_mesh_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class Simulation:
+    """tc_sim: the device-resident monodomain simulation."""
+
+    def __init__(self, mesh: Mesh, sigma_l, sigma_t, chi, cm, theta, dt, precision=TC_FP64,
+                 stream=None):
+        sl = _f64(np.atleast_1d(sigma_l))
+        st = _f64(np.atleast_1d(sigma_t))
+        h = _P()
+        _check(lib().tc_assemble(mesh._h, _d(sl), _d(st), sl.size, chi, cm, theta, dt, precision,
+                                 None if stream is None else _P(int(stream)), C.byref(h)))
+        self._h = h
+        self.n_nodes = mesh.n_nodes
+
+    # -- configuration
+    def set_ionic(self, model, params, init_state=None):
+        p = _f64(np.atleast_1d(params))
+        s = None if init_state is None else _f64(init_state)
+        _check(lib().tc_set_ionic(self._h, model, _d(p), p.size, None if s is None else _d(s)))
+
+    def add_stimulus(self, nodes, start, duration, intensity):
+        nd = _i32(nodes)
+        _check(lib().tc_add_stimulus(self._h, nd.ctypes.data_as(_I32), nd.size, start, duration,
+                                     intensity))
+
+    def set_solver(self, atol, rtol, max_iter):
+        _check(lib().tc_set_solver(self._h, atol, rtol, max_iter))
+
+    def set_activation_threshold(self, v):
+        _check(lib().tc_set_activation_threshold(self._h, v))
+
+    def set_wait_limit(self, polls):
+        _check(lib().tc_set_wait_limit(self._h, polls))
+
+    # -- stepping and I/O
+    def step(self, n_steps=1):
+        st = StepStats()
+        _check(lib().tc_step(self._h, n_steps, C.byref(st)))
+        return st.as_dict()
+
+    def read(self, field=TC_FIELD_V):
+        out = np.empty(self.n_nodes)
+        _check(lib().tc_read_state(self._h, field, _d(out), self.n_nodes))
+        return out
+
+    def write(self, field, values):
+        v = _f64(values)
+        _check(lib().tc_write_state(self._h, field, _d(v), v.size))
+
+    def activation_times(self, v_threshold=0.0):
+        out = np.empty(self.n_nodes)
+        _check(lib().tc_activation_times(self._h, v_threshold, _d(out), self.n_nodes))
+        return out
+
+    @property
+    def step_index(self):
+        v = C.c_int64()
+        _check(lib().tc_get_step_index(self._h, C.byref(v)))
+        return v.value
+
+    @step_index.setter
+    def step_index(self, k):
+        _check(lib().tc_set_step_index(self._h, k))
+
+    def apply(self, op, x):
+        x = _f64(x)
+        y = np.empty(self.n_nodes)
+        _check(lib().tc_apply_operator(self._h, op, _d(x), _d(y), x.size))
+        return y
+
+    def apply_dev(self, op, x_ptr: int, y_ptr: int):
+        _check(lib().tc_apply_operator_dev(self._h, op, _P(x_ptr), _P(y_ptr)))
+
+    def size(self):
+        n, nnz, pad = C.c_int64(), C.c_int64(), C.c_int64()
+        nb = C.c_int32()
+        _check(lib().tc_sim_size(self._h, C.byref(n), C.byref(nnz), C.byref(pad), C.byref(nb)))
+        return {"n_nodes": n.value, "nnz": nnz.value, "padded_nnz": pad.value, "n_blocks": nb.value}
+
+    def set_profiling(self, on=True):
+        _check(lib().tc_set_profiling(self._h, int(bool(on))))
+
+    def profile(self):
+        p = Profile()
+        _check(lib().tc_get_profile(self._h, C.byref(p)))
+        return p.as_dict()
+
+    def reset_profile(self):
+        _check(lib().tc_reset_profile(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tc_sim_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def from_workload(w, stream=None, precision=TC_FP64):
+    """Build a Simulation from an ``inputs.Workload`` (mesh, tissue, model, stimuli, solver)."""
+    mesh = Mesh.from_inputs(w.mesh)
+    sim = Simulation(mesh, w.sigma_l, w.sigma_t, w.chi, w.cm, w.theta, w.dt, precision, stream)
+    sim.mesh = mesh
+    sim.set_activation_threshold(w.v_threshold)
+    if w.model == "ms":
+        sim.set_ionic(TC_MODEL_MS, w.ms.as_array())
+    else:
+        raise TcError(TC_ERR_ARG, f"model {w.model!r} is not available")
+    for s in w.stimuli:
+        sim.add_stimulus(s.nodes, s.start, s.duration, s.intensity)
+    sim.set_solver(w.atol, w.rtol, w.max_iter)
+    return sim
