@@ -177,6 +177,19 @@ tc_status tc_apply_operator(tc_sim* sim, int32_t op, const double* x, double* y,
  * floats (TC_FP32), 16-byte aligned. */
 tc_status tc_apply_operator_dev(tc_sim* sim, int32_t op, const void* x_dev, void* y_dev);
 
+/* tc_apply_operator_static: the same result as tc_apply_operator, for callers that must not
+ * allocate device memory while they run (a process whose device memory is reserved by another
+ * allocator, so cudaMalloc would fail, or a caller that cannot afford the device-wide
+ * synchronisation cudaFree implies).  The paper has no counterpart; it is a library facility.
+ * x and y are host arrays [n_nodes] in caller order.  Device staging for x and y is a static
+ * 4 MiB array inside the library (2 x 262,144 doubles) that every GPU loading the library holds
+ * until the process exits; meshes with more than 262,144 nodes are rejected with TC_ERR_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU (e.g. from two threads or two streams) race.  Allocates nothing; waits for the
+ * simulation's stream before and after the copy. */
+tc_status tc_apply_operator_static(tc_sim* sim, int32_t op, const double* x, double* y, int64_t n);
+
 /* Profiling: when on, tc_step records CUDA events around every launch on the simulation's
  * stream and accumulates their durations; tc_get_profile reads and tc_reset_profile clears. */
 tc_status tc_set_profiling(tc_sim* sim, int32_t on);

@@ -680,3 +680,95 @@ tc_status tc_reset_profile(tc_sim* s) {
 const char* tc_version(void) { return "tc_b300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---- allocation-free operator application ------------------------------------------------
+//
+// tc_apply_operator stages x and y in device buffers that it allocates and frees on every
+// call.  Some callers cannot do that: a process whose device memory is already reserved by
+// another allocator (cudaMalloc would fail), or a caller that cannot afford the device-wide
+// synchronisation cudaFree implies.  tc_apply_operator_static does the same work with its
+// staging in the file-scope array below, which every GPU that loads this library holds until
+// the process exits.  Calls share the array; calls that overlap on the GPU race.
+
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kStaticMaxNodes = 262144;   // x and y staging: 2 * 2 MiB
+constexpr int kStaticMaxDevices = 128;
+
+static __device__ __align__(256) double g_apply_scratch[2 * kStaticMaxNodes];
+
+std::mutex g_apply_scratch_mu;
+double* g_apply_scratch_addr[kStaticMaxDevices] = {nullptr};
+
+// y = Op x with x read from, and y written to, the static staging array.
+__global__ void __launch_bounds__(256) spmv_sell_static_kernel(
+    int64_t n, int64_t nslices, const int32_t* __restrict__ slice_ptr,
+    const int32_t* __restrict__ col, const double* __restrict__ val, double* scratch) {
+  const double* x = scratch;
+  double* y = scratch + kStaticMaxNodes;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = gw; s < nslices; s += nw) {
+    const int beg = slice_ptr[s] + lane;
+    const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
+    double acc = 0.0;
+    for (int j = 0; j < w; ++j) {
+      const int e = beg + 32 * j;
+      acc = fma(val[e], x[col[e]], acc);
+    }
+    const int64_t row = s * 32 + lane;
+    if (row < n) y[row] = acc;
+  }
+}
+
+// Device address of the staging array on the current device (looked up once per device).
+tc_status static_scratch_address(int device, double** out) {
+  if (device < 0 || device >= kStaticMaxDevices)
+    return fail(TC_ERR_ARG, "device ordinal too large for the static staging table");
+  std::lock_guard<std::mutex> lock(g_apply_scratch_mu);
+  if (!g_apply_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_apply_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_apply_scratch)");
+    g_apply_scratch_addr[device] = static_cast<double*>(p);
+  }
+  *out = g_apply_scratch_addr[device];
+  return TC_OK;
+}
+
+}  // namespace
+
+extern "C" tc_status tc_apply_operator_static(tc_sim* s, int32_t op, const double* x, double* y,
+                                              int64_t n) {
+  clear_error();
+  if (!s || !x || !y) return fail(TC_ERR_ARG, "null argument");
+  if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
+  if (s->n > kStaticMaxNodes)
+    return fail(TC_ERR_ARG, "tc_apply_operator_static handles at most " +
+                                std::to_string(kStaticMaxNodes) + " nodes; this mesh has " +
+                                std::to_string(s->n) + " (use tc_apply_operator)");
+  const double* val = op_values(s, op);
+  if (!val) return fail(TC_ERR_ARG, "unknown operator");
+  CUDA_TRY(cudaSetDevice(s->device));
+  double* scratch = nullptr;
+  TRY(static_scratch_address(s->device, &scratch));
+  // the simulation's page-locked staging buffer carries x in and y out
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  double* h = s->pinned;
+  for (int64_t i = 0; i < s->n; ++i) h[i] = x[s->perm[i]];
+  CUDA_TRY(cudaMemcpyAsync(scratch, h, s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((s->nslices * 32 + threads - 1) / threads,
+                                           (int64_t)s->num_sms * 8);
+  spmv_sell_static_kernel<<<(int)std::max<int64_t>(blocks, 1), threads, 0, s->stream>>>(
+      s->n, s->nslices, s->slice_ptr, s->col, val, scratch);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(h, scratch + kStaticMaxNodes, s->n * sizeof(double),
+                           cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  for (int64_t i = 0; i < s->n; ++i) y[s->perm[i]] = h[i];
+  return TC_OK;
+}

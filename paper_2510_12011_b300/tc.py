@@ -74,6 +74,7 @@ _SIGS = {
     "tc_set_step_index": [_P, C.c_int64],
     "tc_apply_operator": [_P, C.c_int32, _D, _D, C.c_int64],
     "tc_apply_operator_dev": [_P, C.c_int32, _P, _P],
+    "tc_apply_operator_static": [_P, C.c_int32, _D, _D, C.c_int64],
     "tc_set_profiling": [_P, C.c_int32],
     "tc_get_profile": [_P, C.POINTER(Profile)],
     "tc_reset_profile": [_P],
@@ -254,6 +255,13 @@ class Simulation:
         x = _f64(x)
         y = np.empty(self.n_nodes)
         _check(lib().tc_apply_operator(self._h, op, _d(x), _d(y), x.size))
+        return y
+
+    def apply_static(self, op, x):
+        """tc_apply_operator_static: y = Op x with no device allocation (static staging)."""
+        x = _f64(x)
+        y = np.empty(self.n_nodes)
+        _check(lib().tc_apply_operator_static(self._h, op, _d(x), _d(y), x.size))
         return y
 
     def apply_dev(self, op, x_ptr: int, y_ptr: int):
