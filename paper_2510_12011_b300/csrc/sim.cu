@@ -1,6 +1,7 @@
 // Device-side simulation object and the C ABI calls that touch the GPU.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -15,8 +16,15 @@ using namespace tc;
 
 namespace {
 
-constexpr int kPcgThreads = 512;
 constexpr int kIonicThreads = 256;
+
+// Launch shape of the PCG kernel: 512 or 1024 threads per block, blocks per SM, and the SELL
+// sorting window; defaults can be overridden through TC_PCG_THREADS, TC_PCG_BLOCKS_PER_SM and
+// TC_SELL_SIGMA (used by the launch-shape sweep).
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
 
 struct Dev {
   void* p = nullptr;
@@ -31,7 +39,7 @@ struct tc_sim {
   int64_t n = 0, nnz = 0, nslices = 0, padded = 0;
   int precision = TC_FP64;
   std::vector<int32_t> perm, inv;   // perm[new] = old
-  int num_sms = 0, blocks_per_sm = 2, nblocks = 0;
+  int num_sms = 0, blocks_per_sm = 1, nblocks = 0, pcg_threads = 1024, sell_sigma = 1024;
   // device arrays
   int32_t *slice_ptr = nullptr, *col = nullptr, *blk_slice = nullptr;
   double *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
@@ -125,14 +133,18 @@ tc_status upload_stimuli(tc_sim* s) {
   return TC_OK;
 }
 
+const void* pcg_kernel_ptr(int threads) {
+  return threads == 1024 ? (const void*)pcg_step_kernel<1024> : (const void*)pcg_step_kernel<512>;
+}
+
 tc_status set_partition(tc_sim* s) {
   int bps = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pcg_step_kernel<kPcgThreads>,
-                                                         kPcgThreads, 0));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pcg_kernel_ptr(s->pcg_threads),
+                                                         s->pcg_threads, 0));
   if (bps < 1) return fail(TC_ERR_CUDA, "PCG kernel cannot be resident on an SM");
   const int per_sm = std::min(bps, std::max(1, s->blocks_per_sm));
   const int64_t max_blocks = (int64_t)per_sm * s->num_sms;
-  constexpr int kWarps = kPcgThreads / 32;
+  const int kWarps = s->pcg_threads / 32;
   const int64_t want = (s->nslices + kWarps - 1) / kWarps;   // at least one slice per warp
   s->nblocks = (int)std::max<int64_t>(1, std::min(max_blocks, want));
   std::vector<int32_t> bs(s->nblocks + 1);
@@ -199,9 +211,12 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   s->n = mesh->n;
   const Csr& pat = mesh->pattern;
   s->nnz = pat.row_ptr[mesh->n];
+  s->pcg_threads = env_int("TC_PCG_THREADS", 1024) == 512 ? 512 : 1024;
+  s->blocks_per_sm = std::max(1, env_int("TC_PCG_BLOCKS_PER_SM", s->pcg_threads == 1024 ? 1 : 2));
+  s->sell_sigma = std::max(1, env_int("TC_SELL_SIGMA", 1024));
   Sell sell;
   try {
-    node_ordering(pat, 1, s->perm);
+    node_ordering(pat, s->sell_sigma, s->perm);
     tc_status st = build_sell(pat, s->perm, sell);
     if (st != TC_OK) return bail(st);
   } catch (const std::bad_alloc&) {
@@ -452,6 +467,7 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
     ia.dt = s->dt;
     ia.theta = s->theta;
     ia.ms = mc;
+    ia.bar = s->bar;
     if (s->prof) {
       cudaEvent_t e = pooled_event(s, ev);
       if (!e) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
@@ -496,8 +512,8 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
       ev++;
     }
     void* args[] = {&pa};
-    CUDA_TRY(cudaLaunchCooperativeKernel((const void*)pcg_step_kernel<kPcgThreads>, s->nblocks,
-                                         kPcgThreads, args, 0, s->stream));
+    CUDA_TRY(cudaLaunchCooperativeKernel(pcg_kernel_ptr(s->pcg_threads), s->nblocks,
+                                         s->pcg_threads, args, 0, s->stream));
     if (s->prof) {
       cudaEvent_t e = pooled_event(s, ev);
       cudaEventRecord(e, s->stream);
@@ -714,11 +730,7 @@ __global__ void __launch_bounds__(256) spmv_sell_static_kernel(
   for (int64_t s = gw; s < nslices; s += nw) {
     const int beg = slice_ptr[s] + lane;
     const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
-    double acc = 0.0;
-    for (int j = 0; j < w; ++j) {
-      const int e = beg + 32 * j;
-      acc = fma(val[e], x[col[e]], acc);
-    }
+    const double acc = sell_dot(col, val, beg, w, x);
     const int64_t row = s * 32 + lane;
     if (row < n) y[row] = acc;
   }

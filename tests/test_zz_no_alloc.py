@@ -6,6 +6,7 @@ contents, so the second call checks that nothing leaks from the first).  Collect
 import numpy as np
 import pytest
 
+from oracle import fem
 from paper_2510_12011_b300 import inputs as I
 from paper_2510_12011_b300 import tc
 
@@ -15,12 +16,16 @@ pytestmark = pytest.mark.gpu
 def test_static_operator_matches_allocating_entry_point():
     w = I.slab_small_ms()
     sim = tc.from_workload(w)
+    m = w.mesh
+    M, K = fem.mass_stiffness(m.xyz, m.tets, m.fibres, w.sigma_l, w.sigma_t)
+    A = fem.system_matrix(M, K, w.chi, w.cm, w.theta, w.dt)
     for call, seed in enumerate((101, 202)):
         x = I.random_vector(w.mesh.n_nodes, seed, -90.0, 30.0)
-        for op in (tc.TC_OP_M, tc.TC_OP_K, tc.TC_OP_A):
+        for op, mat in ((tc.TC_OP_M, M), (tc.TC_OP_K, K), (tc.TC_OP_A, A)):
             ref = sim.apply(op, x)
             got = sim.apply_static(op, x)
-            bound = 32 * np.finfo(float).eps * (np.abs(ref) + 1e-300)
+            # the bound of the operator parity tests: reordered sums of the row's products
+            bound = 32 * np.finfo(float).eps * (abs(mat) @ np.abs(x))
             assert np.all(np.abs(got - ref) <= bound), (call, op)
 
 
