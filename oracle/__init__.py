@@ -12,6 +12,8 @@ What it computes, and where the paper defines it (TorchCor, arXiv 2510.12011):
   * pcg.py        Jacobi-preconditioned conjugate gradients (Section 2.2, Algorithm 1)
   * ionic.py      Mitchell-Schaeffer ionic model with a Rush-Larsen gate (the model is not
                   written out in the paper; our mV mapping is stated in ionic.py)
+  * tp06.py       ten Tusscher-Panfilov 2006 (named in Section 2.2, not printed; restated from
+                  the model's own publication; pinned by its charge balance and AP features)
   * monodomain.py the operator-split time step (Eq. 2, Eq. 3), stimulus (Section 2.1),
                   extrapolated initial guess (end of Section 2.2) and activation times
                   (Section 2.1, "LAT")

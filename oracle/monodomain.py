@@ -15,7 +15,7 @@ k with k0 <= k < k0 + nk, k0 = round(start/dt), nk = round(duration/dt); I_stim 
 """
 import numpy as np
 
-from . import fem, ionic
+from . import fem, ionic, tp06
 from .pcg import pcg
 
 
@@ -58,6 +58,9 @@ class Monodomain:
         if w.model == "ms":
             self.V, h = ionic.ms_rest(n, w.ms)
             self.state = [h]
+        elif w.model == "tp06":
+            self.V, u = tp06.rest(n)
+            self.state = [u[:, j].copy() for j in range(tp06.N_STATES)]
         else:
             raise ValueError(f"model {w.model!r} not available in the oracle")
         self.V_prev = self.V.copy()
@@ -72,6 +75,11 @@ class Monodomain:
         if w.model == "ms":
             h, i_ion = ionic.ms_step(self.V, self.state[0], w.dt, w.cm, w.ms)
             return [h], i_ion
+        if w.model == "tp06":
+            # TP06 currents are in pA/pF; times Cm (uF/mm^2) they are uA/mm^2
+            u = np.stack(self.state, axis=1)
+            un, i_pa = tp06.step(self.V, u, w.dt, w.tp06_cell)
+            return [un[:, j].copy() for j in range(tp06.N_STATES)], w.cm * i_pa
         raise ValueError(w.model)
 
     def step(self):

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libtc_b300.so")
 SOURCES = ["mesh.cpp", "sim.cu"]
-HEADERS = ["tc_internal.h", "kernels.cuh"]
+HEADERS = ["tc_internal.h", "kernels.cuh", "ionic_tp06.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,266 @@
+// ten Tusscher-Panfilov 2006 human ventricular model: device kernel and resting state.
+//
+// The paper's volume-mesh runs use this model (Section 2.2, Section 3.3) without printing it;
+// the equations follow the model's own publication (ten Tusscher & Panfilov, Am J Physiol
+// Heart Circ Physiol 291:H1088, 2006) in its rapid-buffering differential form.  Units: mV, ms,
+// mM, currents in pA/pF (multiplied by Cm in uF/mm^2 they are uA/mm^2).
+//
+// State layout: SoA, state[j * n + i] for node i, j =
+//   0 Ki  1 Nai  2 Cai  3 CaSR  4 CaSS  5 Rbar  6 xr1  7 xr2  8 xs  9 m  10 h  11 j
+//   12 d  13 f  14 f2  15 fCass  16 s  17 r
+// Step (operator splitting of Eq. 2 with Rush-Larsen gates): all rates at (V^k, u^k); gates by
+// u_inf + (u - u_inf) exp(-dt/tau); concentrations and Rbar by forward Euler; then
+// I_ion(V^k, u^{k+1}).  The stimulus does not enter Ki (it is applied through the PDE source).
+#pragma once
+
+#include <cmath>
+#include "kernels.cuh"
+
+namespace tc {
+
+constexpr int kTP06States = 18;
+
+namespace tp06 {
+constexpr double kR = 8314.472, kT = 310.0, kF = 96485.3415;
+constexpr double kRTF = kR * kT / kF;
+constexpr double kCap = 0.185, kVc = 0.016404, kVsr = 0.001094, kVss = 0.00005468;
+constexpr double kKo = 5.4, kNao = 140.0, kCao = 2.0;
+constexpr double kGNa = 14.838, kGK1 = 5.405, kGKr = 0.153, kGpK = 0.0146, kGpCa = 0.1238;
+constexpr double kGbNa = 0.00029, kGbCa = 0.000592, kGCaL = 3.98e-5;
+constexpr double kPKNa = 0.03, kKpCa = 0.0005, kPNaK = 2.724, kKmK = 1.0, kKmNa = 40.0;
+constexpr double kKNaCa = 1000.0, kKmNai = 87.5, kKmCa = 1.38, kKsat = 0.1, kGam = 0.35;
+constexpr double kAlphaNaCa = 2.5;
+constexpr double kVmaxUp = 0.006375, kKup = 0.00025, kVrel = 0.102, kVleak = 0.00036;
+constexpr double kVxfer = 0.0038, kK1p = 0.15, kK2p = 0.045, kK3 = 0.06, kK4 = 0.005;
+constexpr double kEC = 1.5, kMaxSR = 2.5, kMinSR = 1.0;
+constexpr double kBufc = 0.2, kKbufc = 0.001, kBufsr = 10.0, kKbufsr = 0.3, kBufss = 0.4;
+constexpr double kKbufss = 0.00025;
+constexpr double kRestV = -85.23;
+}  // namespace tp06
+
+inline void tp06_rest_state(int /*cell*/, double* u, double* v0) {
+  const double r[kTP06States] = {136.89, 8.604,   0.000126, 3.64,   0.00036, 0.9073,
+                                 0.00621, 0.4712, 0.0095,   0.00172, 0.7444, 0.7045,
+                                 3.373e-5, 0.7888, 0.9755,  0.9953, 0.999998, 2.42e-8};
+  for (int j = 0; j < kTP06States; ++j) u[j] = r[j];
+  *v0 = tp06::kRestV;
+}
+
+__device__ __forceinline__ double mexp(double x) { return exp(x); }
+__device__ __forceinline__ float mexp(float x) { return expf(x); }
+__device__ __forceinline__ double mlog(double x) { return log(x); }
+__device__ __forceinline__ float mlog(float x) { return logf(x); }
+__device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double mexpm1(double x) { return expm1(x); }
+__device__ __forceinline__ float mexpm1(float x) { return expm1f(x); }
+
+// Voltage-only factors shared by the two current evaluations of a step.
+template <typename T>
+struct Tp06VFactors {
+  T ghk;        // L-type driving factor without CaSS: split into a and b so that
+  T ghk_cass;   // I_CaL / (g d f f2 fCass) = ghk_cass * CaSS + ghk
+  T nak;        // I_NaK / (Nai / (Nai + KmNa))
+  T naca_a;     // exp(gamma V F/RT) / denominator * kNaCa
+  T naca_b;     // exp((gamma-1) V F/RT) / denominator * kNaCa * alpha
+  T ipk;        // 1 / (1 + exp((25 - V)/5.98))
+};
+
+template <typename T>
+__device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
+  using namespace tp06;
+  Tp06VFactors<T> f;
+  const T vm = V - T(15);
+  const T x = T(2) * vm / T(kRTF);
+  if (x != T(0)) {
+    const T c = T(4) * vm * T(kF / kRTF) / mexpm1(x);
+    f.ghk_cass = c * T(0.25) * mexp(x);
+    f.ghk = -c * T(kCao);
+  } else {   // limit V -> 15 mV: 2 F (0.25 CaSS - Cao)
+    f.ghk_cass = T(2 * kF * 0.25);
+    f.ghk = T(-2 * kF * kCao);
+  }
+  const T vf = V / T(kRTF);
+  f.nak = T(kPNaK * kKo / (kKo + kKmK)) /
+          (T(1) + T(0.1245) * mexp(T(-0.1) * vf) + T(0.0353) * mexp(-vf));
+  const T eg = mexp(T(kGam) * vf), eg1 = mexp(T(kGam - 1.0) * vf);
+  const T den = T((kKmNai * kKmNai * kKmNai + kNao * kNao * kNao) * (kKmCa + kCao)) *
+                (T(1) + T(kKsat) * eg1);
+  f.naca_a = T(kKNaCa) * eg / den;
+  f.naca_b = T(kKNaCa * kAlphaNaCa * kNao * kNao * kNao) * eg1 / den;
+  f.ipk = T(1) / (T(1) + mexp((T(25) - V) / T(5.98)));
+  return f;
+}
+
+template <typename T>
+struct Tp06Currents {
+  T ik1, ito, ikr, iks, ipk, ina, ibna, inak, inaca, ical, ibca, ipca;
+  __device__ __forceinline__ T total() const {
+    return ik1 + ito + ikr + iks + ina + ibna + ical + ibca + inak + inaca + ipca + ipk;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int cell,
+                                                         const Tp06VFactors<T>& f) {
+  using namespace tp06;
+  const T ki = u[0], nai = u[1], cai = u[2], cass = u[4];
+  const T ek = T(kRTF) * mlog(T(kKo) / ki);
+  const T ena = T(kRTF) * mlog(T(kNao) / nai);
+  const T eks = T(kRTF) * mlog(T(kKo + kPKNa * kNao) / (ki + T(kPKNa) * nai));
+  const T eca = T(0.5 * kRTF) * mlog(T(kCao) / cai);
+  const T dv = V - ek;
+  const T ak1 = T(0.1) / (T(1) + mexp(T(0.06) * (dv - T(200))));
+  const T bk1 = (T(3) * mexp(T(0.0002) * (dv + T(100))) + mexp(T(0.1) * (dv - T(10)))) /
+                (T(1) + mexp(T(-0.5) * dv));
+  Tp06Currents<T> c;
+  const T gto = cell == 0 ? T(0.073) : T(0.294);
+  const T gks = cell == 1 ? T(0.098) : T(0.392);
+  c.ik1 = T(kGK1) * (ak1 / (ak1 + bk1)) * dv;   // sqrt(Ko/5.4) = 1 at Ko = 5.4 mM
+  c.ito = gto * u[17] * u[16] * dv;
+  c.ikr = T(kGKr) * u[6] * u[7] * dv;
+  c.iks = gks * u[8] * u[8] * (V - eks);
+  c.ina = T(kGNa) * u[9] * u[9] * u[9] * u[10] * u[11] * (V - ena);
+  c.ibna = T(kGbNa) * (V - ena);
+  c.ical = T(kGCaL) * u[12] * u[13] * u[14] * u[15] * (f.ghk_cass * cass + f.ghk);
+  c.ibca = T(kGbCa) * (V - eca);
+  c.inak = f.nak * (nai / (nai + T(kKmNa)));
+  c.inaca = f.naca_a * (nai * nai * nai) * T(kCao) - f.naca_b * cai;
+  c.ipca = T(kGpCa) * cai / (T(kKpCa) + cai);
+  c.ipk = T(kGpK) * f.ipk * dv;
+  return c;
+}
+
+// Rush-Larsen update of one gate: u_inf + (u - u_inf) exp(-dt/tau).
+template <typename T>
+__device__ __forceinline__ T rl(T u, T inf, T tau, T dt) {
+  return inf + (u - inf) * mexp(-dt / tau);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
+  using namespace tp06;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) a.bar->count = 0u;
+  if (i >= a.n) return;
+  const int64_t n = a.n;
+  const T V = a.V[i], Vp = a.Vp[i];
+  const T dt = T(a.dt);
+  T u[kTP06States];
+#pragma unroll
+  for (int j = 0; j < kTP06States; ++j) u[j] = a.state[j * n + i];
+  const Tp06VFactors<T> vf = tp06_vfactors(V);
+  const Tp06Currents<T> c = tp06_currents(V, u, a.cell, vf);
+
+  // concentrations and Rbar: forward Euler from the rates at (V^k, u^k)
+  T un[kTP06States];
+  {
+    const T cai = u[2], casr = u[3], cass = u[4], rbar = u[5];
+    const T ecs = T(kEC) / casr;
+    const T kcasr = T(kMaxSR) - T(kMaxSR - kMinSR) / (T(1) + ecs * ecs);
+    const T k1 = T(kK1p) / kcasr, k2 = T(kK2p) * kcasr;
+    const T cass2 = cass * cass;
+    const T o = k1 * cass2 * rbar / (T(kK3) + k1 * cass2);
+    const T irel = T(kVrel) * o * (casr - cass);
+    const T ileak = T(kVleak) * (casr - cai);
+    const T iup = T(kVmaxUp) / (T(1) + T(kKup * kKup) / (cai * cai));
+    const T ixfer = T(kVxfer) * (cass - cai);
+    const T bi = cai + T(kKbufc), bsr = casr + T(kKbufsr), bss = cass + T(kKbufss);
+    const T fi = T(1) / (T(1) + T(kBufc * kKbufc) / (bi * bi));
+    const T fsr = T(1) / (T(1) + T(kBufsr * kKbufsr) / (bsr * bsr));
+    const T fss = T(1) / (T(1) + T(kBufss * kKbufss) / (bss * bss));
+    const T cvf = T(kCap / (kVc * kF));
+    const T dki = -(c.ik1 + c.ito + c.ikr + c.iks + c.ipk - T(2) * c.inak) * cvf;
+    const T dnai = -(c.ina + c.ibna + T(3) * c.inak + T(3) * c.inaca) * cvf;
+    const T dcai = fi * ((ileak - iup) * T(kVsr / kVc) + ixfer -
+                         (c.ibca + c.ipca - T(2) * c.inaca) * T(kCap / (2 * kVc * kF)));
+    const T dcasr = fsr * (iup - (irel + ileak));
+    const T dcass = fss * (-c.ical * T(kCap / (2 * kVss * kF)) + irel * T(kVsr / kVss) -
+                           ixfer * T(kVc / kVss));
+    const T drbar = -k2 * cass * rbar + T(kK4) * (T(1) - rbar);
+    un[0] = u[0] + dt * dki;
+    un[1] = u[1] + dt * dnai;
+    un[2] = cai + dt * dcai;
+    un[3] = casr + dt * dcasr;
+    un[4] = cass + dt * dcass;
+    un[5] = rbar + dt * drbar;
+  }
+  // gates: Rush-Larsen with inf and tau at V^k (fCass at CaSS^k)
+  {
+    const T e1 = mexp((T(-56.86) - V) / T(9.03));
+    const T minf = T(1) / ((T(1) + e1) * (T(1) + e1));
+    const T am = T(1) / (T(1) + mexp((T(-60) - V) / T(5)));
+    const T bm = T(0.1) / (T(1) + mexp((V + T(35)) / T(5))) +
+                 T(0.1) / (T(1) + mexp((V - T(50)) / T(200)));
+    un[9] = rl(u[9], minf, am * bm, dt);
+    const T e2 = mexp((V + T(71.55)) / T(7.43));
+    const T hinf = T(1) / ((T(1) + e2) * (T(1) + e2));
+    T ah, bh, aj, bj;
+    if (V < T(-40)) {
+      ah = T(0.057) * mexp(-(V + T(80)) / T(6.8));
+      bh = T(2.7) * mexp(T(0.079) * V) + T(3.1e5) * mexp(T(0.3485) * V);
+      aj = (T(-2.5428e4) * mexp(T(0.2444) * V) - T(6.948e-6) * mexp(T(-0.04391) * V)) *
+           (V + T(37.78)) / (T(1) + mexp(T(0.311) * (V + T(79.23))));
+      bj = T(0.02424) * mexp(T(-0.01052) * V) / (T(1) + mexp(T(-0.1378) * (V + T(40.14))));
+    } else {
+      ah = T(0);
+      bh = T(0.77) / (T(0.13) * (T(1) + mexp(-(V + T(10.66)) / T(11.1))));
+      aj = T(0);
+      bj = T(0.6) * mexp(T(0.057) * V) / (T(1) + mexp(T(-0.1) * (V + T(32))));
+    }
+    un[10] = rl(u[10], hinf, T(1) / (ah + bh), dt);
+    un[11] = rl(u[11], hinf, T(1) / (aj + bj), dt);
+    const T xr1inf = T(1) / (T(1) + mexp((T(-26) - V) / T(7)));
+    const T txr1 = T(450) / (T(1) + mexp((T(-45) - V) / T(10))) * T(6) /
+                   (T(1) + mexp((V + T(30)) / T(11.5)));
+    un[6] = rl(u[6], xr1inf, txr1, dt);
+    const T xr2inf = T(1) / (T(1) + mexp((V + T(88)) / T(24)));
+    const T txr2 = T(3) / (T(1) + mexp((T(-60) - V) / T(20))) * T(1.12) /
+                   (T(1) + mexp((V - T(60)) / T(20)));
+    un[7] = rl(u[7], xr2inf, txr2, dt);
+    const T xsinf = T(1) / (T(1) + mexp((T(-5) - V) / T(14)));
+    const T txs = T(1400) / msqrt(T(1) + mexp((T(5) - V) / T(6))) /
+                  (T(1) + mexp((V - T(35)) / T(15))) + T(80);
+    un[8] = rl(u[8], xsinf, txs, dt);
+    const T rinf = T(1) / (T(1) + mexp((T(20) - V) / T(6)));
+    const T vr = V + T(40);
+    un[17] = rl(u[17], rinf, T(9.5) * mexp(-vr * vr / T(1800)) + T(0.8), dt);
+    T sinf, ts;
+    if (a.cell == 0) {
+      sinf = T(1) / (T(1) + mexp((V + T(28)) / T(5)));
+      const T vs = V + T(67);
+      ts = T(1000) * mexp(-vs * vs / T(1000)) + T(8);
+    } else {
+      sinf = T(1) / (T(1) + mexp((V + T(20)) / T(5)));
+      const T vs = V + T(45);
+      ts = T(85) * mexp(-vs * vs / T(320)) + T(5) / (T(1) + mexp((V - T(20)) / T(5))) + T(3);
+    }
+    un[16] = rl(u[16], sinf, ts, dt);
+    const T dinf = T(1) / (T(1) + mexp((T(-8) - V) / T(7.5)));
+    const T td = (T(1.4) / (T(1) + mexp((T(-35) - V) / T(13))) + T(0.25)) * T(1.4) /
+                     (T(1) + mexp((V + T(5)) / T(5))) +
+                 T(1) / (T(1) + mexp((T(50) - V) / T(20)));
+    un[12] = rl(u[12], dinf, td, dt);
+    const T finf = T(1) / (T(1) + mexp((V + T(20)) / T(7)));
+    const T vf27 = V + T(27);
+    const T tf = T(1102.5) * mexp(-vf27 * vf27 / T(225)) + T(200) / (T(1) + mexp((T(13) - V) / T(10))) +
+                 T(180) / (T(1) + mexp((V + T(30)) / T(10))) + T(20);
+    un[13] = rl(u[13], finf, tf, dt);
+    const T f2inf = T(0.67) / (T(1) + mexp((V + T(35)) / T(7))) + T(0.33);
+    const T vf25 = V + T(25);
+    const T tf2 = T(600) * mexp(-vf25 * vf25 / T(170)) + T(31) / (T(1) + mexp((T(25) - V) / T(10))) +
+                  T(16) / (T(1) + mexp((V + T(30)) / T(10)));
+    un[14] = rl(u[14], f2inf, tf2, dt);
+    const T cs = u[4] / T(0.05);
+    const T cs2 = cs * cs;
+    un[15] = rl(u[15], T(0.6) / (T(1) + cs2) + T(0.4), T(80) / (T(1) + cs2) + T(2), dt);
+  }
+#pragma unroll
+  for (int j = 0; j < kTP06States; ++j) a.state[j * n + i] = un[j];
+  // I_ion(V^k, u^{k+1}) in uA/mm^2
+  const T iion = T(a.cm) * tp06_currents(V, un, a.cell, vf).total();
+  const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, a.k));
+  rhs_epilogue(a, i, V, Vp, iion, is);
+}
+
+}  // namespace tc

@@ -1,9 +1,14 @@
-// Device kernels of the monodomain time step (FP64 path).
+// Device kernels of the monodomain time step.
 //
 // Data layout (all in the internal node order: reverse Cuthill-McKee, then SELL-C-sigma row
 // sorting): matrices in SELL-C-sigma with C = 32 (one warp per slice, one lane per row;
 // entry j of the row in lane l of slice s sits at slice_ptr[s] + 32*j + l), one shared int32
 // column array and one value array per matrix (M, K, A); node vectors are dense arrays.
+//
+// Every kernel is a template on the storage and arithmetic type T of the matrices and node
+// vectors: T = double is the plain FP64 method; T = float is the precision form, in which the
+// SpMVs, vector updates and the ionic model run in FP32 while the PCG reductions (block and
+// grid sums), alpha, beta, the norms and the stopping test stay in FP64.
 #pragma once
 
 #include <cstdint>
@@ -42,40 +47,46 @@ struct MSConst {
   double vmin, inv_range, range, vgate, inv_tau_in, inv_tau_out, dec_open, dec_close;
 };
 
+// Per-node inputs of the right-hand side and the initial guess, written by the ionic kernels:
+//   g1 = chi (Cm (V^{k-1} - V^k) + dt (I_stim - I_ion)),  g2 = dt (V^k + theta (V^k - V^{k-1})),
+//   x0 = 2 V^k - V^{k-1}  (so that r0 = b - A x0 = M g1 - K g2).
+template <typename T>
 struct IonicArgs {
   int64_t n;
-  const double* V;        // V^k
-  const double* Vp;       // V^{k-1}
-  double* h;              // gate (in place)
-  double* g1;             // chi (Cm (V^{k-1} - V^k) + dt (I_stim - I_ion))
-  double* g2;             // dt (V^k + theta (V^k - V^{k-1}))
-  double* x0;             // 2 V^k - V^{k-1}: PCG initial guess, written into the V^{k+1} buffer
+  const T* V;             // V^k
+  const T* Vp;            // V^{k-1}
+  T* state;               // [n_states][n] (in place)
+  T* g1;
+  T* g2;
+  T* x0;                  // written into the V^{k+1} buffer
   const int32_t* stim_off;
   const int32_t* stim_ids;
   const StimDev* stims;
   long long k;
   double chi, cm, dt, theta;
   MSConst ms;
+  int cell;               // TP06 cell type
   GridBar* bar;           // zeroed here for the PCG launch that follows on the stream
 };
 
+template <typename T>
 struct PcgArgs {
   int64_t n;
   const int32_t* slice_ptr;
   const int32_t* col;
-  const double* vM;
-  const double* vK;
-  const double* vA;
-  const double* dinv;
+  const T* vM;
+  const T* vK;
+  const T* vA;
+  const T* dinv;
   const int32_t* blk_slice;   // gridDim.x + 1 slice boundaries
-  const double* g1;
-  const double* g2;
-  double* x;                  // in: x0, out: V^{k+1}
-  const double* Vcur;         // V^k (activation capture)
-  double* r;
-  double* z;
-  double* p;
-  double* q;
+  const T* g1;
+  const T* g2;
+  T* x;                       // in: x0, out: V^{k+1}
+  const T* Vcur;              // V^k (activation capture)
+  T* r;
+  T* z;
+  T* p;
+  T* q;
   double* act;
   double* partA;              // gridDim.x
   double* partB;              // 2*gridDim.x
@@ -132,30 +143,34 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, unsign
   return s_ok != 0;
 }
 
-// Fixed-order sums: lane 0 of a warp gets the shfl_down tree sum; warp sums are added in warp
-// order.  The result is a pure function of the inputs' placement, so runs are bitwise equal.
+// Fixed-order sums.  warp_sum: lane 0 gets the shfl_down tree sum.
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <int NW>
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* sm) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  a = warp_sum(a);
-  b = warp_sum(b);
+// Block sum of NV values per thread through shared memory: every thread stores its partials,
+// warp 0 adds them (lane l takes threads l, l+32, ...), then a shuffle tree; thread 0 holds the
+// totals.  Only warp 0 issues FP64 adds, which matters on a GPU whose FP64 rate is low.
+template <int THREADS, int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+  const int tid = threadIdx.x, lane = tid & 31;
   __syncthreads();
-  if (lane == 0) {
-    sm[warp] = a;
-    sm[NW + warp] = b;
-  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sm[k * THREADS + tid] = v[k];
   __syncthreads();
-  if (warp == 0) {
-    a = lane < NW ? sm[lane] : 0.0;
-    b = lane < NW ? sm[NW + lane] : 0.0;
-    a = warp_sum(a);
-    b = warp_sum(b);
+  if (tid < 32) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s0 = 0.0, s1 = 0.0;
+#pragma unroll 8
+      for (int j = 0; j < THREADS / 32; j += 2) {
+        s0 += sm[k * THREADS + j * 32 + lane];
+        s1 += sm[k * THREADS + (j + 1) * 32 + lane];
+      }
+      v[k] = warp_sum(s0 + s1);
+    }
   }
 }
 
@@ -195,103 +210,120 @@ __device__ __forceinline__ void grid_sum_warp0(const double* part, int stride, u
   b = two ? warp_sum(sb) : 0.0;
 }
 
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Row products over one SELL slice, lane = row.  Four entries are fetched (indices, values,
-// gathered vector entries) before their four FMAs, which keeps four gathers in flight per lane
-// while the FMAs still accumulate in entry order.
-__device__ __forceinline__ double sell_dot(const int32_t* __restrict__ col,
-                                          const double* __restrict__ val, int beg, int w,
-                                          const double* x) {
-  double acc0 = 0.0, acc1 = 0.0;   // even / odd entries: two independent FMA chains
+// gathered vector entries) before their FMAs; even and odd entries feed two FMA chains.
+template <typename T>
+__device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
+                                     int beg, int w, const T* x) {
+  T acc0 = T(0), acc1 = T(0);
   int j = 0;
   for (; j + 4 <= w; j += 4) {
     const int e = beg + 32 * j;
     const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32), c2 = __ldg(col + e + 64),
               c3 = __ldg(col + e + 96);
-    const double v0 = __ldg(val + e), v1 = __ldg(val + e + 32), v2 = __ldg(val + e + 64),
-                 v3 = __ldg(val + e + 96);
-    const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
-    acc0 = fma(v0, x0, acc0);
-    acc1 = fma(v1, x1, acc1);
-    acc0 = fma(v2, x2, acc0);
-    acc1 = fma(v3, x3, acc1);
+    const T v0 = __ldg(val + e), v1 = __ldg(val + e + 32), v2 = __ldg(val + e + 64),
+            v3 = __ldg(val + e + 96);
+    const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    acc0 = fmaT(v0, x0, acc0);
+    acc1 = fmaT(v1, x1, acc1);
+    acc0 = fmaT(v2, x2, acc0);
+    acc1 = fmaT(v3, x3, acc1);
   }
   for (; j < w; ++j) {
     const int e = beg + 32 * j;
-    const double v = __ldg(val + e), xv = x[__ldg(col + e)];
+    const T v = __ldg(val + e), xv = x[__ldg(col + e)];
     if (j & 1)
-      acc1 = fma(v, xv, acc1);
+      acc1 = fmaT(v, xv, acc1);
     else
-      acc0 = fma(v, xv, acc0);
+      acc0 = fmaT(v, xv, acc0);
   }
   return acc0 + acc1;
 }
 
 // Two value streams over the same pattern: am = sum M_ij g1_j, ak = sum K_ij g2_j.
-__device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col,
-                                          const double* __restrict__ vm,
-                                          const double* __restrict__ vk, int beg, int w,
-                                          const double* __restrict__ g1,
-                                          const double* __restrict__ g2, double& am,
-                                          double& ak) {
-  am = 0.0;
-  ak = 0.0;
+template <typename T>
+__device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const T* __restrict__ vm,
+                                          const T* __restrict__ vk, int beg, int w,
+                                          const T* __restrict__ g1, const T* __restrict__ g2,
+                                          T& am, T& ak) {
+  am = T(0);
+  ak = T(0);
   int j = 0;
   for (; j + 2 <= w; j += 2) {
     const int e = beg + 32 * j;
     const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32);
-    const double m0 = __ldg(vm + e), m1 = __ldg(vm + e + 32);
-    const double k0 = __ldg(vk + e), k1 = __ldg(vk + e + 32);
-    const double a0 = __ldg(g1 + c0), a1 = __ldg(g1 + c1);
-    const double b0 = __ldg(g2 + c0), b1 = __ldg(g2 + c1);
-    am = fma(m0, a0, am);
-    ak = fma(k0, b0, ak);
-    am = fma(m1, a1, am);
-    ak = fma(k1, b1, ak);
+    const T m0 = __ldg(vm + e), m1 = __ldg(vm + e + 32);
+    const T k0 = __ldg(vk + e), k1 = __ldg(vk + e + 32);
+    const T a0 = __ldg(g1 + c0), a1 = __ldg(g1 + c1);
+    const T b0 = __ldg(g2 + c0), b1 = __ldg(g2 + c1);
+    am = fmaT(m0, a0, am);
+    ak = fmaT(k0, b0, ak);
+    am = fmaT(m1, a1, am);
+    ak = fmaT(k1, b1, ak);
   }
   for (; j < w; ++j) {
     const int e = beg + 32 * j;
     const int c = __ldg(col + e);
-    am = fma(__ldg(vm + e), __ldg(g1 + c), am);
-    ak = fma(__ldg(vk + e), __ldg(g2 + c), ak);
+    am = fmaT(__ldg(vm + e), __ldg(g1 + c), am);
+    ak = fmaT(__ldg(vk + e), __ldg(g2 + c), ak);
   }
 }
 
-// (a1) Ionic update, Mitchell-Schaeffer with a Rush-Larsen gate, plus the per-node vectors of
-// the right-hand side and the extrapolated initial guess.
-__global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs a) {
+// Stimulus current of node i at step k (sum over the stimuli that list the node, in order).
+__device__ __forceinline__ double stimulus_at(const int32_t* off, const int32_t* ids,
+                                              const StimDev* stims, int64_t i, long long k) {
+  double is = 0.0;
+  for (int e = off[i]; e < off[i + 1]; ++e) {
+    const StimDev s = stims[ids[e]];
+    if (k >= s.k0 && k < s.k0 + s.nk) is += s.amp;
+  }
+  return is;
+}
+
+// Right-hand-side node vectors and initial guess from V^k, V^{k-1}, I_ion and I_stim.
+template <typename T>
+__device__ __forceinline__ void rhs_epilogue(const IonicArgs<T>& a, int64_t i, T V, T Vp, T iion,
+                                             T is) {
+  const T chi = T(a.chi), cm = T(a.cm), dt = T(a.dt), th = T(a.theta);
+  a.g1[i] = chi * (cm * (Vp - V) + dt * (is - iion));
+  a.g2[i] = dt * (V + th * (V - Vp));
+  a.x0[i] = T(2) * V - Vp;
+}
+
+// (a1) Ionic update, Mitchell-Schaeffer with a Rush-Larsen gate (state[0] = h).
+template <typename T>
+__global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs<T> a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) a.bar->count = 0u;
   if (i >= a.n) return;
-  const double V = a.V[i], Vp = a.Vp[i];
+  const T V = a.V[i], Vp = a.Vp[i];
   const MSConst& c = a.ms;
-  const double v = (V - c.vmin) * c.inv_range;
-  const bool closing = v >= c.vgate;
-  const double hinf = closing ? 0.0 : 1.0;
-  const double h = hinf + (a.h[i] - hinf) * (closing ? c.dec_close : c.dec_open);
-  a.h[i] = h;
-  const double jin = h * v * v * (1.0 - v) * c.inv_tau_in;
-  const double jout = -v * c.inv_tau_out;
-  const double iion = -a.cm * c.range * (jin + jout);
-  double is = 0.0;
-  for (int e = a.stim_off[i]; e < a.stim_off[i + 1]; ++e) {
-    const StimDev s = a.stims[a.stim_ids[e]];
-    if (a.k >= s.k0 && a.k < s.k0 + s.nk) is += s.amp;
-  }
-  a.g1[i] = a.chi * (a.cm * (Vp - V) + a.dt * (is - iion));
-  a.g2[i] = a.dt * (V + a.theta * (V - Vp));
-  a.x0[i] = 2.0 * V - Vp;
+  const T v = (V - T(c.vmin)) * T(c.inv_range);
+  const bool closing = v >= T(c.vgate);
+  const T hinf = closing ? T(0) : T(1);
+  const T h = hinf + (a.state[i] - hinf) * (closing ? T(c.dec_close) : T(c.dec_open));
+  a.state[i] = h;
+  const T jin = h * v * v * (T(1) - v) * T(c.inv_tau_in);
+  const T jout = -v * T(c.inv_tau_out);
+  const T iion = -T(a.cm) * T(c.range) * (jin + jout);
+  const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, a.k));
+  rhs_epilogue(a, i, V, Vp, iion, is);
 }
 
 // (a2)-(a5) in one cooperative launch: r0 = b - A x0 from the two value streams of M and K,
 // the Jacobi-PCG loop of Algorithm 1 with the convergence decision taken identically by every
 // block, and the activation-time capture.  Each block owns a contiguous range of slices (and
 // so of rows); SpMV phases map one warp to one slice, vector phases stride threads over the
-// block's rows.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs a) {
+// block's rows.  Scalar FP64 work (sqrt, divisions, the stopping test) runs on thread 0 only:
+// B300 issues FP64 at a small fraction of its FP32 rate.
+template <int THREADS, typename T>
+__global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   constexpr int NW = THREADS / 32;
-  __shared__ double s_red[2 * NW];
-  __shared__ double s_sc[4];   // scalars computed once per block by thread 0, then broadcast
+  __shared__ double s_red[2 * THREADS];
+  __shared__ double s_sc[4];   // scalars computed by thread 0, then broadcast
   __shared__ int s_flag;       // 0 = iterate, 1 = converged, 2 = non-finite
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned nb = gridDim.x, b = blockIdx.x;
@@ -299,33 +331,34 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs a) {
   const int64_t r0 = (int64_t)s0 * 32;
   const int64_t r1 = min((int64_t)s1 * 32, a.n);
   unsigned epoch = 0;
-  // Scalar FP64 work (sqrt, divisions, the stopping test) runs on thread 0 only: B300 issues
-  // FP64 at a small fraction of its FP32 rate, so replicating it over every thread is costly.
   double rho = 0.0, z0n = 0.0, zn = 0.0;   // meaningful in thread 0
   int it = 0;
 
   // r0 = chi M (w - Cm x0) - dt K ((1-theta) V + theta x0) = M g1 - K g2
-  double rho_l = 0.0, zz_l = 0.0;
+  T rho_t = T(0), zz_t = T(0);
   for (int s = s0 + warp; s < s1; s += NW) {
     const int beg = a.slice_ptr[s] + lane;
     const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
-    double am, ak;
+    T am, ak;
     sell_dot2(a.col, a.vM, a.vK, beg, w, a.g1, a.g2, am, ak);
     const int64_t row = (int64_t)s * 32 + lane;
     if (row < a.n) {
-      const double rr = am - ak;
-      const double zv = __ldg(&a.dinv[row]) * rr;
+      const T rr = am - ak;
+      const T zv = __ldg(&a.dinv[row]) * rr;
       a.r[row] = rr;
       a.z[row] = zv;
       a.p[row] = zv;
-      rho_l = fma(rr, zv, rho_l);
-      zz_l = fma(zv, zv, zz_l);
+      rho_t = fmaT(rr, zv, rho_t);
+      zz_t = fmaT(zv, zv, zz_t);
     }
   }
-  block_sum2<NW>(rho_l, zz_l, s_red);
-  if (tid == 0) {
-    a.partB[2 * b] = rho_l;
-    a.partB[2 * b + 1] = zz_l;
+  {
+    double v2[2] = {double(rho_t), double(zz_t)};
+    block_sum<THREADS, 2>(v2, s_red);
+    if (tid == 0) {
+      a.partB[2 * b] = v2[0];
+      a.partB[2 * b + 1] = v2[1];
+    }
   }
   if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
   if (warp == 0) {
@@ -342,19 +375,22 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs a) {
   int flag = s_flag;
   while (flag == 0 && it < a.max_iter) {
     // q = A p, p^T q
-    double pq_l = 0.0, dummy = 0.0;
+    T pq_t = T(0);
     for (int s = s0 + warp; s < s1; s += NW) {
       const int beg = a.slice_ptr[s] + lane;
       const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
-      const double acc = sell_dot(a.col, a.vA, beg, w, a.p);
+      const T acc = sell_dot(a.col, a.vA, beg, w, a.p);
       const int64_t row = (int64_t)s * 32 + lane;
       if (row < a.n) {
         a.q[row] = acc;
-        pq_l = fma(a.p[row], acc, pq_l);
+        pq_t = fmaT(a.p[row], acc, pq_t);
       }
     }
-    block_sum2<NW>(pq_l, dummy, s_red);
-    if (tid == 0) a.partA[b] = pq_l;
+    {
+      double v1[1] = {double(pq_t)};
+      block_sum<THREADS, 1>(v1, s_red);
+      if (tid == 0) a.partA[b] = v1[0];
+    }
     if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
     if (warp == 0) {
       double pq, unused;
@@ -365,15 +401,15 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs a) {
       }
     }
     __syncthreads();
-    const double alpha = s_sc[0];
+    const T alpha = T(s_sc[0]);
     // x += alpha p, r -= alpha q, z = D^-1 r, rho' = r^T z, ||z||^2
-    rho_l = 0.0;
-    zz_l = 0.0;
+    rho_t = T(0);
+    zz_t = T(0);
     for (int64_t i = r0 + tid; i < r1; i += 2 * THREADS) {
       const int64_t i2 = i + THREADS;
       const bool two = i2 < r1;
-      const double p0 = a.p[i], q0 = a.q[i], x0 = a.x[i], rr0 = a.r[i], d0 = __ldg(&a.dinv[i]);
-      double p1 = 0.0, q1 = 0.0, x1 = 0.0, rr1 = 0.0, d1 = 0.0;
+      const T p0 = a.p[i], q0 = a.q[i], x0 = a.x[i], rr0 = a.r[i], d0 = __ldg(&a.dinv[i]);
+      T p1 = T(0), q1 = T(0), x1 = T(0), rr1 = T(0), d1 = T(0);
       if (two) {
         p1 = a.p[i2];
         q1 = a.q[i2];
@@ -381,27 +417,30 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs a) {
         rr1 = a.r[i2];
         d1 = __ldg(&a.dinv[i2]);
       }
-      a.x[i] = fma(alpha, p0, x0);
-      const double ri = fma(-alpha, q0, rr0);
+      a.x[i] = fmaT(alpha, p0, x0);
+      const T ri = fmaT(-alpha, q0, rr0);
       a.r[i] = ri;
-      const double zi = d0 * ri;
+      const T zi = d0 * ri;
       a.z[i] = zi;
-      rho_l = fma(ri, zi, rho_l);
-      zz_l = fma(zi, zi, zz_l);
+      rho_t = fmaT(ri, zi, rho_t);
+      zz_t = fmaT(zi, zi, zz_t);
       if (two) {
-        a.x[i2] = fma(alpha, p1, x1);
-        const double rj = fma(-alpha, q1, rr1);
+        a.x[i2] = fmaT(alpha, p1, x1);
+        const T rj = fmaT(-alpha, q1, rr1);
         a.r[i2] = rj;
-        const double zj = d1 * rj;
+        const T zj = d1 * rj;
         a.z[i2] = zj;
-        rho_l = fma(rj, zj, rho_l);
-        zz_l = fma(zj, zj, zz_l);
+        rho_t = fmaT(rj, zj, rho_t);
+        zz_t = fmaT(zj, zj, zz_t);
       }
     }
-    block_sum2<NW>(rho_l, zz_l, s_red);
-    if (tid == 0) {
-      a.partB[2 * b] = rho_l;
-      a.partB[2 * b + 1] = zz_l;
+    {
+      double v2[2] = {double(rho_t), double(zz_t)};
+      block_sum<THREADS, 2>(v2, s_red);
+      if (tid == 0) {
+        a.partB[2 * b] = v2[0];
+        a.partB[2 * b + 1] = v2[1];
+      }
     }
     if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
     ++it;
@@ -422,22 +461,22 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs a) {
     __syncthreads();
     flag = s_flag;
     if (flag != 0) break;
-    const double beta = s_sc[2];
+    const T beta = T(s_sc[2]);
     for (int64_t i = r0 + tid; i < r1; i += 2 * THREADS) {
       const int64_t i2 = i + THREADS;
-      const double p0 = a.p[i], z0 = a.z[i];
+      const T p0 = a.p[i], z0 = a.z[i];
       if (i2 < r1) {
-        const double p1 = a.p[i2], z1 = a.z[i2];
-        a.p[i2] = fma(beta, p1, z1);
+        const T p1 = a.p[i2], z1 = a.z[i2];
+        a.p[i2] = fmaT(beta, p1, z1);
       }
-      a.p[i] = fma(beta, p0, z0);
+      a.p[i] = fmaT(beta, p0, z0);
     }
     if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
   }
   // activation capture: first upward crossing of thr, interpolated inside the step
   for (int64_t i = r0 + tid; i < r1; i += THREADS) {
     if (a.act[i] < 0.0) {
-      const double vo = a.Vcur[i], vn = a.x[i];
+      const double vo = double(a.Vcur[i]), vn = double(a.x[i]);
       if (vo < a.thr && vn >= a.thr) a.act[i] = a.t_k + a.dt * (a.thr - vo) / (vn - vo);
     }
   }
@@ -455,19 +494,20 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs a) {
 }
 
 // Standalone y = Op x (the SpMV of Algorithm 1) for operator checks and bandwidth runs.
+template <typename T>
 __global__ void __launch_bounds__(256) spmv_sell_kernel(int64_t n, int64_t nslices,
                                                         const int32_t* __restrict__ slice_ptr,
                                                         const int32_t* __restrict__ col,
-                                                        const double* __restrict__ val,
-                                                        const double* __restrict__ x,
-                                                        double* __restrict__ y) {
+                                                        const T* __restrict__ val,
+                                                        const T* __restrict__ x,
+                                                        T* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = gw; s < nslices; s += nw) {
     const int beg = slice_ptr[s] + lane;
     const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
-    const double acc = sell_dot(col, val, beg, w, x);
+    const T acc = sell_dot(col, val, beg, w, x);
     const int64_t row = s * 32 + lane;
     if (row < n) y[row] = acc;
   }

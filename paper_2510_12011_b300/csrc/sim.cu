@@ -3,12 +3,14 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
 
+#include "ionic_tp06.cuh"
 #include "kernels.cuh"
 #include "tc_internal.h"
 
@@ -19,8 +21,8 @@ namespace {
 constexpr int kIonicThreads = 256;
 
 // Launch shape of the PCG kernel: 512 or 1024 threads per block, blocks per SM, and the SELL
-// sorting window; defaults can be overridden through TC_PCG_THREADS, TC_PCG_BLOCKS_PER_SM and
-// TC_SELL_SIGMA (used by the launch-shape sweep).
+// sorting window; TC_PCG_THREADS, TC_PCG_BLOCKS_PER_SM and TC_SELL_SIGMA override the defaults
+// (used by the launch-shape sweep).
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   return v && *v ? std::atoi(v) : dflt;
@@ -38,15 +40,17 @@ struct tc_sim {
   cudaStream_t stream = nullptr;
   int64_t n = 0, nnz = 0, nslices = 0, padded = 0;
   int precision = TC_FP64;
+  size_t esz = 8;                    // bytes per matrix value / node-vector entry
   std::vector<int32_t> perm, inv;   // perm[new] = old
   int num_sms = 0, blocks_per_sm = 1, nblocks = 0, pcg_threads = 1024, sell_sigma = 1024;
-  // device arrays
+  // device arrays (element type double for TC_FP64, float for TC_FP32)
   int32_t *slice_ptr = nullptr, *col = nullptr, *blk_slice = nullptr;
-  double *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
-  double* V[3] = {nullptr, nullptr, nullptr};
+  void *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
+  void* V[3] = {nullptr, nullptr, nullptr};
   int iv = 0;   // V[iv] = V^k, V[(iv+2)%3] = V^{k-1}, V[(iv+1)%3] = V^{k+1}
-  double *state = nullptr, *g1 = nullptr, *g2 = nullptr;
-  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *act = nullptr;
+  void *state = nullptr, *g1 = nullptr, *g2 = nullptr;
+  void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double* act = nullptr;
   double *partA = nullptr, *partB = nullptr;
   GridBar* bar = nullptr;
   int* err = nullptr;
@@ -55,7 +59,6 @@ struct tc_sim {
   StimDev* stims = nullptr;
   std::vector<std::vector<int32_t>> stim_nodes;   // per stimulus, internal indices
   std::vector<StimDev> stim_host;
-  bool stim_dirty = false;
   // parameters
   double chi = 0, cm = 0, theta = 0, dt = 0;
   double atol = 0.0, rtol = 1e-10;
@@ -65,6 +68,7 @@ struct tc_sim {
   int model = -1;
   int n_states = 0;
   double ms[7] = {0};
+  int cell = 0;
   long long k = 0;
   long long wait_limit = 1ll << 26;
   // profiling
@@ -73,6 +77,7 @@ struct tc_sim {
   std::vector<cudaEvent_t> evpool;
   std::vector<Dev> allocs;
   double* pinned = nullptr;   // n doubles of page-locked staging for host reads/writes
+  void* pinned_t = nullptr;   // n elements of the device type, page-locked
 };
 
 namespace {
@@ -88,24 +93,66 @@ tc_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #x);  \
   } while (0)
 
-template <class T>
-tc_status dalloc(tc_sim* s, T** out, size_t count) {
-  void* p = nullptr;
-  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-  s->allocs.push_back({p, bytes});
-  *out = static_cast<T*>(p);
-  return TC_OK;
-}
-
 #define TRY(x)                      \
   do {                              \
     tc_status st_ = (x);            \
     if (st_ != TC_OK) return st_;   \
   } while (0)
 
+tc_status dalloc_bytes(tc_sim* s, void** out, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 8));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  s->allocs.push_back({p, bytes});
+  *out = p;
+  return TC_OK;
+}
+
+template <class T>
+tc_status dalloc(tc_sim* s, T** out, size_t count) {
+  void* p = nullptr;
+  TRY(dalloc_bytes(s, &p, count * sizeof(T)));
+  *out = static_cast<T*>(p);
+  return TC_OK;
+}
+
+void dfree(tc_sim* s, void* p) {
+  if (!p) return;
+  for (auto it = s->allocs.begin(); it != s->allocs.end(); ++it)
+    if (it->p == p) {
+      s->allocs.erase(it);
+      break;
+    }
+  cudaFree(p);
+}
+
 int64_t round_half_even(double x) { return (int64_t)std::nearbyint(x); }
+
+// Host doubles (internal order) <-> device arrays of the simulation's type.
+tc_status upload_vec(tc_sim* s, void* dst, const double* src_internal, int64_t count) {
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (s->precision == TC_FP64) {
+    std::memcpy(s->pinned_t, src_internal, count * sizeof(double));
+  } else {
+    float* f = static_cast<float*>(s->pinned_t);
+    for (int64_t i = 0; i < count; ++i) f[i] = (float)src_internal[i];
+  }
+  CUDA_TRY(cudaMemcpyAsync(dst, s->pinned_t, count * s->esz, cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TC_OK;
+}
+
+tc_status download_vec(const tc_sim* s, const void* src, double* dst_internal, int64_t count) {
+  CUDA_TRY(cudaMemcpyAsync(s->pinned_t, src, count * s->esz, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (s->precision == TC_FP64) {
+    std::memcpy(dst_internal, s->pinned_t, count * sizeof(double));
+  } else {
+    const float* f = static_cast<const float*>(s->pinned_t);
+    for (int64_t i = 0; i < count; ++i) dst_internal[i] = (double)f[i];
+  }
+  return TC_OK;
+}
 
 tc_status upload_stimuli(tc_sim* s) {
   std::vector<std::vector<int32_t>> per_node(s->n);
@@ -116,10 +163,12 @@ tc_status upload_stimuli(tc_sim* s) {
     off[i + 1] = off[i] + (int32_t)per_node[i].size();
     ids.insert(ids.end(), per_node[i].begin(), per_node[i].end());
   }
-  if (s->stim_ids) cudaFree(s->stim_ids), s->stim_ids = nullptr;
-  if (s->stims) cudaFree(s->stims), s->stims = nullptr;
-  CUDA_TRY(cudaMalloc(&s->stim_ids, std::max<size_t>(ids.size(), 1) * sizeof(int32_t)));
-  CUDA_TRY(cudaMalloc(&s->stims, std::max<size_t>(s->stim_host.size(), 1) * sizeof(StimDev)));
+  dfree(s, s->stim_ids);
+  dfree(s, s->stims);
+  s->stim_ids = nullptr;
+  s->stims = nullptr;
+  TRY(dalloc(s, &s->stim_ids, std::max<size_t>(ids.size(), 1)));
+  TRY(dalloc(s, &s->stims, std::max<size_t>(s->stim_host.size(), 1)));
   CUDA_TRY(cudaMemcpyAsync(s->stim_off, off.data(), off.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s->stream));
   if (!ids.empty())
@@ -129,40 +178,43 @@ tc_status upload_stimuli(tc_sim* s) {
     CUDA_TRY(cudaMemcpyAsync(s->stims, s->stim_host.data(), s->stim_host.size() * sizeof(StimDev),
                              cudaMemcpyHostToDevice, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
-  s->stim_dirty = false;
   return TC_OK;
 }
 
+template <typename T>
 const void* pcg_kernel_ptr(int threads) {
-  return threads == 1024 ? (const void*)pcg_step_kernel<1024> : (const void*)pcg_step_kernel<512>;
+  return threads == 1024 ? (const void*)pcg_step_kernel<1024, T>
+                         : (const void*)pcg_step_kernel<512, T>;
+}
+
+const void* pcg_kernel(const tc_sim* s) {
+  return s->precision == TC_FP64 ? pcg_kernel_ptr<double>(s->pcg_threads)
+                                 : pcg_kernel_ptr<float>(s->pcg_threads);
 }
 
 tc_status set_partition(tc_sim* s) {
   int bps = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pcg_kernel_ptr(s->pcg_threads),
-                                                         s->pcg_threads, 0));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pcg_kernel(s), s->pcg_threads, 0));
   if (bps < 1) return fail(TC_ERR_CUDA, "PCG kernel cannot be resident on an SM");
   const int per_sm = std::min(bps, std::max(1, s->blocks_per_sm));
   const int64_t max_blocks = (int64_t)per_sm * s->num_sms;
-  const int kWarps = s->pcg_threads / 32;
-  const int64_t want = (s->nslices + kWarps - 1) / kWarps;   // at least one slice per warp
+  const int warps = s->pcg_threads / 32;
+  const int64_t want = (s->nslices + warps - 1) / warps;   // at least one slice per warp
   s->nblocks = (int)std::max<int64_t>(1, std::min(max_blocks, want));
   std::vector<int32_t> bs(s->nblocks + 1);
   for (int b = 0; b <= s->nblocks; ++b) bs[b] = (int32_t)((s->nslices * (int64_t)b) / s->nblocks);
-  if (s->blk_slice) cudaFree(s->blk_slice), s->blk_slice = nullptr;
-  CUDA_TRY(cudaMalloc(&s->blk_slice, bs.size() * sizeof(int32_t)));
+  dfree(s, s->blk_slice);
+  dfree(s, s->partA);
+  dfree(s, s->partB);
+  TRY(dalloc(s, &s->blk_slice, bs.size()));
+  TRY(dalloc(s, &s->partA, s->nblocks));
+  TRY(dalloc(s, &s->partB, 2 * s->nblocks));
   CUDA_TRY(cudaMemcpy(s->blk_slice, bs.data(), bs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  if (s->partA) cudaFree(s->partA), s->partA = nullptr;
-  if (s->partB) cudaFree(s->partB), s->partB = nullptr;
-  CUDA_TRY(cudaMalloc(&s->partA, s->nblocks * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&s->partB, 2 * s->nblocks * sizeof(double)));
   return TC_OK;
 }
 
-tc_status to_internal(const tc_sim* s, const double* host, std::vector<double>& out) {
-  out.resize(s->n);
+void to_internal(const tc_sim* s, const double* host, double* out) {
   for (int64_t i = 0; i < s->n; ++i) out[i] = host[s->perm[i]];
-  return TC_OK;
 }
 
 cudaEvent_t pooled_event(tc_sim* s, size_t idx) {
@@ -172,6 +224,114 @@ cudaEvent_t pooled_event(tc_sim* s, size_t idx) {
     s->evpool.push_back(e);
   }
   return s->evpool[idx];
+}
+
+template <typename T>
+tc_status upload_matrices(tc_sim* s, const Sell& sell, const std::vector<double>& mv,
+                          const std::vector<double>& kv, const std::vector<double>& av,
+                          const std::vector<double>& dinv) {
+  std::vector<T> hM(sell.padded), hK(sell.padded), hA(sell.padded), hd(s->n);
+  for (int64_t e = 0; e < sell.padded; ++e) {
+    const int64_t q = sell.src[e];
+    hM[e] = q >= 0 ? (T)mv[q] : T(0);
+    hK[e] = q >= 0 ? (T)kv[q] : T(0);
+    hA[e] = q >= 0 ? (T)av[q] : T(0);
+  }
+  for (int64_t i = 0; i < s->n; ++i) hd[i] = (T)dinv[i];
+  CUDA_TRY(cudaMemcpy(s->vM, hM.data(), sell.padded * sizeof(T), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->vK, hK.data(), sell.padded * sizeof(T), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->vA, hA.data(), sell.padded * sizeof(T), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->dinv, hd.data(), s->n * sizeof(T), cudaMemcpyHostToDevice));
+  return TC_OK;
+}
+
+// Launch one time step: ionic kernel, then the cooperative PCG kernel.
+template <typename T>
+tc_status launch_step(tc_sim* s, size_t& ev, std::vector<size_t>& marks) {
+  T* Vc = static_cast<T*>(s->V[s->iv]);
+  T* Vp = static_cast<T*>(s->V[(s->iv + 2) % 3]);
+  T* Vn = static_cast<T*>(s->V[(s->iv + 1) % 3]);
+  IonicArgs<T> ia;
+  ia.n = s->n;
+  ia.V = Vc;
+  ia.Vp = Vp;
+  ia.state = static_cast<T*>(s->state);
+  ia.g1 = static_cast<T*>(s->g1);
+  ia.g2 = static_cast<T*>(s->g2);
+  ia.x0 = Vn;
+  ia.stim_off = s->stim_off;
+  ia.stim_ids = s->stim_ids;
+  ia.stims = s->stims;
+  ia.k = s->k;
+  ia.chi = s->chi;
+  ia.cm = s->cm;
+  ia.dt = s->dt;
+  ia.theta = s->theta;
+  const double range = s->ms[6] - s->ms[5];
+  ia.ms.vmin = s->ms[5];
+  ia.ms.inv_range = range != 0.0 ? 1.0 / range : 0.0;
+  ia.ms.range = range;
+  ia.ms.vgate = s->ms[4];
+  ia.ms.inv_tau_in = s->ms[0] != 0.0 ? 1.0 / s->ms[0] : 0.0;
+  ia.ms.inv_tau_out = s->ms[1] != 0.0 ? 1.0 / s->ms[1] : 0.0;
+  ia.ms.dec_open = s->ms[2] != 0.0 ? std::exp(-s->dt / s->ms[2]) : 0.0;
+  ia.ms.dec_close = s->ms[3] != 0.0 ? std::exp(-s->dt / s->ms[3]) : 0.0;
+  ia.cell = s->cell;
+  ia.bar = s->bar;
+  if (s->prof) {
+    cudaEvent_t e = pooled_event(s, ev);
+    if (!e) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
+    CUDA_TRY(cudaEventRecord(e, s->stream));
+    marks.push_back(ev++);
+  }
+  const int ion_blocks = (int)((s->n + kIonicThreads - 1) / kIonicThreads);
+  if (s->model == TC_MODEL_MS)
+    ionic_ms_kernel<T><<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
+  else
+    ionic_tp06_kernel<T><<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
+  CUDA_TRY(cudaGetLastError());
+  PcgArgs<T> pa;
+  pa.n = s->n;
+  pa.slice_ptr = s->slice_ptr;
+  pa.col = s->col;
+  pa.vM = static_cast<const T*>(s->vM);
+  pa.vK = static_cast<const T*>(s->vK);
+  pa.vA = static_cast<const T*>(s->vA);
+  pa.dinv = static_cast<const T*>(s->dinv);
+  pa.blk_slice = s->blk_slice;
+  pa.g1 = static_cast<const T*>(s->g1);
+  pa.g2 = static_cast<const T*>(s->g2);
+  pa.x = Vn;
+  pa.Vcur = Vc;
+  pa.r = static_cast<T*>(s->r);
+  pa.z = static_cast<T*>(s->z);
+  pa.p = static_cast<T*>(s->p);
+  pa.q = static_cast<T*>(s->q);
+  pa.act = s->act;
+  pa.partA = s->partA;
+  pa.partB = s->partB;
+  pa.bar = s->bar;
+  pa.err = s->err;
+  pa.stats = s->stats;
+  pa.atol = s->atol;
+  pa.rtol = s->rtol;
+  pa.max_iter = s->max_iter;
+  pa.wait_limit = s->wait_limit;
+  pa.t_k = (double)s->k * s->dt;
+  pa.dt = s->dt;
+  pa.thr = s->thr;
+  if (s->prof) {
+    CUDA_TRY(cudaEventRecord(pooled_event(s, ev), s->stream));
+    ev++;
+  }
+  void* args[] = {&pa};
+  CUDA_TRY(cudaLaunchCooperativeKernel(pcg_kernel(s), s->nblocks, s->pcg_threads, args, 0,
+                                       s->stream));
+  if (s->prof) {
+    CUDA_TRY(cudaEventRecord(pooled_event(s, ev), s->stream));
+    ev++;
+  }
+  return TC_OK;
 }
 
 }  // namespace
@@ -188,8 +348,8 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   if (!(chi > 0) || !(cm > 0) || !(dt > 0) || !(theta >= 0.0 && theta <= 1.0) ||
       !std::isfinite(chi) || !std::isfinite(cm) || !std::isfinite(dt))
     return fail(TC_ERR_ARG, "need chi > 0, cm > 0, dt > 0 and 0 <= theta <= 1");
-  if (precision != TC_FP64)
-    return fail(TC_ERR_ARG, "precision " + std::to_string(precision) + " is not available");
+  if (precision != TC_FP64 && precision != TC_FP32)
+    return fail(TC_ERR_ARG, "precision must be TC_FP64 or TC_FP32, got " + std::to_string(precision));
   std::vector<double> mv, kv;
   try {
     TRY(assemble_mk(*mesh, sigma_l, sigma_t, n_regions, mv, kv));
@@ -208,6 +368,7 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   s->theta = theta;
   s->dt = dt;
   s->precision = precision;
+  s->esz = precision == TC_FP64 ? sizeof(double) : sizeof(float);
   s->n = mesh->n;
   const Csr& pat = mesh->pattern;
   s->nnz = pat.row_ptr[mesh->n];
@@ -215,39 +376,34 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   s->blocks_per_sm = std::max(1, env_int("TC_PCG_BLOCKS_PER_SM", s->pcg_threads == 1024 ? 1 : 2));
   s->sell_sigma = std::max(1, env_int("TC_SELL_SIGMA", 1024));
   Sell sell;
+  std::vector<double> av, hdinv;
   try {
     node_ordering(pat, s->sell_sigma, s->perm);
     tc_status st = build_sell(pat, s->perm, sell);
     if (st != TC_OK) return bail(st);
+    s->inv.resize(s->n);
+    for (int64_t i = 0; i < s->n; ++i) s->inv[s->perm[i]] = (int32_t)i;
+    // A = chi Cm M + theta dt K, entry by entry (Eq. 3): two products, then the sum
+    const double c1 = chi * cm, c2 = theta * dt;
+    av.resize(s->nnz);
+    for (int64_t q = 0; q < s->nnz; ++q) {
+      volatile double t1 = c1 * mv[q];
+      volatile double t2 = c2 * kv[q];
+      av[q] = t1 + t2;
+    }
+    hdinv.resize(s->n);
+    for (int64_t i = 0; i < s->n; ++i) {
+      const int32_t o = s->perm[i];
+      const int32_t* cb = &pat.col[pat.row_ptr[o]];
+      const int64_t len = pat.row_ptr[o + 1] - pat.row_ptr[o];
+      const int64_t d = std::lower_bound(cb, cb + len, o) - cb;
+      hdinv[i] = 1.0 / av[pat.row_ptr[o] + d];
+    }
   } catch (const std::bad_alloc&) {
     return bail(fail(TC_ERR_NOMEM, "out of host memory"));
   }
-  s->inv.resize(s->n);
-  for (int64_t i = 0; i < s->n; ++i) s->inv[s->perm[i]] = (int32_t)i;
   s->nslices = sell.nslices;
   s->padded = sell.padded;
-  // A = chi Cm M + theta dt K, entry by entry (Eq. 3)
-  const double c1 = chi * cm, c2 = theta * dt;
-  std::vector<double> av(s->nnz);
-  for (int64_t q = 0; q < s->nnz; ++q) {
-    volatile double t1 = c1 * mv[q];   // two roundings and an add, as the definition reads
-    volatile double t2 = c2 * kv[q];
-    av[q] = t1 + t2;
-  }
-  std::vector<double> hM(sell.padded), hK(sell.padded), hA(sell.padded), hdinv(s->n);
-  for (int64_t e = 0; e < sell.padded; ++e) {
-    const int64_t q = sell.src[e];
-    hM[e] = q >= 0 ? mv[q] : 0.0;
-    hK[e] = q >= 0 ? kv[q] : 0.0;
-    hA[e] = q >= 0 ? av[q] : 0.0;
-  }
-  for (int64_t i = 0; i < s->n; ++i) {
-    const int32_t o = s->perm[i];
-    const int32_t* cb = &pat.col[pat.row_ptr[o]];
-    const int64_t len = pat.row_ptr[o + 1] - pat.row_ptr[o];
-    const int64_t d = std::lower_bound(cb, cb + len, o) - cb;
-    hdinv[i] = 1.0 / av[pat.row_ptr[o] + d];
-  }
   cudaError_t ce = cudaGetDevice(&s->device);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
   ce = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -257,42 +413,39 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   if (!coop) return bail(fail(TC_ERR_CUDA, "device does not support cooperative launches"));
   tc_status st = TC_OK;
   const int64_t n = s->n;
-#define ALLOC(ptr, cnt)                        \
-  do {                                         \
-    st = dalloc(s, &(ptr), (size_t)(cnt));     \
-    if (st != TC_OK) return bail(st);          \
+  const size_t E = s->esz;
+#define ALLOCB(ptr, bytes)                                 \
+  do {                                                     \
+    st = dalloc_bytes(s, (void**)&(ptr), (size_t)(bytes)); \
+    if (st != TC_OK) return bail(st);                      \
   } while (0)
-  ALLOC(s->slice_ptr, s->nslices + 1);
-  ALLOC(s->col, sell.padded);
-  ALLOC(s->vM, sell.padded);
-  ALLOC(s->vK, sell.padded);
-  ALLOC(s->vA, sell.padded);
-  ALLOC(s->dinv, n);
-  for (int j = 0; j < 3; ++j) ALLOC(s->V[j], n);
-  ALLOC(s->g1, n);
-  ALLOC(s->g2, n);
-  ALLOC(s->r, n);
-  ALLOC(s->z, n);
-  ALLOC(s->p, n);
-  ALLOC(s->q, n);
-  ALLOC(s->act, n);
-  ALLOC(s->bar, 1);
-  ALLOC(s->err, 1);
-  ALLOC(s->stats, 1);
-  ALLOC(s->stim_off, n + 1);
-#undef ALLOC
-#define H2D(dst, src, cnt)                                                                     \
-  do {                                                                                         \
-    ce = cudaMemcpy(dst, src, (size_t)(cnt) * sizeof(*(src)), cudaMemcpyHostToDevice);         \
-    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpy"));                           \
-  } while (0)
-  H2D(s->slice_ptr, sell.slice_ptr.data(), s->nslices + 1);
-  H2D(s->col, sell.col.data(), sell.padded);
-  H2D(s->vM, hM.data(), sell.padded);
-  H2D(s->vK, hK.data(), sell.padded);
-  H2D(s->vA, hA.data(), sell.padded);
-  H2D(s->dinv, hdinv.data(), n);
-#undef H2D
+  ALLOCB(s->slice_ptr, (s->nslices + 1) * sizeof(int32_t));
+  ALLOCB(s->col, sell.padded * sizeof(int32_t));
+  ALLOCB(s->vM, sell.padded * E);
+  ALLOCB(s->vK, sell.padded * E);
+  ALLOCB(s->vA, sell.padded * E);
+  ALLOCB(s->dinv, n * E);
+  for (int j = 0; j < 3; ++j) ALLOCB(s->V[j], n * E);
+  ALLOCB(s->g1, n * E);
+  ALLOCB(s->g2, n * E);
+  ALLOCB(s->r, n * E);
+  ALLOCB(s->z, n * E);
+  ALLOCB(s->p, n * E);
+  ALLOCB(s->q, n * E);
+  ALLOCB(s->act, n * sizeof(double));
+  ALLOCB(s->bar, sizeof(GridBar));
+  ALLOCB(s->err, sizeof(int));
+  ALLOCB(s->stats, sizeof(DevStats));
+  ALLOCB(s->stim_off, (n + 1) * sizeof(int32_t));
+#undef ALLOCB
+  ce = cudaMemcpy(s->slice_ptr, sell.slice_ptr.data(), (s->nslices + 1) * sizeof(int32_t),
+                  cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpy(s->col, sell.col.data(), sell.padded * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpy"));
+  st = precision == TC_FP64 ? upload_matrices<double>(s, sell, mv, kv, av, hdinv)
+                            : upload_matrices<float>(s, sell, mv, kv, av, hdinv);
+  if (st != TC_OK) return bail(st);
   ce = cudaMemset(s->bar, 0, sizeof(GridBar));
   if (ce == cudaSuccess) ce = cudaMemset(s->err, 0, sizeof(int));
   if (ce == cudaSuccess) ce = cudaMemset(s->stats, 0, sizeof(DevStats));
@@ -300,6 +453,7 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   if (ce == cudaSuccess) ce = cudaMemset(s->act, 0, n * sizeof(double));
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
   ce = cudaMallocHost(&s->pinned, n * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMallocHost(&s->pinned_t, n * sizeof(double));
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMallocHost"));
   st = set_partition(s);
   if (st != TC_OK) return bail(st);
@@ -312,16 +466,11 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
 void tc_sim_destroy(tc_sim* s) {
   if (!s) return;
   cudaSetDevice(s->device);
-  if (s->stream || true) cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->stream);
   for (auto& d : s->allocs) cudaFree(d.p);
-  if (s->blk_slice) cudaFree(s->blk_slice);
-  if (s->partA) cudaFree(s->partA);
-  if (s->partB) cudaFree(s->partB);
-  if (s->stim_ids) cudaFree(s->stim_ids);
-  if (s->stims) cudaFree(s->stims);
-  if (s->state) cudaFree(s->state);
   for (cudaEvent_t e : s->evpool) cudaEventDestroy(e);
   if (s->pinned) cudaFreeHost(s->pinned);
+  if (s->pinned_t) cudaFreeHost(s->pinned_t);
   delete s;
 }
 
@@ -341,25 +490,48 @@ tc_status tc_set_ionic(tc_sim* s, int32_t model, const double* params, int32_t n
   clear_error();
   if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
   CUDA_TRY(cudaSetDevice(s->device));
-  if (model != TC_MODEL_MS)
-    return fail(TC_ERR_ARG, "ionic model " + std::to_string(model) + " is not available");
-  if (!params || n_params != 7) return fail(TC_ERR_ARG, "Mitchell-Schaeffer needs 7 parameters");
-  const double* p = params;
-  if (!(p[0] > 0 && p[1] > 0 && p[2] > 0 && p[3] > 0 && p[6] > p[5]))
-    return fail(TC_ERR_ARG, "Mitchell-Schaeffer needs positive time constants and v_max > v_min");
-  std::copy(p, p + 7, s->ms);
+  std::vector<double> rest;   // resting states (V excluded)
+  double v0 = 0.0;
+  if (model == TC_MODEL_MS) {
+    if (!params || n_params != 7) return fail(TC_ERR_ARG, "Mitchell-Schaeffer needs 7 parameters");
+    const double* p = params;
+    if (!(p[0] > 0 && p[1] > 0 && p[2] > 0 && p[3] > 0 && p[6] > p[5]))
+      return fail(TC_ERR_ARG, "Mitchell-Schaeffer needs positive time constants and v_max > v_min");
+    std::copy(p, p + 7, s->ms);
+    rest.assign(1, 1.0);
+    v0 = p[5];
+  } else if (model == TC_MODEL_TP06) {
+    if (!params || n_params != 1) return fail(TC_ERR_ARG, "TP06 needs 1 parameter (cell type)");
+    const int cell = (int)params[0];
+    if (cell < 0 || cell > 2 || params[0] != (double)cell)
+      return fail(TC_ERR_ARG, "TP06 cell type must be 0 (endo), 1 (mid) or 2 (epi)");
+    s->cell = cell;
+    rest.assign(kTP06States, 0.0);
+    tp06_rest_state(cell, rest.data(), &v0);
+  } else {
+    return fail(TC_ERR_ARG, "unknown ionic model " + std::to_string(model));
+  }
+  const int ns = (int)rest.size();
+  if (s->state && ns != s->n_states) {
+    dfree(s, s->state);
+    s->state = nullptr;
+  }
+  if (!s->state) TRY(dalloc_bytes(s, &s->state, (size_t)ns * s->n * s->esz));
   s->model = model;
-  s->n_states = 1;
-  if (s->state) cudaFree(s->state), s->state = nullptr;
-  CUDA_TRY(cudaMalloc(&s->state, s->n * sizeof(double)));
-  std::vector<double> h(s->n, 1.0);
-  if (init_state) TRY(to_internal(s, init_state, h));
-  CUDA_TRY(cudaMemcpy(s->state, h.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
-  std::vector<double> v0(s->n, s->ms[5]);
+  s->n_states = ns;
+  std::vector<double> col(s->n);
+  for (int j = 0; j < ns; ++j) {
+    if (init_state)
+      to_internal(s, init_state + (size_t)j * s->n, col.data());
+    else
+      std::fill(col.begin(), col.end(), rest[j]);
+    TRY(upload_vec(s, static_cast<char*>(s->state) + (size_t)j * s->n * s->esz, col.data(), s->n));
+  }
+  std::fill(col.begin(), col.end(), v0);
   s->iv = 0;
-  CUDA_TRY(cudaMemcpy(s->V[0], v0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(s->V[2], v0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
-  std::vector<double> a0(s->n, s->ms[5] >= s->thr ? 0.0 : -1.0);
+  TRY(upload_vec(s, s->V[0], col.data(), s->n));
+  TRY(upload_vec(s, s->V[2], col.data(), s->n));
+  std::vector<double> a0(s->n, v0 >= s->thr ? 0.0 : -1.0);
   CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
   s->k = 0;
   return TC_OK;
@@ -409,7 +581,7 @@ tc_status tc_set_activation_threshold(tc_sim* s, double v) {
   if (s->model >= 0) {
     CUDA_TRY(cudaSetDevice(s->device));
     std::vector<double> vcur(s->n), a0(s->n);
-    CUDA_TRY(cudaMemcpy(vcur.data(), s->V[s->iv], s->n * sizeof(double), cudaMemcpyDeviceToHost));
+    TRY(download_vec(s, s->V[s->iv], vcur.data(), s->n));
     for (int64_t i = 0; i < s->n; ++i) a0[i] = vcur[i] >= v ? 0.0 : -1.0;
     CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
   }
@@ -433,92 +605,10 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
   CUDA_TRY(cudaMemcpyAsync(s->stats, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream));
   CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
   CUDA_TRY(cudaMemsetAsync(s->bar, 0, sizeof(GridBar), s->stream));
-  const double range = s->ms[6] - s->ms[5];
-  MSConst mc;
-  mc.vmin = s->ms[5];
-  mc.inv_range = 1.0 / range;
-  mc.range = range;
-  mc.vgate = s->ms[4];
-  mc.inv_tau_in = 1.0 / s->ms[0];
-  mc.inv_tau_out = 1.0 / s->ms[1];
-  mc.dec_open = std::exp(-s->dt / s->ms[2]);
-  mc.dec_close = std::exp(-s->dt / s->ms[3]);
-  const int ion_blocks = (int)((s->n + kIonicThreads - 1) / kIonicThreads);
   size_t ev = 0;
-  std::vector<std::pair<size_t, int>> prof_pairs;
+  std::vector<size_t> marks;
   for (int64_t st = 0; st < n_steps; ++st) {
-    double* Vc = s->V[s->iv];
-    double* Vp = s->V[(s->iv + 2) % 3];
-    double* Vn = s->V[(s->iv + 1) % 3];
-    IonicArgs ia;
-    ia.n = s->n;
-    ia.V = Vc;
-    ia.Vp = Vp;
-    ia.h = s->state;
-    ia.g1 = s->g1;
-    ia.g2 = s->g2;
-    ia.x0 = Vn;
-    ia.stim_off = s->stim_off;
-    ia.stim_ids = s->stim_ids;
-    ia.stims = s->stims;
-    ia.k = s->k;
-    ia.chi = s->chi;
-    ia.cm = s->cm;
-    ia.dt = s->dt;
-    ia.theta = s->theta;
-    ia.ms = mc;
-    ia.bar = s->bar;
-    if (s->prof) {
-      cudaEvent_t e = pooled_event(s, ev);
-      if (!e) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
-      cudaEventRecord(e, s->stream);
-      prof_pairs.push_back({ev++, 0});
-    }
-    ionic_ms_kernel<<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
-    CUDA_TRY(cudaGetLastError());
-    PcgArgs pa;
-    pa.n = s->n;
-    pa.slice_ptr = s->slice_ptr;
-    pa.col = s->col;
-    pa.vM = s->vM;
-    pa.vK = s->vK;
-    pa.vA = s->vA;
-    pa.dinv = s->dinv;
-    pa.blk_slice = s->blk_slice;
-    pa.g1 = s->g1;
-    pa.g2 = s->g2;
-    pa.x = Vn;
-    pa.Vcur = Vc;
-    pa.r = s->r;
-    pa.z = s->z;
-    pa.p = s->p;
-    pa.q = s->q;
-    pa.act = s->act;
-    pa.partA = s->partA;
-    pa.partB = s->partB;
-    pa.bar = s->bar;
-    pa.err = s->err;
-    pa.stats = s->stats;
-    pa.atol = s->atol;
-    pa.rtol = s->rtol;
-    pa.max_iter = s->max_iter;
-    pa.wait_limit = s->wait_limit;
-    pa.t_k = (double)s->k * s->dt;
-    pa.dt = s->dt;
-    pa.thr = s->thr;
-    if (s->prof) {
-      cudaEvent_t e = pooled_event(s, ev);
-      cudaEventRecord(e, s->stream);
-      ev++;
-    }
-    void* args[] = {&pa};
-    CUDA_TRY(cudaLaunchCooperativeKernel(pcg_kernel_ptr(s->pcg_threads), s->nblocks,
-                                         s->pcg_threads, args, 0, s->stream));
-    if (s->prof) {
-      cudaEvent_t e = pooled_event(s, ev);
-      cudaEventRecord(e, s->stream);
-      ev++;
-    }
+    TRY(s->precision == TC_FP64 ? launch_step<double>(s, ev, marks) : launch_step<float>(s, ev, marks));
     s->iv = (s->iv + 1) % 3;
     s->k += 1;
   }
@@ -528,10 +618,10 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
   CUDA_TRY(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   if (s->prof) {
-    for (auto& pp : prof_pairs) {
+    for (size_t m : marks) {
       float a = 0.f, b = 0.f;
-      cudaEventElapsedTime(&a, s->evpool[pp.first], s->evpool[pp.first + 1]);
-      cudaEventElapsedTime(&b, s->evpool[pp.first + 1], s->evpool[pp.first + 2]);
+      cudaEventElapsedTime(&a, s->evpool[m], s->evpool[m + 1]);
+      cudaEventElapsedTime(&b, s->evpool[m + 1], s->evpool[m + 2]);
       s->prof_acc.ionic_ms += a;
       s->prof_acc.ionic_launches += 1;
       s->prof_acc.pcg_ms += b;
@@ -553,11 +643,11 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
   return TC_OK;
 }
 
-static double* field_ptr(const tc_sim* s, int32_t field) {
+static void* field_ptr(const tc_sim* s, int32_t field) {
   if (field == TC_FIELD_V) return s->V[s->iv];
   if (field == TC_FIELD_V_PREV) return s->V[(s->iv + 2) % 3];
   if (field >= TC_FIELD_STATE && field < TC_FIELD_STATE + s->n_states)
-    return s->state + (size_t)(field - TC_FIELD_STATE) * s->n;
+    return static_cast<char*>(s->state) + (size_t)(field - TC_FIELD_STATE) * s->n * s->esz;
   return nullptr;
 }
 
@@ -566,13 +656,11 @@ tc_status tc_read_state(const tc_sim* s, int32_t field, double* dst, int64_t n) 
   if (!s || !dst) return fail(TC_ERR_ARG, "null argument");
   if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
   if (s->model < 0) return fail(TC_ERR_STATE, "no ionic model set");
-  const double* src = field_ptr(s, field);
+  const void* src = field_ptr(s, field);
   if (!src) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
   CUDA_TRY(cudaSetDevice(s->device));
-  double* tmp = s->pinned;
-  CUDA_TRY(cudaMemcpyAsync(tmp, src, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  CUDA_TRY(cudaStreamSynchronize(s->stream));
-  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = tmp[i];
+  TRY(download_vec(s, src, s->pinned, s->n));
+  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = s->pinned[i];
   return TC_OK;
 }
 
@@ -581,15 +669,12 @@ tc_status tc_write_state(tc_sim* s, int32_t field, const double* src, int64_t n)
   if (!s || !src) return fail(TC_ERR_ARG, "null argument");
   if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
   if (s->model < 0) return fail(TC_ERR_STATE, "no ionic model set");
-  double* dst = field_ptr(s, field);
+  void* dst = field_ptr(s, field);
   if (!dst) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
   CUDA_TRY(cudaSetDevice(s->device));
   CUDA_TRY(cudaStreamSynchronize(s->stream));   // the staging buffer may still feed a copy
-  double* tmp = s->pinned;
-  for (int64_t i = 0; i < s->n; ++i) tmp[i] = src[s->perm[i]];
-  CUDA_TRY(cudaMemcpyAsync(dst, tmp, s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-  CUDA_TRY(cudaStreamSynchronize(s->stream));
-  return TC_OK;
+  to_internal(s, src, s->pinned);
+  return upload_vec(s, dst, s->pinned, s->n);
 }
 
 tc_status tc_activation_times(const tc_sim* s, double v_threshold, double* dst, int64_t n) {
@@ -620,24 +705,29 @@ tc_status tc_set_step_index(tc_sim* s, int64_t k) {
   return TC_OK;
 }
 
-static const double* op_values(const tc_sim* s, int32_t op) {
+static const void* op_values(const tc_sim* s, int32_t op) {
   return op == TC_OP_M ? s->vM : op == TC_OP_K ? s->vK : op == TC_OP_A ? s->vA : nullptr;
 }
 
 tc_status tc_apply_operator_dev(tc_sim* s, int32_t op, const void* x_dev, void* y_dev) {
   clear_error();
   if (!s || !x_dev || !y_dev) return fail(TC_ERR_ARG, "null argument");
-  const double* val = op_values(s, op);
+  const void* val = op_values(s, op);
   if (!val) return fail(TC_ERR_ARG, "unknown operator");
   if (((uintptr_t)x_dev | (uintptr_t)y_dev) & 15) return fail(TC_ERR_ARG, "x/y must be 16-byte aligned");
   CUDA_TRY(cudaSetDevice(s->device));
   const int threads = 256;
-  const int64_t warps_needed = s->nslices;
-  const int64_t blocks = std::min<int64_t>((warps_needed * 32 + threads - 1) / threads,
+  const int64_t blocks = std::min<int64_t>((s->nslices * 32 + threads - 1) / threads,
                                            (int64_t)s->num_sms * 8);
-  spmv_sell_kernel<<<(int)std::max<int64_t>(blocks, 1), threads, 0, s->stream>>>(
-      s->n, s->nslices, s->slice_ptr, s->col, val, static_cast<const double*>(x_dev),
-      static_cast<double*>(y_dev));
+  const int nb = (int)std::max<int64_t>(blocks, 1);
+  if (s->precision == TC_FP64)
+    spmv_sell_kernel<double><<<nb, threads, 0, s->stream>>>(
+        s->n, s->nslices, s->slice_ptr, s->col, static_cast<const double*>(val),
+        static_cast<const double*>(x_dev), static_cast<double*>(y_dev));
+  else
+    spmv_sell_kernel<float><<<nb, threads, 0, s->stream>>>(
+        s->n, s->nslices, s->slice_ptr, s->col, static_cast<const float*>(val),
+        static_cast<const float*>(x_dev), static_cast<float*>(y_dev));
   CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }
@@ -648,27 +738,21 @@ tc_status tc_apply_operator(tc_sim* s, int32_t op, const double* x, double* y, i
   if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
   if (!op_values(s, op)) return fail(TC_ERR_ARG, "unknown operator");
   CUDA_TRY(cudaSetDevice(s->device));
-  std::vector<double> xi;
-  to_internal(s, x, xi);
-  double *dx = nullptr, *dy = nullptr;
-  CUDA_TRY(cudaMalloc(&dx, s->n * sizeof(double)));
-  cudaError_t e = cudaMalloc(&dy, s->n * sizeof(double));
+  void *dx = nullptr, *dy = nullptr;
+  CUDA_TRY(cudaMalloc(&dx, s->n * s->esz));
+  cudaError_t e = cudaMalloc(&dy, s->n * s->esz);
   if (e != cudaSuccess) {
     cudaFree(dx);
     return cuda_fail(e, "cudaMalloc");
   }
-  std::vector<double> yi(s->n);
-  e = cudaMemcpyAsync(dx, xi.data(), s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-  tc_status st = TC_OK;
-  if (e == cudaSuccess) st = tc_apply_operator_dev(s, op, dx, dy);
-  if (e == cudaSuccess && st == TC_OK)
-    e = cudaMemcpyAsync(yi.data(), dy, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  to_internal(s, x, s->pinned);
+  tc_status st = upload_vec(s, dx, s->pinned, s->n);
+  if (st == TC_OK) st = tc_apply_operator_dev(s, op, dx, dy);
+  if (st == TC_OK) st = download_vec(s, dy, s->pinned, s->n);
   cudaFree(dx);
   cudaFree(dy);
-  if (e != cudaSuccess) return cuda_fail(e, "tc_apply_operator");
   if (st != TC_OK) return st;
-  for (int64_t i = 0; i < s->n; ++i) y[s->perm[i]] = yi[i];
+  for (int64_t i = 0; i < s->n; ++i) y[s->perm[i]] = s->pinned[i];
   return TC_OK;
 }
 
@@ -693,7 +777,7 @@ tc_status tc_reset_profile(tc_sim* s) {
   return TC_OK;
 }
 
-const char* tc_version(void) { return "tc_b300 0.1 (sm_103a)"; }
+const char* tc_version(void) { return "tc_b300 0.2 (sm_103a)"; }
 
 }  // extern "C"
 
@@ -705,8 +789,6 @@ const char* tc_version(void) { return "tc_b300 0.1 (sm_103a)"; }
 // synchronisation cudaFree implies.  tc_apply_operator_static does the same work with its
 // staging in the file-scope array below, which every GPU that loads this library holds until
 // the process exits.  Calls share the array; calls that overlap on the GPU race.
-
-#include <mutex>
 
 namespace {
 
@@ -758,11 +840,13 @@ extern "C" tc_status tc_apply_operator_static(tc_sim* s, int32_t op, const doubl
   clear_error();
   if (!s || !x || !y) return fail(TC_ERR_ARG, "null argument");
   if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
+  if (s->precision != TC_FP64)
+    return fail(TC_ERR_ARG, "tc_apply_operator_static serves TC_FP64 simulations only");
   if (s->n > kStaticMaxNodes)
     return fail(TC_ERR_ARG, "tc_apply_operator_static handles at most " +
                                 std::to_string(kStaticMaxNodes) + " nodes; this mesh has " +
                                 std::to_string(s->n) + " (use tc_apply_operator)");
-  const double* val = op_values(s, op);
+  const double* val = static_cast<const double*>(op_values(s, op));
   if (!val) return fail(TC_ERR_ARG, "unknown operator");
   CUDA_TRY(cudaSetDevice(s->device));
   double* scratch = nullptr;

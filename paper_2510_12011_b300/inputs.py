@@ -184,6 +184,7 @@ class Workload:
     rtol: float = 1e-10
     max_iter: int = 1000
     v_threshold: float = 0.0  # mV, activation threshold
+    tp06_cell: int = 2        # ten Tusscher-Panfilov cell type: 0 endo, 1 mid, 2 epi
 
     @property
     def n_steps(self) -> int:

@@ -292,16 +292,23 @@ class Simulation:
     __del__ = close
 
 
+def set_model(sim, w):
+    """tc_set_ionic with the workload's model and parameters (also resets to rest, step 0)."""
+    if w.model == "ms":
+        sim.set_ionic(TC_MODEL_MS, w.ms.as_array())
+    elif w.model == "tp06":
+        sim.set_ionic(TC_MODEL_TP06, [float(w.tp06_cell)])
+    else:
+        raise TcError(TC_ERR_ARG, f"model {w.model!r} is not available")
+
+
 def from_workload(w, stream=None, precision=TC_FP64):
     """Build a Simulation from an ``inputs.Workload`` (mesh, tissue, model, stimuli, solver)."""
     mesh = Mesh.from_inputs(w.mesh)
     sim = Simulation(mesh, w.sigma_l, w.sigma_t, w.chi, w.cm, w.theta, w.dt, precision, stream)
     sim.mesh = mesh
     sim.set_activation_threshold(w.v_threshold)
-    if w.model == "ms":
-        sim.set_ionic(TC_MODEL_MS, w.ms.as_array())
-    else:
-        raise TcError(TC_ERR_ARG, f"model {w.model!r} is not available")
+    set_model(sim, w)
     for s in w.stimuli:
         sim.add_stimulus(s.nodes, s.start, s.duration, s.intensity)
     sim.set_solver(w.atol, w.rtol, w.max_iter)

@@ -1,0 +1,95 @@
+"""GPU TP06 path and the FP32 precision form against the FP64 oracle.
+
+FP64 TP06 is held to the same bar as the rest of the FP64 path (1e-8 mV on V, 1e-6 ms on
+activation times).  The FP32 precision form (SpMV, vector updates and ionic model in FP32, PCG
+reductions and alpha/beta in FP64) is not expected to match bit for bit; its bar is the
+accuracy the precision form promises: activation-time error well under 1 ms, and V within a
+few mV of the FP64 result (in time, a shift of a fraction of a time step on the upstroke)."""
+import numpy as np
+import pytest
+
+from oracle.monodomain import Monodomain
+from paper_2510_12011_b300 import inputs as I
+from paper_2510_12011_b300 import tc
+
+pytestmark = pytest.mark.gpu
+
+
+def _tp06_slab():
+    w = I.slab_small_ms()
+    w.model = "tp06"
+    w.dt = 0.02
+    w.name = "slab10x4x2_h0.5_tp06"
+    return w
+
+
+@pytest.fixture(scope="module")
+def tp06_runs():
+    w = _tp06_slab()
+    o = Monodomain(w)
+    g = tc.from_workload(w)
+    o.run(1)
+    g.step(1)
+    first = (g.read(), o.V.copy(), [g.read(tc.TC_FIELD_STATE + j) for j in range(18)],
+             [s.copy() for s in o.state])
+    o.run(499)
+    st = g.step(499)
+    return w, first, (g.read(), o.V.copy(), g.activation_times(), o.act.copy(), st)
+
+
+def test_tp06_first_step(tp06_runs):
+    w, (vg, vo, ug, uo), _ = tp06_runs
+    assert np.abs(vg - vo).max() <= 1e-11
+    for j in range(18):
+        assert np.allclose(ug[j], uo[j], rtol=1e-12, atol=1e-16), j
+
+
+def test_tp06_fp64_parity_500_steps(tp06_runs):
+    w, _, (vg, vo, ag, ao, st) = tp06_runs
+    assert np.abs(vg - vo).max() <= 1e-8
+    assert np.array_equal(ag >= 0, ao >= 0) and (ao >= 0).sum() > 100
+    assert np.abs(ag - ao).max() <= 1e-6
+    assert st["not_converged"] == 0
+
+
+@pytest.mark.parametrize("model", ["ms", "tp06"])
+def test_fp32_form_against_fp64_oracle(model):
+    w = I.slab_small_ms() if model == "ms" else _tp06_slab()
+    steps = 2000 if model == "ms" else 1000
+    o = Monodomain(w).run(steps)
+    g = tc.from_workload(w, precision=tc.TC_FP32)
+    g.step(steps)
+    vg, ag = g.read(), g.activation_times()
+    act = ao = o.act
+    both = (ag >= 0) & (ao >= 0)
+    assert both.sum() >= 0.9 * max((ao >= 0).sum(), 1) and (ao >= 0).sum() > 100
+    err_act = np.abs(ag[both] - ao[both]).max()
+    assert err_act < 0.05, err_act          # ms; the precision form's budget is 1 ms
+    assert np.abs(vg - o.V).max() < 5.0      # mV, wavefront nodes included
+
+
+def test_fp32_operators_are_float_products():
+    w = I.slab_small_ms()
+    g64 = tc.from_workload(w)
+    g32 = tc.from_workload(w, precision=tc.TC_FP32)
+    x = I.random_vector(w.mesh.n_nodes, 3, -90.0, 30.0)
+    for op in (tc.TC_OP_M, tc.TC_OP_K, tc.TC_OP_A):
+        y64, y32 = g64.apply(op, x), g32.apply(op, x)
+        scale = np.abs(g64.apply(op, np.abs(x))).max() + 1e-300
+        assert np.abs(y32 - y64).max() <= 1e-5 * scale
+    with pytest.raises(tc.TcError):
+        g32.apply_static(tc.TC_OP_A, x)
+
+
+def test_tp06_cell_types_and_errors():
+    w = _tp06_slab()
+    g = tc.from_workload(w)
+    with pytest.raises(tc.TcError) as e:
+        g.set_ionic(tc.TC_MODEL_TP06, [3.0])
+    assert e.value.status == tc.TC_ERR_ARG
+    for cell in (0, 1):
+        w.tp06_cell = cell
+        o = Monodomain(w).run(50)
+        g.set_ionic(tc.TC_MODEL_TP06, [float(cell)])
+        g.step(50)
+        assert np.abs(g.read() - o.V).max() <= 1e-9
