@@ -1,10 +1,11 @@
 #!/usr/bin/env python
-"""Benchmark of the monodomain hot path: node-steps/s of the plain FP64 method on one B300.
+"""Benchmark of the monodomain hot path: node-steps/s of the plain FP64 method on one B300,
+with the FP32 precision form timed on the same steps and its error against the FP64 result.
 
 One step = ionic update + RHS + Jacobi-PCG solve + activation capture for every node of the
 workload (one time step k -> k+1 of the operator-split scheme).  The default workload is the
-40x16x6 mm slab at h = 0.2 mm (504,711 nodes, 2,880,000 tets, dt = 0.02 ms, 5000 steps =
-100 ms).  Inputs are synthetic and seeded.
+40x16x6 mm slab at h = 0.2 mm (504,711 nodes, 2,880,000 tets) with the ten Tusscher-Panfilov
+2006 epicardial model, dt = 0.02 ms, 5000 steps = 100 ms.  Inputs are synthetic and seeded.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -31,7 +32,13 @@ sys.path.insert(0, ROOT)
 
 from paper_2510_12011_b300 import inputs as I  # noqa: E402
 
-METRIC = "node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + activation capture)"
+METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + activation "
+          "capture); FP32 precision form alongside")
+# FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
+# profiles/ (thread-level FP64 instructions / nodes); used to turn the live launch time into an
+# achieved FP64 instruction rate.
+TP06_FP64_INSTR_PER_NODE = 2405.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 110.9e6   # dram read + write of the same capture
 
 
 def parse():
@@ -40,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["large_ms", "small_ms"], default="large_ms")
+    ap.add_argument("--workload", choices=["large_tp06", "large_ms", "small_ms"], default="large_tp06")
+    ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -48,6 +56,8 @@ def parse():
 
 
 def workload(name):
+    if name == "large_tp06":
+        return I.slab_large("tp06")
     if name == "large_ms":
         return I.slab_large("ms")
     return I.slab_small_ms()
@@ -59,6 +69,15 @@ def measured_peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6400.0), "measured"
     return 6400.0, "fallback"
+
+
+# FP64 pipe of B300: 2 thread-level FP64 instructions (DFMA/DADD/DMUL) per clock per SM
+# (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 2 inst/cycle/SM).
+SMS = 148
+
+
+def fp64_instr_peak(sm_mhz):
+    return 2.0 * SMS * (sm_mhz or 2032.0) * 1e6
 
 
 # ---- algorithmic bytes (FP64 values, int32 indices; SELL padding not counted) -------------
@@ -166,6 +185,49 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def timed_steps(sim, w, K, W, stream, torch):
+    """W warm-up steps, back to rest at step 0, then K steps timed with CUDA events on the
+    simulation's stream (per-launch events inside tc_step give the per-kernel split)."""
+    from paper_2510_12011_b300 import tc
+    sim.step(W)
+    tc.set_model(sim, w)
+    sim.set_profiling(True)
+    sim.reset_profile()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sim.profile()
+    sim.set_profiling(False)
+    return e0.elapsed_time(e1), stats, prof
+
+
+def apd90_check(w_big, torch):
+    """APD90 error of the FP32 form against the FP64 path over one full beat (400 ms) of the
+    10x4x2 mm slab with the same ionic model (the timed workload ends before repolarisation)."""
+    from paper_2510_12011_b300 import tc
+    w = I.slab_small_ms()
+    w.model, w.tp06_cell, w.dt, w.t_end = w_big.model, w_big.tp06_cell, w_big.dt, 400.0
+    w.rtol, w.atol, w.max_iter = w_big.rtol, w_big.atol, w_big.max_iter
+    out = {}
+    for prec in (tc.TC_FP64, tc.TC_FP32):
+        g = tc.from_workload(w, precision=prec)
+        g.step(w.n_steps)
+        out[prec] = (g.apd90(), g.activation_times())
+        g.close()
+    a64, a32 = out[tc.TC_FP64][0], out[tc.TC_FP32][0]
+    ok = (a64 > 0) & (a32 > 0)
+    rel = np.abs(a32[ok] - a64[ok]) / a64[ok]
+    return {"workload": f"slab10x4x2_h0.5_{w.model}, {w.t_end:g} ms (one beat)",
+            "nodes_repolarised": int(ok.sum()), "nodes": int(a64.size),
+            "apd90_fp64_ms_mean": float(a64[ok].mean()) if ok.any() else None,
+            "apd90_err_pct_max": float(100 * rel.max()) if ok.any() else None,
+            "act_err_ms_max": float(np.abs(out[tc.TC_FP32][1] - out[tc.TC_FP64][1]).max())}
+
+
 def run_ours(args):
     import torch
     from paper_2510_12011_b300 import tc
@@ -190,25 +252,13 @@ def run_ours(args):
 
     sim = tc.from_workload(w, stream=stream.cuda_stream)
     size = sim.size()
-    sim.step(W)
-    sim.set_ionic(tc.TC_MODEL_MS, w.ms.as_array())     # back to rest, step 0
-    sim.set_profiling(True)
-    sim.reset_profile()
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stats = sim.step(K)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, stats, prof = timed_steps(sim, w, K, W, stream, torch)
     barrier()
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    prof = sim.profile()
-    sim.set_profiling(False)
+    v64, act64 = sim.read(), sim.activation_times()
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -218,10 +268,25 @@ def run_ours(args):
     # roofline of the dominant kernel (by accumulated device time)
     peak, peak_kind = measured_peaks()
     pcg_launch_ms = prof["pcg_ms"] / max(prof["pcg_launches"], 1)
+    ion_launch_ms = prof["ionic_ms"] / max(prof["ionic_launches"], 1)
     iters = prof["pcg_iterations"] / max(prof["pcg_launches"], 1)
     bytes_launch = pcg_launch_bytes(n, size["nnz"], (n + 31) // 32, iters)
-    achieved = bytes_launch / (pcg_launch_ms * 1e-3) / 1e9
-    dominant = "pcg_step_kernel" if prof["pcg_ms"] >= prof["ionic_ms"] else "ionic_ms_kernel"
+    pcg_gbs = bytes_launch / (pcg_launch_ms * 1e-3) / 1e9
+    roof_pcg = {"kernel": "pcg_step_kernel", "bound": "hbm", "achieved": pcg_gbs, "peak": peak,
+                "unit": "GB/s", "frac": pcg_gbs / peak, "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": bytes_launch,
+                "avg_launch_ms": pcg_launch_ms}
+    if prof["ionic_ms"] > prof["pcg_ms"] and w.model == "tp06" and TP06_FP64_INSTR_PER_NODE:
+        ach = TP06_FP64_INSTR_PER_NODE * n / (ion_launch_ms * 1e-3)
+        pk = fp64_instr_peak(clk.get("sm_mhz"))
+        roofline = {"kernel": "ionic_tp06_kernel<double>", "bound": "alu", "achieved": ach / 1e12,
+                    "peak": pk / 1e12, "unit": "T FP64 thread-instr/s", "frac": ach / pk,
+                    "traffic": TP06_FP64_DRAM_BYTES_PER_LAUNCH * n / 504711,
+                    "traffic_unit": "bytes per launch (ncu dram read + write)",
+                    "peak_source": "FP64 pipe: 2 instr/clk/SM x 148 SMs x median SM clock of the run",
+                    "fp64_instr_per_node": TP06_FP64_INSTR_PER_NODE, "avg_launch_ms": ion_launch_ms}
+    else:
+        roofline = roof_pcg
 
     # SpMV HBM GB/s: y = A x alone, L2 flushed before every launch
     x = torch.randn(n, dtype=torch.float64, device=dev)
@@ -240,36 +305,56 @@ def run_ours(args):
             times.append(a.elapsed_time(b))
     spmv_ms = float(np.median(times))
     spmv_gbs = spmv_bytes(n, size["nnz"]) / (spmv_ms * 1e-3) / 1e9
-    del flush
+    del flush, x, y
 
-    # end to end through the C ABI with host buffers: each step uploads V^k, V^{k-1} and the
-    # ionic state from page-locked host memory, steps once and reads V^{k+1} back
+    # end to end through the C ABI with host buffers: each step uploads V^k, V^{k-1} and every
+    # ionic state from page-locked host memory, steps once and reads V^{k+1} and the states back
     Ke = max(1, min(args.e2e_steps, K))
-    sim.set_ionic(tc.TC_MODEL_MS, w.ms.as_array())
-    hv = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-    hp = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-    hh = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-    hv[:] = w.ms.v_min
-    hp[:] = w.ms.v_min
-    hh[:] = 1.0
+    tc.set_model(sim, w)
+    n_states = 1 if w.model == "ms" else 18
+    fields = [tc.TC_FIELD_V, tc.TC_FIELD_V_PREV] + [tc.TC_FIELD_STATE + j for j in range(n_states)]
+    host = {f: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for f in fields}
+    for f in fields:
+        host[f][:] = sim.read(f)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(Ke):
-        sim.write(tc.TC_FIELD_V, hv)
-        sim.write(tc.TC_FIELD_V_PREV, hp)
-        sim.write(tc.TC_FIELD_STATE, hh)
+        for f in fields:
+            sim.write(f, host[f])
         sim.step(1)
-        hp[:] = hv
-        hv[:] = sim.read(tc.TC_FIELD_V)
-        hh[:] = sim.read(tc.TC_FIELD_STATE)
+        host[tc.TC_FIELD_V_PREV][:] = host[tc.TC_FIELD_V]
+        for f in fields:
+            if f != tc.TC_FIELD_V_PREV:
+                host[f][:] = sim.read(f)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
-    e2e = {"value": n * Ke * world / e2e_s, "unit": "node-steps/s", "h2d_bytes_per_step": 3 * 8 * n,
-           "d2h_bytes_per_step": 2 * 8 * n, "steps": Ke,
-           "what": "per step: tc_write_state(V^k, V^{k-1}, gate) from pinned host arrays, "
-                   "tc_step(1), tc_read_state(V^{k+1}, gate) to host"}
+    e2e = {"value": n * Ke * world / e2e_s, "unit": "node-steps/s",
+           "h2d_bytes_per_step": len(fields) * 8 * n, "d2h_bytes_per_step": (len(fields) - 1) * 8 * n,
+           "steps": Ke,
+           "what": "per step: tc_write_state of V^k, V^{k-1} and every ionic state from pinned host "
+                   "arrays, tc_step(1), tc_read_state of V^{k+1} and the states"}
+    sim.close()
+
+    # FP32 precision form on the same workload and steps, and its error against FP64
+    fp32 = None
+    if not args.no_fp32:
+        sim32 = tc.from_workload(w, stream=stream.cuda_stream, precision=tc.TC_FP32)
+        ms32, st32, prof32 = timed_steps(sim32, w, K, W, stream, torch)
+        v32, act32 = sim32.read(), sim32.activation_times()
+        both = (act32 >= 0) & (act64 >= 0)
+        fp32 = {"value": n * K * world / (ms32 * 1e-3), "unit": "node-steps/s",
+                "ms_per_step": ms32 / K, "dtype": "f32 (FP64 reductions, alpha, beta)",
+                "speedup_vs_fp64": ms / ms32,
+                "act_err_ms_max": float(np.abs(act32[both] - act64[both]).max()) if both.any() else None,
+                "activated_fp64": int((act64 >= 0).sum()), "activated_fp32": int((act32 >= 0).sum()),
+                "v_err_mv_max": float(np.abs(v32 - v64).max()),
+                "mean_cg_iterations": st32["cg_iterations"] / max(K, 1),
+                "kernels": {"ionic_ms": prof32["ionic_ms"], "pcg_ms": prof32["pcg_ms"]}}
+        sim32.close()
+        if w.model == "tp06":
+            fp32["apd90"] = apd90_check(w, torch)
 
     if rank != 0:
         return
@@ -280,6 +365,7 @@ def run_ours(args):
         "config": {"workload": w.name, "n_nodes": n, "n_tets": w.mesh.n_tets, "nnz": size["nnz"],
                    "padded_nnz": size["padded_nnz"], "pcg_blocks": size["n_blocks"],
                    "dt_ms": w.dt, "simulated_ms": K * w.dt, "ionic_model": w.model,
+                   "tp06_cell": w.tp06_cell if w.model == "tp06" else None,
                    "pcg": {"atol": w.atol, "rtol": w.rtol, "max_iter": w.max_iter},
                    "l2": "inputs larger than L2: one step streams M, K, A values and indices "
                          f"({size['padded_nnz'] * 28 / 1e6:.0f} MB) plus node vectors vs 132.6 MB L2",
@@ -288,15 +374,14 @@ def run_ours(args):
                   "mean_cg_iterations": stats["cg_iterations"] / max(K, 1),
                   "max_cg_iterations": stats["max_iterations"],
                   "not_converged": stats["not_converged"]},
-        "kernels": {"ionic_ms_kernel": {"launches": prof["ionic_launches"], "ms": prof["ionic_ms"]},
+        "kernels": {"ionic": {"launches": prof["ionic_launches"], "ms": prof["ionic_ms"]},
                     "pcg_step_kernel": {"launches": prof["pcg_launches"], "ms": prof["pcg_ms"],
                                         "iterations": prof["pcg_iterations"]}},
-        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"{peak_kind} hbm_gbs",
-                     "bytes_per_launch": bytes_launch, "avg_launch_ms": pcg_launch_ms},
+        "roofline": roofline,
+        "roofline_pcg": roof_pcg,
         "spmv": {"value": spmv_gbs, "unit": "GB/s", "ms": spmv_ms, "bytes": spmv_bytes(n, size["nnz"]),
                  "frac": spmv_gbs / peak, "l2": "flushed (512 MB read) before every launch"},
+        "fp32_form": fp32,
         "e2e": e2e,
         "gpu_launches": prof["ionic_launches"] + prof["pcg_launches"],
         "clocks": clk,

@@ -164,6 +164,18 @@ tc_status tc_write_state(tc_sim* sim, int32_t field, const double* host_src, int
  * capture threshold (TC_ERR_STATE otherwise). */
 tc_status tc_activation_times(const tc_sim* sim, double v_threshold, double* host_dst, int64_t n);
 
+/* Repolarisation (Section 2.1, LRT: V returns below -70 mV with a negative time derivative).
+ * tc_set_repolarisation_threshold: the LRT threshold (default -70 mV); only before stepping.
+ * tc_repolarisation_times: per node, the first downward crossing of that threshold after
+ *   activation, linearly interpolated within the step; -1 if none yet.
+ * tc_apd90: per node, APD90 = t90 - activation time, where t90 is the first downward crossing
+ *   of V_rest + 0.1 (V_peak - V_rest) after activation (V_peak: maximum of V since activation,
+ *   V_rest: the model's resting potential set by tc_set_ionic); -1 where undefined.
+ * Arrays: host, [n_nodes], caller order. */
+tc_status tc_set_repolarisation_threshold(tc_sim* sim, double v_threshold);
+tc_status tc_repolarisation_times(const tc_sim* sim, double* host_dst, int64_t n);
+tc_status tc_apd90(const tc_sim* sim, double* host_dst, int64_t n);
+
 /* tc_get_step_index / tc_set_step_index: the step counter k (for checkpoint/restart). */
 tc_status tc_get_step_index(const tc_sim* sim, int64_t* k);
 tc_status tc_set_step_index(tc_sim* sim, int64_t k);

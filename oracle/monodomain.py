@@ -31,6 +31,20 @@ def capture(act, v_old, v_new, t_k, dt, thr):
     return act
 
 
+def capture_repolarisation(act, vpeak, rep90, lrt, v_old, v_new, t_k, dt, v_rest, lrt_thr):
+    """After activation: track the peak, and record the first downward crossings of the 90 %
+    repolarisation level v_rest + 0.1 (peak - v_rest) and of the LRT threshold (Section 2.1: back
+    below -70 mV with a negative time derivative), linearly interpolated inside the step.
+    Nodes activated in this very step only get their peak set."""
+    m = act >= 0.0
+    vpeak[m] = np.maximum(vpeak[m], v_new[m])
+    t90 = v_rest + 0.1 * (vpeak - v_rest)
+    c90 = m & (rep90 < 0.0) & (v_old >= t90) & (v_new < t90)
+    rep90[c90] = t_k + dt * (v_old[c90] - t90[c90]) / (v_old[c90] - v_new[c90])
+    cl = m & (lrt < 0.0) & (v_old >= lrt_thr) & (v_new < lrt_thr)
+    lrt[cl] = t_k + dt * (v_old[cl] - lrt_thr) / (v_old[cl] - v_new[cl])
+
+
 def stimulus_current(stimuli, k, dt, n):
     """Nodal I_stim (uA/mm^2) at step k."""
     i_stim = np.zeros(n)
@@ -66,6 +80,11 @@ class Monodomain:
         self.V_prev = self.V.copy()
         self.act = np.full(n, -1.0)
         self.act[self.V >= w.v_threshold] = 0.0
+        self.v_rest = float(self.V[0])
+        self.vpeak = self.V.copy()
+        self.rep90 = np.full(n, -1.0)
+        self.lrt = np.full(n, -1.0)
+        self.lrt_thr = -70.0
         self.k = 0
         self.iters = []
         self.converged = []
@@ -90,11 +109,20 @@ class Monodomain:
         b = rhs(self.M, self.K, self.V, i_ion, i_stim, w.chi, w.cm, w.theta, w.dt)
         x0 = 2.0 * self.V - self.V_prev
         v_new, it, _, ok = pcg(self.A, b, x0, self.diag, w.atol, w.rtol, w.max_iter)
+        was_active = self.act >= 0.0
         capture(self.act, self.V, v_new, t_k, w.dt, w.v_threshold)
+        newly = (~was_active) & (self.act >= 0.0)
+        self.vpeak[newly] = v_new[newly]
+        act_before = np.where(was_active, self.act, -1.0)
+        capture_repolarisation(act_before, self.vpeak, self.rep90, self.lrt, self.V, v_new, t_k,
+                               w.dt, self.v_rest, self.lrt_thr)
         self.V_prev, self.V = self.V, v_new
         self.k += 1
         self.iters.append(it)
         self.converged.append(ok)
+
+    def apd90(self):
+        return np.where((self.rep90 >= 0.0) & (self.act >= 0.0), self.rep90 - self.act, -1.0)
 
     def run(self, n_steps):
         for _ in range(n_steps):

@@ -88,6 +88,9 @@ struct PcgArgs {
   T* p;
   T* q;
   double* act;
+  double* vpeak;              // per-node maximum of V since activation
+  double* rep90;              // time of the 90 % repolarisation crossing (APD90 = rep90 - act)
+  double* lrt;                // repolarisation time: first downward crossing of lrt_thr
   double* partA;              // gridDim.x
   double* partB;              // 2*gridDim.x
   GridBar* bar;
@@ -97,6 +100,7 @@ struct PcgArgs {
   int max_iter;
   long long wait_limit;
   double t_k, dt, thr;
+  double v_rest, lrt_thr;
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -473,11 +477,23 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
     }
     if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
   }
-  // activation capture: first upward crossing of thr, interpolated inside the step
+  // activation capture (first upward crossing of thr) and, after activation, the peak, the
+  // 90 % repolarisation crossing and the LRT crossing, each interpolated inside the step
   for (int64_t i = r0 + tid; i < r1; i += THREADS) {
+    const double vo = double(a.Vcur[i]), vn = double(a.x[i]);
     if (a.act[i] < 0.0) {
-      const double vo = double(a.Vcur[i]), vn = double(a.x[i]);
-      if (vo < a.thr && vn >= a.thr) a.act[i] = a.t_k + a.dt * (a.thr - vo) / (vn - vo);
+      if (vo < a.thr && vn >= a.thr) {
+        a.act[i] = a.t_k + a.dt * (a.thr - vo) / (vn - vo);
+        a.vpeak[i] = vn;
+      }
+    } else if (a.rep90[i] < 0.0 || a.lrt[i] < 0.0) {
+      const double vp = fmax(a.vpeak[i], vn);
+      a.vpeak[i] = vp;
+      const double t90 = a.v_rest + 0.1 * (vp - a.v_rest);
+      if (a.rep90[i] < 0.0 && vo >= t90 && vn < t90)
+        a.rep90[i] = a.t_k + a.dt * (vo - t90) / (vo - vn);
+      if (a.lrt[i] < 0.0 && vo >= a.lrt_thr && vn < a.lrt_thr)
+        a.lrt[i] = a.t_k + a.dt * (vo - a.lrt_thr) / (vo - vn);
     }
   }
   if (b == 0 && tid == 0) {

@@ -51,6 +51,8 @@ struct tc_sim {
   void *state = nullptr, *g1 = nullptr, *g2 = nullptr;
   void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double* act = nullptr;
+  double *vpeak = nullptr, *rep90 = nullptr, *lrt = nullptr;
+  double v_rest = 0.0, lrt_thr = -70.0;
   double *partA = nullptr, *partB = nullptr;
   GridBar* bar = nullptr;
   int* err = nullptr;
@@ -308,6 +310,11 @@ tc_status launch_step(tc_sim* s, size_t& ev, std::vector<size_t>& marks) {
   pa.p = static_cast<T*>(s->p);
   pa.q = static_cast<T*>(s->q);
   pa.act = s->act;
+  pa.vpeak = s->vpeak;
+  pa.rep90 = s->rep90;
+  pa.lrt = s->lrt;
+  pa.v_rest = s->v_rest;
+  pa.lrt_thr = s->lrt_thr;
   pa.partA = s->partA;
   pa.partB = s->partB;
   pa.bar = s->bar;
@@ -433,6 +440,9 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   ALLOCB(s->p, n * E);
   ALLOCB(s->q, n * E);
   ALLOCB(s->act, n * sizeof(double));
+  ALLOCB(s->vpeak, n * sizeof(double));
+  ALLOCB(s->rep90, n * sizeof(double));
+  ALLOCB(s->lrt, n * sizeof(double));
   ALLOCB(s->bar, sizeof(GridBar));
   ALLOCB(s->err, sizeof(int));
   ALLOCB(s->stats, sizeof(DevStats));
@@ -531,8 +541,13 @@ tc_status tc_set_ionic(tc_sim* s, int32_t model, const double* params, int32_t n
   s->iv = 0;
   TRY(upload_vec(s, s->V[0], col.data(), s->n));
   TRY(upload_vec(s, s->V[2], col.data(), s->n));
-  std::vector<double> a0(s->n, v0 >= s->thr ? 0.0 : -1.0);
+  std::vector<double> a0(s->n, v0 >= s->thr ? 0.0 : -1.0), m1(s->n, -1.0);
   CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->rep90, m1.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->lrt, m1.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  std::fill(m1.begin(), m1.end(), v0);
+  CUDA_TRY(cudaMemcpy(s->vpeak, m1.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  s->v_rest = v0;
   s->k = 0;
   return TC_OK;
 }
@@ -688,6 +703,39 @@ tc_status tc_activation_times(const tc_sim* s, double v_threshold, double* dst, 
   CUDA_TRY(cudaMemcpyAsync(tmp, s->act, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = tmp[i];
+  return TC_OK;
+}
+
+static tc_status read_double_field(const tc_sim* s, const double* src, double* dst, int64_t n) {
+  if (!s || !dst) return fail(TC_ERR_ARG, "null argument");
+  if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
+  if (s->model < 0) return fail(TC_ERR_STATE, "no ionic model set");
+  CUDA_TRY(cudaSetDevice(s->device));
+  CUDA_TRY(cudaMemcpyAsync(s->pinned, src, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = s->pinned[i];
+  return TC_OK;
+}
+
+tc_status tc_set_repolarisation_threshold(tc_sim* s, double v) {
+  clear_error();
+  if (!s || !std::isfinite(v)) return fail(TC_ERR_ARG, "bad threshold");
+  if (s->thr_locked) return fail(TC_ERR_STATE, "threshold is fixed once stepping has started");
+  s->lrt_thr = v;
+  return TC_OK;
+}
+
+tc_status tc_repolarisation_times(const tc_sim* s, double* dst, int64_t n) {
+  clear_error();
+  return read_double_field(s, s ? s->lrt : nullptr, dst, n);
+}
+
+tc_status tc_apd90(const tc_sim* s, double* dst, int64_t n) {
+  clear_error();
+  TRY(read_double_field(s, s ? s->rep90 : nullptr, dst, n));
+  std::vector<double> act(n);
+  TRY(read_double_field(s, s->act, act.data(), n));
+  for (int64_t i = 0; i < n; ++i) dst[i] = (dst[i] >= 0.0 && act[i] >= 0.0) ? dst[i] - act[i] : -1.0;
   return TC_OK;
 }
 

@@ -70,6 +70,9 @@ _SIGS = {
     "tc_read_state": [_P, C.c_int32, _D, C.c_int64],
     "tc_write_state": [_P, C.c_int32, _D, C.c_int64],
     "tc_activation_times": [_P, C.c_double, _D, C.c_int64],
+    "tc_set_repolarisation_threshold": [_P, C.c_double],
+    "tc_repolarisation_times": [_P, _D, C.c_int64],
+    "tc_apd90": [_P, _D, C.c_int64],
     "tc_get_step_index": [_P, _I64],
     "tc_set_step_index": [_P, C.c_int64],
     "tc_apply_operator": [_P, C.c_int32, _D, _D, C.c_int64],
@@ -239,6 +242,19 @@ class Simulation:
     def activation_times(self, v_threshold=0.0):
         out = np.empty(self.n_nodes)
         _check(lib().tc_activation_times(self._h, v_threshold, _d(out), self.n_nodes))
+        return out
+
+    def set_repolarisation_threshold(self, v):
+        _check(lib().tc_set_repolarisation_threshold(self._h, v))
+
+    def repolarisation_times(self):
+        out = np.empty(self.n_nodes)
+        _check(lib().tc_repolarisation_times(self._h, _d(out), self.n_nodes))
+        return out
+
+    def apd90(self):
+        out = np.empty(self.n_nodes)
+        _check(lib().tc_apd90(self._h, _d(out), self.n_nodes))
         return out
 
     @property

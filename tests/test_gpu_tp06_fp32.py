@@ -93,3 +93,31 @@ def test_tp06_cell_types_and_errors():
         g.set_ionic(tc.TC_MODEL_TP06, [float(cell)])
         g.step(50)
         assert np.abs(g.read() - o.V).max() <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def tiny_tp06_beat():
+    # a 2x1x1 mm slab (45 nodes) through one full TP06 beat: 400 ms at dt = 0.02 ms
+    w = I.slab_custom(2.0, 1.0, 1.0, 0.5, dt=0.02, model="tp06", t_end=400.0)
+    o = Monodomain(w).run(w.n_steps)
+    g64 = tc.from_workload(w)
+    g64.step(w.n_steps)
+    g32 = tc.from_workload(w, precision=tc.TC_FP32)
+    g32.step(w.n_steps)
+    return w, o, g64, g32
+
+
+def test_repolarisation_parity_fp64(tiny_tp06_beat):
+    w, o, g, _ = tiny_tp06_beat
+    assert np.all(o.apd90() > 200.0) and np.all(o.lrt > 0.0)
+    assert np.abs(g.activation_times() - o.act).max() <= 1e-6
+    assert np.abs(g.repolarisation_times() - o.lrt).max() <= 1e-6
+    assert np.abs(g.apd90() - o.apd90()).max() <= 1e-6
+
+
+def test_fp32_form_apd90_within_two_percent(tiny_tp06_beat):
+    w, o, _, g = tiny_tp06_beat
+    apd_o, apd_g = o.apd90(), g.apd90()
+    assert np.all(apd_g > 0.0)
+    assert np.abs(apd_g - apd_o).max() <= 0.02 * apd_o.max()
+    assert np.abs(g.activation_times() - o.act).max() <= 1.0

@@ -137,3 +137,30 @@ def test_small_slab_wave_speed_ratio():
     assert np.all(s.act >= 0.0)
     assert 0.85 * np.sqrt(0.17 / 0.019) < cx / cy < 1.15 * np.sqrt(0.17 / 0.019)
     assert max(s.iters) < 1000 and all(s.converged)
+
+
+def test_repolarisation_capture_on_piecewise_linear_ap():
+    # V rises from -85 to +20 mV over 2 ms, then falls at 1.05 mV/ms back to -85 mV.
+    # Activation (0 mV) at 2*85/105 ms; 90 % repolarisation level -85 + 0.1*105 = -74.5 mV
+    # crossed at 2 + 94.5/1.05 = 92 ms; LRT level -70 mV at 2 + 90/1.05 ms.
+    from oracle.monodomain import capture_repolarisation
+
+    def v(t):
+        return np.where(t <= 2.0, -85.0 + 52.5 * t, 20.0 - 1.05 * (t - 2.0))
+
+    dt = 0.01
+    act = np.full(1, -1.0)
+    vpeak = np.full(1, -85.0)
+    rep90 = np.full(1, -1.0)
+    lrt = np.full(1, -1.0)
+    for k in range(12000):
+        vo, vn = v(np.array([k * dt])), v(np.array([(k + 1) * dt]))
+        before = act.copy()
+        capture(act, vo, vn, k * dt, dt, 0.0)
+        if before[0] < 0 <= act[0]:
+            vpeak[:] = vn
+        capture_repolarisation(before, vpeak, rep90, lrt, vo, vn, k * dt, dt, -85.0, -70.0)
+    assert abs(act[0] - 170.0 / 105.0) < 1e-9
+    assert abs(vpeak[0] - 20.0) < 1e-9
+    assert abs(rep90[0] - 92.0) < 1e-9
+    assert abs(lrt[0] - (2.0 + 90.0 / 1.05)) < 1e-9
