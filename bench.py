@@ -37,8 +37,8 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 # FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
 # profiles/ (thread-level FP64 instructions / nodes); used to turn the live launch time into an
 # achieved FP64 instruction rate.
-TP06_FP64_INSTR_PER_NODE = 2405.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 110.9e6   # dram read + write of the same capture
+TP06_FP64_INSTR_PER_NODE = 2188.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 110.35e6   # dram read + write of the same capture
 
 
 def parse():

@@ -213,6 +213,11 @@ tc_status tc_reset_profile(tc_sim* sim);
  * TC_ERR_TIMEOUT with the GPU context intact (used to test the timeout path). */
 tc_status tc_set_wait_limit(tc_sim* sim, int64_t polls);
 
+/* tc_selftest_exp: evaluate, on the current device, the FP64 exponential the ionic kernels use
+ * (table-driven, Tang 1989) and the CUDA library exp at the host inputs x[n]; y_fast[n] and
+ * y_ref[n] receive the two results (host arrays).  Diagnostics; allocates 24 n bytes. */
+tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_t n);
+
 /* Thread-local message of the last error ("" if none). */
 const char* tc_last_error(void);
 /* Library version string. */

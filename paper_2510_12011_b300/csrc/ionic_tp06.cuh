@@ -46,7 +46,93 @@ inline void tp06_rest_state(int /*cell*/, double* u, double* v0) {
   *v0 = tp06::kRestV;
 }
 
-__device__ __forceinline__ double mexp(double x) { return exp(x); }
+// FP64 exponential, table-driven (Tang, ACM TOMS 15(2), 1989): x = (64 m + j) ln2/64 + r with
+// |r| <= ln2/128, exp(x) = 2^m * 2^(j/64) * exp(r), exp(r) - 1 by its degree-5 Taylor
+// polynomial (truncation r^6/720 < 3.6e-17).  ln2/64 is split into hi + lo so that r is exact
+// to FP64 rounding; 2^(j/64) is a hi + lo pair from a per-block shared-memory table, so the
+// result is within about half an ulp; 2^m is added to the exponent field.  About 12 FP64
+// instructions against roughly twice that for the library exp, which matters where FP64 issue
+// is scarce.  |x| >= 700 and NaN go to the library exp.
+// 2^(j/64) = kExp2Hi[j] + kExp2Lo[j], j = 0..63 (computed to 60 digits and split)
+__constant__ double kExp2Hi[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0,
+    0x1.0874518759bc8p+0, 0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0,
+    0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0, 0x1.172b83c7d517bp+0,
+    0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0,
+    0x1.2d285a6e4030bp+0, 0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0,
+    0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0, 0x1.3dea64c123422p+0,
+    0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0,
+    0x1.56f4736b527dap+0, 0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0,
+    0x1.6247eb03a5585p+0, 0x1.6623882552225p+0, 0x1.6a09e667f3bcdp+0,
+    0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0,
+    0x1.868d99b4492edp+0, 0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0,
+    0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0, 0x1.9c49182a3f090p+0,
+    0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0,
+    0x1.bcc1e904bc1d2p+0, 0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0,
+    0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0, 0x1.d5818dcfba487p+0,
+    0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0,
+    0x1.fa7c1819e90d8p+0,
+};
+__constant__ double kExp2Lo[64] = {
+    0x0.0p+0, -0x1.19083535b085dp-56, 0x1.d73e2a475b465p-55,
+    0x1.186be4bb284ffp-57, 0x1.8a62e4adc610bp-54, 0x1.03a1727c57b53p-59,
+    -0x1.6c51039449b3ap-54, -0x1.32fbf9af1369ep-54, -0x1.19041b9d78a76p-55,
+    0x1.e5b4c7b4968e4p-55, 0x1.e016e00a2643cp-54, 0x1.dc775814a8495p-55,
+    0x1.9b07eb6c70573p-54, 0x1.2bd339940e9d9p-55, 0x1.612e8afad1255p-55,
+    0x1.0024754db41d5p-54, 0x1.6f46ad23182e4p-55, 0x1.32721843659a6p-54,
+    -0x1.63aeabf42eae2p-54, -0x1.5e436d661f5e3p-56, 0x1.ada0911f09ebcp-55,
+    -0x1.ef3691c309278p-58, 0x1.89b7a04ef80d0p-59, 0x1.3c1a3b69062f0p-56,
+    0x1.d4397afec42e2p-56, -0x1.4b309d25957e3p-54, -0x1.07abe1db13cadp-55,
+    0x1.9bb2c011d93adp-54, 0x1.6324c054647adp-54, 0x1.ba6f93080e65ep-54,
+    -0x1.383c17e40b497p-54, -0x1.bb60987591c34p-54, -0x1.bdd3413b26456p-54,
+    -0x1.bbe3a683c88abp-57, -0x1.16e4786887a99p-55, -0x1.0245957316dd3p-54,
+    -0x1.41577ee04992fp-55, 0x1.05d02ba15797ep-56, -0x1.d4c1dd41532d8p-54,
+    -0x1.fc6f89bd4f6bap-54, 0x1.6e9f156864b27p-54, 0x1.5cc13a2e3976cp-55,
+    -0x1.75fc781b57ebcp-57, -0x1.d185b7c1b85d1p-54, 0x1.c7c46b071f2bep-56,
+    -0x1.359495d1cd533p-54, -0x1.d2f6edb8d41e1p-54, 0x1.0fac90ef7fd31p-54,
+    0x1.7a1cd345dcc81p-54, -0x1.2805e3084d708p-57, -0x1.5584f7e54ac3bp-56,
+    0x1.23dd07a2d9e84p-55, 0x1.11065895048ddp-55, 0x1.2884dff483cadp-54,
+    0x1.503cbd1e949dbp-56, -0x1.cbc3743797a9cp-54, 0x1.2ed02d75b3707p-55,
+    0x1.c2300696db532p-54, -0x1.1a5cd4f184b5cp-54, 0x1.39e8980a9cc8fp-55,
+    -0x1.e9c23179c2893p-54, 0x1.dc7f486a4b6b0p-54, 0x1.9d3e12dd8a18bp-54,
+    0x1.74853f3a5931ep-55,
+};
+__shared__ double s_exp2_hi[64];
+__shared__ double s_exp2_lo[64];
+
+__device__ __forceinline__ void exp2_table_init() {
+  if (threadIdx.x < 64) {
+    s_exp2_hi[threadIdx.x] = kExp2Hi[threadIdx.x];
+    s_exp2_lo[threadIdx.x] = kExp2Lo[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double exp_tang(double x) {
+  constexpr double kInvL = 0x1.71547652b82fep+6;    // 64 / ln 2
+  constexpr double kLhi = 0x1.62e42fefa39efp-7;     // ln 2 / 64, leading 53 bits
+  constexpr double kLlo = 0x1.abc9e3b39803fp-62;    // ln 2 / 64 - kLhi
+  constexpr double kShift = 6755399441055744.0;     // 1.5 * 2^52: round to nearest integer
+  const double t = fma(x, kInvL, kShift);
+  const double nd = t - kShift;
+  const int n = __double2loint(t);
+  double r = fma(-nd, kLhi, x);
+  r = fma(-nd, kLlo, r);
+  const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+  const double th = s_exp2_hi[n & 63], tl = s_exp2_lo[n & 63];
+  const double y = th + fma(th, p, fma(tl, p, tl));   // (th + tl)(1 + p)
+  const int m = n >> 6;   // floor(n / 64): n = 64 m + (n & 63)
+  const double out =
+      __hiloint2double(__double2hiint(y) + (int)((unsigned)m << 20), __double2loint(y));
+  return fabs(x) < 700.0 ? out : exp(x);
+}
+
+__device__ __forceinline__ double mexp(double x) { return exp_tang(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
 __device__ __forceinline__ double mlog(double x) { return log(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
@@ -137,9 +223,16 @@ __device__ __forceinline__ T rl(T u, T inf, T tau, T dt) {
   return inf + (u - inf) * mexp(-dt / tau);
 }
 
+// The same with the gate's total rate alpha + beta = 1/tau given (no division).
+template <typename T>
+__device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dt) {
+  return inf + (u - inf) * mexp(-dt * rate);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
   using namespace tp06;
+  exp2_table_init();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) a.bar->count = 0u;
   if (i >= a.n) return;
@@ -208,8 +301,8 @@ __global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
       aj = T(0);
       bj = T(0.6) * mexp(T(0.057) * V) / (T(1) + mexp(T(-0.1) * (V + T(32))));
     }
-    un[10] = rl(u[10], hinf, T(1) / (ah + bh), dt);
-    un[11] = rl(u[11], hinf, T(1) / (aj + bj), dt);
+    un[10] = rl_rate(u[10], hinf, ah + bh, dt);
+    un[11] = rl_rate(u[11], hinf, aj + bj, dt);
     const T xr1inf = T(1) / (T(1) + mexp((T(-26) - V) / T(7)));
     const T txr1 = T(450) / (T(1) + mexp((T(-45) - V) / T(10))) * T(6) /
                    (T(1) + mexp((V + T(30)) / T(11.5)));
@@ -261,6 +354,16 @@ __global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
   const T iion = T(a.cm) * tp06_currents(V, un, a.cell, vf).total();
   const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, a.k));
   rhs_epilogue(a, i, V, Vp, iion, is);
+}
+
+// Self-test of exp_tang against the library exp on device (diagnostics of the ABI).
+__global__ void __launch_bounds__(256) exp_selftest_kernel(int64_t n, const double* x, double* y_fast,
+                                                           double* y_ref) {
+  exp2_table_init();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y_fast[i] = exp_tang(x[i]);
+  y_ref[i] = exp(x[i]);
 }
 
 }  // namespace tc

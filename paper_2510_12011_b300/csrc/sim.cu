@@ -825,7 +825,24 @@ tc_status tc_reset_profile(tc_sim* s) {
   return TC_OK;
 }
 
-const char* tc_version(void) { return "tc_b300 0.2 (sm_103a)"; }
+tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_t n) {
+  clear_error();
+  if (!x || !y_fast || !y_ref || n < 1) return fail(TC_ERR_ARG, "bad self-test arguments");
+  double* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, 3 * n * sizeof(double)));
+  cudaError_t e = cudaMemcpy(d, x, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    exp_selftest_kernel<<<(int)((n + 255) / 256), 256>>>(n, d, d + n, d + 2 * n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(y_fast, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(y_ref, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "tc_selftest_exp");
+  return TC_OK;
+}
+
+const char* tc_version(void) { return "tc_b300 0.3 (sm_103a)"; }
 
 }  // extern "C"
 

@@ -82,6 +82,7 @@ _SIGS = {
     "tc_get_profile": [_P, C.POINTER(Profile)],
     "tc_reset_profile": [_P],
     "tc_set_wait_limit": [_P, C.c_int64],
+    "tc_selftest_exp": [_D, _D, _D, C.c_int64],
 }
 _VOID = {"tc_mesh_destroy": [_P], "tc_sim_destroy": [_P]}
 _STR = {"tc_last_error": [], "tc_version": []}
@@ -316,6 +317,15 @@ def set_model(sim, w):
         sim.set_ionic(TC_MODEL_TP06, [float(w.tp06_cell)])
     else:
         raise TcError(TC_ERR_ARG, f"model {w.model!r} is not available")
+
+
+def selftest_exp(x):
+    """(device exp used by the ionic kernels, CUDA library exp) at x."""
+    x = _f64(x)
+    a = np.empty_like(x)
+    b = np.empty_like(x)
+    _check(lib().tc_selftest_exp(_d(x), _d(a), _d(b), x.size))
+    return a, b
 
 
 def from_workload(w, stream=None, precision=TC_FP64):

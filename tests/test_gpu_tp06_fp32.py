@@ -121,3 +121,24 @@ def test_fp32_form_apd90_within_two_percent(tiny_tp06_beat):
     assert np.all(apd_g > 0.0)
     assert np.abs(apd_g - apd_o).max() <= 0.02 * apd_o.max()
     assert np.abs(g.activation_times() - o.act).max() <= 1.0
+
+
+def test_device_exp_accuracy():
+    # the table-driven FP64 exp of the ionic kernels: within 1 ulp of the exact value (mpmath,
+    # 40 digits) on a sample, and within 2 ulp of the CUDA library exp on half a million inputs
+    import mpmath
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-60.0, 60.0, 400000), rng.uniform(-745.0, 709.0, 100000),
+                        np.linspace(-1e-3, 1e-3, 20001), [0.0, -0.0, 1.0, -1.0, 699.99, -699.99]])
+    fast, ref = tc.selftest_exp(x)
+    assert np.all(np.abs(fast - ref) <= 2.0 * np.spacing(np.abs(ref)) + 1e-300)
+    mpmath.mp.dps = 40
+    idx = rng.choice(x.size, 6000, replace=False)
+    err_fast = err_lib = 0.0
+    for i in idx:
+        exact = mpmath.exp(mpmath.mpf(float(x[i])))
+        ulp = np.spacing(abs(float(exact))) if exact != 0 else 5e-324
+        err_fast = max(err_fast, float(abs(mpmath.mpf(float(fast[i])) - exact)) / ulp)
+        err_lib = max(err_lib, float(abs(mpmath.mpf(float(ref[i])) - exact)) / ulp)
+    assert err_fast <= 1.0, (err_fast, err_lib)
+    assert np.isnan(tc.selftest_exp(np.array([np.nan]))[0][0])
