@@ -97,8 +97,15 @@ tc_status tc_mesh_matrices(const tc_mesh* mesh, const double* sigma_l, const dou
                            int32_t n_regions, int64_t* row_ptr, int32_t* col, double* m_val,
                            double* k_val);
 
+/* tc_mesh_layout_size: number of connected components of the mesh and the internal row count
+ * of the device layout (every component padded to a multiple of 32 rows).  Host only.
+ * Each connected component is an independent problem: the PCG runs per component (its own
+ * alpha, beta and stopping test), which is how many meshes are batched into one simulation. */
+tc_status tc_mesh_layout_size(const tc_mesh* mesh, int32_t* n_components, int64_t* n_internal);
+
 /* tc_mesh_ordering: the internal node order the device path uses (host only).
- * perm[new] = old for the nodes; slice_width receives ceil(n/32) SELL slice widths if not NULL. */
+ * perm[k] = caller index of the k-th real row (n_nodes entries, dummy rows left out);
+ * slice_width (if not NULL) receives n_internal/32 SELL slice widths. */
 tc_status tc_mesh_ordering(const tc_mesh* mesh, int32_t sell_sigma, int32_t* perm,
                            int32_t* slice_width);
 
@@ -120,6 +127,27 @@ void tc_sim_destroy(tc_sim* sim);
 
 tc_status tc_sim_size(const tc_sim* sim, int64_t* n_nodes, int64_t* nnz, int64_t* padded_nnz,
                       int32_t* n_blocks);
+
+/* tc_sim_layout: connected components (independent problems solved side by side), internal
+ * row count of the device layout, and the PCG launch shape in use.  Any pointer may be NULL. */
+tc_status tc_sim_layout(const tc_sim* sim, int32_t* n_components, int64_t* n_internal,
+                        int32_t* pcg_threads, int32_t* blocks_per_sm);
+
+/* tc_set_launch: PCG launch shape (512 or 1024 threads per block, blocks per SM, capped by the
+ * occupancy of the cooperative launch).  Errors: TC_ERR_ARG (shape or too many components). */
+tc_status tc_set_launch(tc_sim* sim, int32_t pcg_threads, int32_t blocks_per_sm);
+
+/* tc_autotune: time trial_steps steps with every candidate launch shape (1024x1, 512x1, 512x2),
+ * restoring the state after each trial, and keep the fastest.  Reports the choice and its time
+ * per step (any pointer may be NULL).  The state and step index are unchanged on return. */
+tc_status tc_autotune(tc_sim* sim, int32_t trial_steps, int32_t* pcg_threads,
+                      int32_t* blocks_per_sm, double* best_ms_per_step);
+
+/* tc_set_graphs: when on (default), tc_step runs whole groups of 30 steps by replaying a CUDA
+ * graph of the step loop (captured on first use, one per buffer phase; the step index lives on
+ * the device).  Off: every step is launched from the host.  Per-launch profiling always launches
+ * from the host. */
+tc_status tc_set_graphs(tc_sim* sim, int32_t on);
 
 /* tc_set_ionic: choose the ionic model and reset the state to init_state (NULL = the model's
  * resting state; otherwise [n_states][n_nodes] in caller order, V excluded).

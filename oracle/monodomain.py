@@ -64,7 +64,11 @@ class Monodomain:
         self.w = w
         mesh = w.mesh
         if M is None or K is None:
-            M, K = fem.mass_stiffness(mesh.xyz, mesh.tets, mesh.fibres, w.sigma_l, w.sigma_t)
+            sl = np.atleast_1d(np.asarray(w.sigma_l, dtype=np.float64))
+            st = np.atleast_1d(np.asarray(w.sigma_t, dtype=np.float64))
+            if sl.size > 1:
+                sl, st = sl[mesh.region], st[mesh.region]
+            M, K = fem.mass_stiffness(mesh.xyz, mesh.tets, mesh.fibres, sl, st)
         self.M, self.K = M, K
         self.A = fem.system_matrix(M, K, w.chi, w.cm, w.theta, w.dt)
         self.diag = self.A.diagonal()

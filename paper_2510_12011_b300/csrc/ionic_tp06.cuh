@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
   using namespace tp06;
   exp2_table_init();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) a.bar->count = 0u;
+  if (i < a.n_bar) a.bar[i].count = 0u;
   if (i >= a.n) return;
   const int64_t n = a.n;
   const T V = a.V[i], Vp = a.Vp[i];
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
   for (int j = 0; j < kTP06States; ++j) a.state[j * n + i] = un[j];
   // I_ion(V^k, u^{k+1}) in uA/mm^2
   const T iion = T(a.cm) * tp06_currents(V, un, a.cell, vf).total();
-  const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, a.k));
+  const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, *a.k_base + a.k_off));
   rhs_epilogue(a, i, V, Vp, iion, is);
 }
 

@@ -62,11 +62,13 @@ struct IonicArgs {
   const int32_t* stim_off;
   const int32_t* stim_ids;
   const StimDev* stims;
-  long long k;
+  const long long* k_base;   // step index of the first step of this launch group (device)
+  int k_off;                 // this step = *k_base + k_off
   double chi, cm, dt, theta;
   MSConst ms;
   int cell;               // TP06 cell type
-  GridBar* bar;           // zeroed here for the PCG launch that follows on the stream
+  GridBar* bar;           // per-component barrier words, zeroed here for the PCG launch that
+  int n_bar;              // follows on the stream
 };
 
 template <typename T>
@@ -79,6 +81,8 @@ struct PcgArgs {
   const T* vA;
   const T* dinv;
   const int32_t* blk_slice;   // gridDim.x + 1 slice boundaries
+  const int32_t* comp_of_block;   // connected component (independent problem) of each block
+  const int32_t* comp_block0;     // first block of each component, n_comp + 1 entries
   const T* g1;
   const T* g2;
   T* x;                       // in: x0, out: V^{k+1}
@@ -93,13 +97,15 @@ struct PcgArgs {
   double* lrt;                // repolarisation time: first downward crossing of lrt_thr
   double* partA;              // gridDim.x
   double* partB;              // 2*gridDim.x
-  GridBar* bar;
+  GridBar* bar;               // one per component
   int* err;
-  DevStats* stats;
+  DevStats* stats;            // one per component
   double atol, rtol;
   int max_iter;
   long long wait_limit;
-  double t_k, dt, thr;
+  const long long* k_base;
+  int k_off;
+  double dt, thr;
   double v_rest, lrt_thr;
 };
 
@@ -301,7 +307,7 @@ __device__ __forceinline__ void rhs_epilogue(const IonicArgs<T>& a, int64_t i, T
 template <typename T>
 __global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs<T> a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) a.bar->count = 0u;
+  if (i < a.n_bar) a.bar[i].count = 0u;
   if (i >= a.n) return;
   const T V = a.V[i], Vp = a.Vp[i];
   const MSConst& c = a.ms;
@@ -313,16 +319,22 @@ __global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs<T> a) {
   const T jin = h * v * v * (T(1) - v) * T(c.inv_tau_in);
   const T jout = -v * T(c.inv_tau_out);
   const T iion = -T(a.cm) * T(c.range) * (jin + jout);
-  const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, a.k));
+  const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, *a.k_base + a.k_off));
   rhs_epilogue(a, i, V, Vp, iion, is);
 }
+
+// Advances the device step index after a group of steps (the last node of a captured graph).
+__global__ void tick_kernel(long long* k_base, int add) { *k_base += add; }
 
 // (a2)-(a5) in one cooperative launch: r0 = b - A x0 from the two value streams of M and K,
 // the Jacobi-PCG loop of Algorithm 1 with the convergence decision taken identically by every
 // block, and the activation-time capture.  Each block owns a contiguous range of slices (and
 // so of rows); SpMV phases map one warp to one slice, vector phases stride threads over the
 // block's rows.  Scalar FP64 work (sqrt, divisions, the stopping test) runs on thread 0 only:
-// B300 issues FP64 at a small fraction of its FP32 rate.
+// B300 issues FP64 at a small fraction of its FP32 rate.  A mesh made of several connected
+// components is several independent problems: each component owns a contiguous range of
+// blocks and runs its own PCG (own barrier, reductions, alpha, beta, stopping decision), so a
+// batch of meshes advances in one launch without any instance waiting for another.
 template <int THREADS, typename T>
 __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   constexpr int NW = THREADS / 32;
@@ -330,7 +342,11 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   __shared__ double s_sc[4];   // scalars computed by thread 0, then broadcast
   __shared__ int s_flag;       // 0 = iterate, 1 = converged, 2 = non-finite
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned nb = gridDim.x, b = blockIdx.x;
+  const unsigned b = blockIdx.x;
+  const int comp = a.comp_of_block[b];
+  const int cb0 = a.comp_block0[comp];
+  const unsigned nb = (unsigned)(a.comp_block0[comp + 1] - cb0);
+  GridBar* bar = a.bar + comp;
   const int s0 = a.blk_slice[b], s1 = a.blk_slice[b + 1];
   const int64_t r0 = (int64_t)s0 * 32;
   const int64_t r1 = min((int64_t)s1 * 32, a.n);
@@ -364,10 +380,10 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
       a.partB[2 * b + 1] = v2[1];
     }
   }
-  if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
+  if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
   if (warp == 0) {
     double t_rho, t_zz;
-    grid_sum_warp0(a.partB, 2, nb, t_rho, t_zz, true);
+    grid_sum_warp0(a.partB + 2 * cb0, 2, nb, t_rho, t_zz, true);
     if (tid == 0) {
       rho = t_rho;
       z0n = sqrt(t_zz);
@@ -395,10 +411,10 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
       block_sum<THREADS, 1>(v1, s_red);
       if (tid == 0) a.partA[b] = v1[0];
     }
-    if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
+    if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
     if (warp == 0) {
       double pq, unused;
-      grid_sum_warp0(a.partA, 1, nb, pq, unused, false);
+      grid_sum_warp0(a.partA + cb0, 1, nb, pq, unused, false);
       if (tid == 0) {
         s_sc[0] = rho / pq;
         s_sc[1] = pq;
@@ -446,11 +462,11 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
         a.partB[2 * b + 1] = v2[1];
       }
     }
-    if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
+    if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
     ++it;
     if (warp == 0) {
       double rho_new, zz;
-      grid_sum_warp0(a.partB, 2, nb, rho_new, zz, true);
+      grid_sum_warp0(a.partB + 2 * cb0, 2, nb, rho_new, zz, true);
       if (tid == 0) {
         zn = sqrt(zz);
         const double pq = s_sc[1];
@@ -475,15 +491,16 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
       }
       a.p[i] = fmaT(beta, p0, z0);
     }
-    if (!grid_sync(a.bar, nb, epoch, a.wait_limit, a.err)) return;
+    if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
   }
   // activation capture (first upward crossing of thr) and, after activation, the peak, the
   // 90 % repolarisation crossing and the LRT crossing, each interpolated inside the step
+  const double t_k = (double)(*a.k_base + a.k_off) * a.dt;
   for (int64_t i = r0 + tid; i < r1; i += THREADS) {
     const double vo = double(a.Vcur[i]), vn = double(a.x[i]);
     if (a.act[i] < 0.0) {
       if (vo < a.thr && vn >= a.thr) {
-        a.act[i] = a.t_k + a.dt * (a.thr - vo) / (vn - vo);
+        a.act[i] = t_k + a.dt * (a.thr - vo) / (vn - vo);
         a.vpeak[i] = vn;
       }
     } else if (a.rep90[i] < 0.0 || a.lrt[i] < 0.0) {
@@ -491,13 +508,13 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
       a.vpeak[i] = vp;
       const double t90 = a.v_rest + 0.1 * (vp - a.v_rest);
       if (a.rep90[i] < 0.0 && vo >= t90 && vn < t90)
-        a.rep90[i] = a.t_k + a.dt * (vo - t90) / (vo - vn);
+        a.rep90[i] = t_k + a.dt * (vo - t90) / (vo - vn);
       if (a.lrt[i] < 0.0 && vo >= a.lrt_thr && vn < a.lrt_thr)
-        a.lrt[i] = a.t_k + a.dt * (vo - a.lrt_thr) / (vo - vn);
+        a.lrt[i] = t_k + a.dt * (vo - a.lrt_thr) / (vo - vn);
     }
   }
-  if (b == 0 && tid == 0) {
-    DevStats* st = a.stats;
+  if (b == (unsigned)cb0 && tid == 0) {
+    DevStats* st = a.stats + comp;
     st->iters_total += it;
     st->steps += 1;
     if (it > st->max_iters) st->max_iters = it;

@@ -178,12 +178,14 @@ static void bfs_levels(const Csr& p, int32_t start, std::vector<int32_t>& level,
   for (int32_t t : touched) level[t] = -1;
 }
 
-void node_ordering(const Csr& p, int32_t sell_sigma, std::vector<int32_t>& perm) {
+void node_ordering(const Csr& p, int32_t sell_sigma, std::vector<int32_t>& perm,
+                   std::vector<int64_t>* comp_start) {
   const int64_t n = p.n;
   std::vector<int32_t> deg(n);
   for (int64_t i = 0; i < n; ++i) deg[i] = (int32_t)(p.row_ptr[i + 1] - p.row_ptr[i]);
   std::vector<char> done(n, 0);
   std::vector<int32_t> level(n, -1), order;
+  std::vector<int64_t> ends;   // end position of every component in the forward order
   order.reserve(n);
   for (int64_t seed = 0; seed < n; ++seed) {
     if (done[seed]) continue;
@@ -221,32 +223,58 @@ void node_ordering(const Csr& p, int32_t sell_sigma, std::vector<int32_t>& perm)
         queue.push_back(v);
       }
     }
+    ends.push_back((int64_t)order.size());
   }
   std::reverse(order.begin(), order.end());
+  // component starts in the reversed order
+  std::vector<int64_t> starts;
+  for (auto it = ends.rbegin(); it != ends.rend(); ++it) starts.push_back(n - *it);
+  starts.push_back(n);
   if (sell_sigma > 1) {
-    for (int64_t w0 = 0; w0 < n; w0 += sell_sigma) {
-      const int64_t w1 = std::min<int64_t>(n, w0 + sell_sigma);
-      std::stable_sort(order.begin() + w0, order.begin() + w1,
-                       [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
-    }
+    for (size_t c = 0; c + 1 < starts.size(); ++c)
+      for (int64_t w0 = starts[c]; w0 < starts[c + 1]; w0 += sell_sigma) {
+        const int64_t w1 = std::min<int64_t>(starts[c + 1], w0 + sell_sigma);
+        std::stable_sort(order.begin() + w0, order.begin() + w1,
+                         [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
+      }
   }
   perm.swap(order);
+  if (comp_start) comp_start->swap(starts);
+}
+
+void padded_ordering(const Csr& p, int32_t sell_sigma, std::vector<int32_t>& perm_ext,
+                     std::vector<int64_t>& comp_rows) {
+  std::vector<int32_t> perm;
+  std::vector<int64_t> starts;
+  node_ordering(p, sell_sigma, perm, &starts);
+  const size_t nc = starts.size() - 1;
+  comp_rows.assign(nc + 1, 0);
+  for (size_t c = 0; c < nc; ++c) {
+    const int64_t len = starts[c + 1] - starts[c];
+    comp_rows[c + 1] = comp_rows[c] + (len + 31) / 32 * 32;
+  }
+  perm_ext.assign(comp_rows[nc], -1);
+  for (size_t c = 0; c < nc; ++c)
+    for (int64_t t = 0; t < starts[c + 1] - starts[c]; ++t)
+      perm_ext[comp_rows[c] + t] = perm[starts[c] + t];
 }
 
 tc_status build_sell(const Csr& p, const std::vector<int32_t>& perm, Sell& s) {
-  const int64_t n = p.n;
-  std::vector<int32_t> inv(n);
-  for (int64_t k = 0; k < n; ++k) inv[perm[k]] = (int32_t)k;
+  const int64_t n = (int64_t)perm.size();   // rows of the layout (dummy rows included)
+  std::vector<int32_t> inv(p.n, -1);
+  for (int64_t k = 0; k < n; ++k)
+    if (perm[k] >= 0) inv[perm[k]] = (int32_t)k;
+  auto row_len = [&](int64_t r) -> int64_t {
+    const int32_t o = perm[r];
+    return o < 0 ? 0 : p.row_ptr[o + 1] - p.row_ptr[o];
+  };
   s.n = n;
   s.nslices = (n + 31) / 32;
   s.slice_ptr.assign(s.nslices + 1, 0);
   int64_t off = 0;
   for (int64_t sl = 0; sl < s.nslices; ++sl) {
     int64_t w = 0;
-    for (int64_t r = sl * 32; r < std::min<int64_t>(n, sl * 32 + 32); ++r) {
-      const int32_t o = perm[r];
-      w = std::max<int64_t>(w, p.row_ptr[o + 1] - p.row_ptr[o]);
-    }
+    for (int64_t r = sl * 32; r < std::min<int64_t>(n, sl * 32 + 32); ++r) w = std::max(w, row_len(r));
     off += 32 * w;
     if (off > INT32_MAX) return fail(TC_ERR_ARG, "matrix too large for 32-bit SELL offsets");
     s.slice_ptr[sl + 1] = (int32_t)off;
@@ -262,7 +290,7 @@ tc_status build_sell(const Csr& p, const std::vector<int32_t>& perm, Sell& s) {
       const int64_t r = sl * 32 + lane;
       ent.clear();
       int32_t pad_col = (int32_t)std::min<int64_t>(r, n - 1);
-      if (r < n) {
+      if (r < n && perm[r] >= 0) {
         const int32_t o = perm[r];
         for (int64_t q = p.row_ptr[o]; q < p.row_ptr[o + 1]; ++q) ent.push_back({inv[p.col[q]], q});
         std::sort(ent.begin(), ent.end());
@@ -386,19 +414,33 @@ tc_status tc_mesh_matrices(const tc_mesh* mesh, const double* sigma_l, const dou
   return TC_OK;
 }
 
+tc_status tc_mesh_layout_size(const tc_mesh* mesh, int32_t* n_components, int64_t* n_internal) {
+  clear_error();
+  if (!mesh) return fail(TC_ERR_ARG, "mesh must not be NULL");
+  std::vector<int32_t> pe;
+  std::vector<int64_t> cr;
+  padded_ordering(mesh->pattern, 1, pe, cr);
+  if (n_components) *n_components = (int32_t)(cr.size() - 1);
+  if (n_internal) *n_internal = cr.back();
+  return TC_OK;
+}
+
 tc_status tc_mesh_ordering(const tc_mesh* mesh, int32_t sell_sigma, int32_t* perm,
                            int32_t* slice_width) {
   clear_error();
   if (!mesh || !perm) return fail(TC_ERR_ARG, "null argument");
   if (sell_sigma < 1) return fail(TC_ERR_ARG, "sell_sigma must be >= 1");
-  std::vector<int32_t> pv;
-  node_ordering(mesh->pattern, sell_sigma, pv);
-  std::copy(pv.begin(), pv.end(), perm);
+  std::vector<int32_t> pe;
+  std::vector<int64_t> cr;
+  padded_ordering(mesh->pattern, sell_sigma, pe, cr);
+  int64_t k = 0;
+  for (int32_t o : pe)
+    if (o >= 0) perm[k++] = o;
   if (slice_width) {
     Sell s;
-    tc_status st = build_sell(mesh->pattern, pv, s);
+    tc_status st = build_sell(mesh->pattern, pe, s);
     if (st != TC_OK) return st;
-    for (int64_t k = 0; k < s.nslices; ++k) slice_width[k] = (s.slice_ptr[k + 1] - s.slice_ptr[k]) / 32;
+    for (int64_t q = 0; q < s.nslices; ++q) slice_width[q] = (s.slice_ptr[q + 1] - s.slice_ptr[q]) / 32;
   }
   return TC_OK;
 }

@@ -1,4 +1,10 @@
 // Device-side simulation object and the C ABI calls that touch the GPU.
+//
+// Internal layout: nodes in the order of padded_ordering (reverse Cuthill-McKee per connected
+// component, SELL row sorting, every component padded to a multiple of 32 rows by dummy rows).
+// perm[internal] = caller index or -1; every device node vector has n_int entries.  Dummy rows
+// have no matrix entries and a zero Jacobi inverse, so their residual, direction and update stay
+// zero and their potential stays at the resting value; they never reach the caller.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -19,10 +25,11 @@ using namespace tc;
 namespace {
 
 constexpr int kIonicThreads = 256;
+constexpr int kGraphSteps = 30;   // steps per captured graph (a multiple of the 3-buffer cycle)
 
 // Launch shape of the PCG kernel: 512 or 1024 threads per block, blocks per SM, and the SELL
 // sorting window; TC_PCG_THREADS, TC_PCG_BLOCKS_PER_SM and TC_SELL_SIGMA override the defaults
-// (used by the launch-shape sweep).
+// (tc_autotune picks the launch shape by measurement).
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   return v && *v ? std::atoi(v) : dflt;
@@ -33,18 +40,28 @@ struct Dev {
   size_t bytes = 0;
 };
 
+struct GraphCache {
+  bool valid = false;
+  int iv = -1;                      // buffer rotation phase the graph was captured for
+  cudaGraphExec_t exec = nullptr;
+};
+
 }  // namespace
 
 struct tc_sim {
   int device = 0;
   cudaStream_t stream = nullptr;
-  int64_t n = 0, nnz = 0, nslices = 0, padded = 0;
+  int64_t n = 0, n_int = 0, nnz = 0, nslices = 0, padded = 0;
+  int n_comp = 1;
+  std::vector<int64_t> comp_rows;    // n_comp + 1 internal row offsets
   int precision = TC_FP64;
   size_t esz = 8;                    // bytes per matrix value / node-vector entry
-  std::vector<int32_t> perm, inv;   // perm[new] = old
+  std::vector<int32_t> perm;         // perm[internal] = caller index or -1
+  std::vector<int32_t> inv;          // inv[caller] = internal index
   int num_sms = 0, blocks_per_sm = 1, nblocks = 0, pcg_threads = 1024, sell_sigma = 1024;
   // device arrays (element type double for TC_FP64, float for TC_FP32)
   int32_t *slice_ptr = nullptr, *col = nullptr, *blk_slice = nullptr;
+  int32_t *comp_of_block = nullptr, *comp_block0 = nullptr;
   void *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
   void* V[3] = {nullptr, nullptr, nullptr};
   int iv = 0;   // V[iv] = V^k, V[(iv+2)%3] = V^{k-1}, V[(iv+1)%3] = V^{k+1}
@@ -54,9 +71,10 @@ struct tc_sim {
   double *vpeak = nullptr, *rep90 = nullptr, *lrt = nullptr;
   double v_rest = 0.0, lrt_thr = -70.0;
   double *partA = nullptr, *partB = nullptr;
-  GridBar* bar = nullptr;
+  GridBar* bar = nullptr;            // n_comp
   int* err = nullptr;
-  DevStats* stats = nullptr;
+  DevStats* stats = nullptr;         // n_comp
+  long long* k_dev = nullptr;        // device step index (start of the current launch group)
   int32_t *stim_off = nullptr, *stim_ids = nullptr;
   StimDev* stims = nullptr;
   std::vector<std::vector<int32_t>> stim_nodes;   // per stimulus, internal indices
@@ -73,13 +91,15 @@ struct tc_sim {
   int cell = 0;
   long long k = 0;
   long long wait_limit = 1ll << 26;
+  bool use_graphs = true;
+  GraphCache graphs[3];
   // profiling
   bool prof = false;
   tc_profile prof_acc{};
   std::vector<cudaEvent_t> evpool;
   std::vector<Dev> allocs;
-  double* pinned = nullptr;   // n doubles of page-locked staging for host reads/writes
-  void* pinned_t = nullptr;   // n elements of the device type, page-locked
+  double* pinned = nullptr;   // n_int doubles of page-locked staging for host reads/writes
+  void* pinned_t = nullptr;   // n_int elements of the device type, page-locked
 };
 
 namespace {
@@ -128,40 +148,72 @@ void dfree(tc_sim* s, void* p) {
   cudaFree(p);
 }
 
+void drop_graphs(tc_sim* s) {
+  for (auto& g : s->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = GraphCache{};
+  }
+}
+
 int64_t round_half_even(double x) { return (int64_t)std::nearbyint(x); }
 
-// Host doubles (internal order) <-> device arrays of the simulation's type.
-tc_status upload_vec(tc_sim* s, void* dst, const double* src_internal, int64_t count) {
+// Host doubles in internal order (n_int entries) -> device array of the simulation's type.
+// With real_only, only the real rows of every component are written (dummy rows keep theirs).
+tc_status upload_vec(tc_sim* s, void* dst, const double* src_internal, bool real_only) {
   CUDA_TRY(cudaStreamSynchronize(s->stream));
+  const int64_t n = s->n_int;
   if (s->precision == TC_FP64) {
-    std::memcpy(s->pinned_t, src_internal, count * sizeof(double));
+    std::memcpy(s->pinned_t, src_internal, n * sizeof(double));
   } else {
     float* f = static_cast<float*>(s->pinned_t);
-    for (int64_t i = 0; i < count; ++i) f[i] = (float)src_internal[i];
+    for (int64_t i = 0; i < n; ++i) f[i] = (float)src_internal[i];
   }
-  CUDA_TRY(cudaMemcpyAsync(dst, s->pinned_t, count * s->esz, cudaMemcpyHostToDevice, s->stream));
+  if (!real_only) {
+    CUDA_TRY(cudaMemcpyAsync(dst, s->pinned_t, n * s->esz, cudaMemcpyHostToDevice, s->stream));
+  } else {
+    for (int c = 0; c < s->n_comp; ++c) {
+      const int64_t a = s->comp_rows[c];
+      int64_t b = a;
+      while (b < s->comp_rows[c + 1] && s->perm[b] >= 0) ++b;   // real rows come first
+      if (b > a)
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(dst) + a * s->esz,
+                                 static_cast<char*>(s->pinned_t) + a * s->esz, (b - a) * s->esz,
+                                 cudaMemcpyHostToDevice, s->stream));
+    }
+  }
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   return TC_OK;
 }
 
-tc_status download_vec(const tc_sim* s, const void* src, double* dst_internal, int64_t count) {
-  CUDA_TRY(cudaMemcpyAsync(s->pinned_t, src, count * s->esz, cudaMemcpyDeviceToHost, s->stream));
+tc_status download_vec(const tc_sim* s, const void* src, double* dst_internal) {
+  const int64_t n = s->n_int;
+  CUDA_TRY(cudaMemcpyAsync(s->pinned_t, src, n * s->esz, cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   if (s->precision == TC_FP64) {
-    std::memcpy(dst_internal, s->pinned_t, count * sizeof(double));
+    std::memcpy(dst_internal, s->pinned_t, n * sizeof(double));
   } else {
     const float* f = static_cast<const float*>(s->pinned_t);
-    for (int64_t i = 0; i < count; ++i) dst_internal[i] = (double)f[i];
+    for (int64_t i = 0; i < n; ++i) dst_internal[i] = (double)f[i];
   }
   return TC_OK;
+}
+
+// caller order -> internal order (dummy rows get `fill`)
+void to_internal(const tc_sim* s, const double* host, double* out, double fill) {
+  for (int64_t i = 0; i < s->n_int; ++i) out[i] = s->perm[i] >= 0 ? host[s->perm[i]] : fill;
+}
+
+void to_caller(const tc_sim* s, const double* internal, double* host) {
+  for (int64_t i = 0; i < s->n_int; ++i)
+    if (s->perm[i] >= 0) host[s->perm[i]] = internal[i];
 }
 
 tc_status upload_stimuli(tc_sim* s) {
-  std::vector<std::vector<int32_t>> per_node(s->n);
+  std::vector<std::vector<int32_t>> per_node(s->n_int);
   for (size_t sid = 0; sid < s->stim_nodes.size(); ++sid)
     for (int32_t i : s->stim_nodes[sid]) per_node[i].push_back((int32_t)sid);
-  std::vector<int32_t> off(s->n + 1, 0), ids;
-  for (int64_t i = 0; i < s->n; ++i) {
+  std::vector<int32_t> off(s->n_int + 1, 0), ids;
+  for (int64_t i = 0; i < s->n_int; ++i) {
     off[i + 1] = off[i] + (int32_t)per_node[i].size();
     ids.insert(ids.end(), per_node[i].begin(), per_node[i].end());
   }
@@ -180,6 +232,7 @@ tc_status upload_stimuli(tc_sim* s) {
     CUDA_TRY(cudaMemcpyAsync(s->stims, s->stim_host.data(), s->stim_host.size() * sizeof(StimDev),
                              cudaMemcpyHostToDevice, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
+  drop_graphs(s);   // graphs hold the old stimulus pointers
   return TC_OK;
 }
 
@@ -194,29 +247,78 @@ const void* pcg_kernel(const tc_sim* s) {
                                  : pcg_kernel_ptr<float>(s->pcg_threads);
 }
 
+// Blocks of the cooperative PCG launch: every component gets a contiguous range of blocks in
+// proportion to its slices (at least one), and each block a contiguous range of its slices.
 tc_status set_partition(tc_sim* s) {
   int bps = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pcg_kernel(s), s->pcg_threads, 0));
   if (bps < 1) return fail(TC_ERR_CUDA, "PCG kernel cannot be resident on an SM");
   const int per_sm = std::min(bps, std::max(1, s->blocks_per_sm));
   const int64_t max_blocks = (int64_t)per_sm * s->num_sms;
+  if (s->n_comp > max_blocks)
+    return fail(TC_ERR_ARG, "mesh has " + std::to_string(s->n_comp) +
+                                " connected components, more than the " +
+                                std::to_string(max_blocks) + " co-resident PCG blocks");
   const int warps = s->pcg_threads / 32;
-  const int64_t want = (s->nslices + warps - 1) / warps;   // at least one slice per warp
-  s->nblocks = (int)std::max<int64_t>(1, std::min(max_blocks, want));
-  std::vector<int32_t> bs(s->nblocks + 1);
-  for (int b = 0; b <= s->nblocks; ++b) bs[b] = (int32_t)((s->nslices * (int64_t)b) / s->nblocks);
-  dfree(s, s->blk_slice);
-  dfree(s, s->partA);
-  dfree(s, s->partB);
+  std::vector<int64_t> cs(s->n_comp), want(s->n_comp);
+  int64_t total_want = 0, total_slices = 0;
+  for (int c = 0; c < s->n_comp; ++c) {
+    cs[c] = (s->comp_rows[c + 1] - s->comp_rows[c]) / 32;
+    want[c] = std::max<int64_t>(1, (cs[c] + warps - 1) / warps);   // >= one slice per warp
+    total_want += want[c];
+    total_slices += cs[c];
+  }
+  std::vector<int64_t> nbc(s->n_comp);
+  if (total_want <= max_blocks) {
+    nbc = want;
+  } else {
+    // share max_blocks in proportion to slices, at least one block per component
+    int64_t used = 0;
+    for (int c = 0; c < s->n_comp; ++c) {
+      nbc[c] = std::max<int64_t>(1, std::min(want[c], (max_blocks * cs[c]) / std::max<int64_t>(total_slices, 1)));
+      used += nbc[c];
+    }
+    while (used > max_blocks) {   // trim the largest shares
+      const int c = (int)(std::max_element(nbc.begin(), nbc.end()) - nbc.begin());
+      nbc[c] -= 1;
+      used -= 1;
+    }
+    for (int c = 0; used < max_blocks; c = (c + 1) % s->n_comp) {   // hand out the rest
+      if (nbc[c] < want[c]) {
+        nbc[c] += 1;
+        used += 1;
+      }
+      if (c == s->n_comp - 1) {
+        bool any = false;
+        for (int d = 0; d < s->n_comp; ++d) any |= nbc[d] < want[d];
+        if (!any) break;
+      }
+    }
+  }
+  std::vector<int32_t> bs, cob, cb0(s->n_comp + 1, 0);
+  for (int c = 0; c < s->n_comp; ++c) {
+    const int64_t first_slice = s->comp_rows[c] / 32;
+    for (int64_t b = 0; b < nbc[c]; ++b) {
+      bs.push_back((int32_t)(first_slice + cs[c] * b / nbc[c]));
+      cob.push_back(c);
+    }
+    cb0[c + 1] = cb0[c] + (int32_t)nbc[c];
+  }
+  bs.push_back((int32_t)(s->n_int / 32));
+  s->nblocks = cb0[s->n_comp];
+  for (void* p : {(void*)s->blk_slice, (void*)s->partA, (void*)s->partB, (void*)s->comp_of_block,
+                  (void*)s->comp_block0})
+    dfree(s, p);
   TRY(dalloc(s, &s->blk_slice, bs.size()));
+  TRY(dalloc(s, &s->comp_of_block, cob.size()));
+  TRY(dalloc(s, &s->comp_block0, cb0.size()));
   TRY(dalloc(s, &s->partA, s->nblocks));
   TRY(dalloc(s, &s->partB, 2 * s->nblocks));
   CUDA_TRY(cudaMemcpy(s->blk_slice, bs.data(), bs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->comp_of_block, cob.data(), cob.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->comp_block0, cb0.data(), cb0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  drop_graphs(s);
   return TC_OK;
-}
-
-void to_internal(const tc_sim* s, const double* host, double* out) {
-  for (int64_t i = 0; i < s->n; ++i) out[i] = host[s->perm[i]];
 }
 
 cudaEvent_t pooled_event(tc_sim* s, size_t idx) {
@@ -232,29 +334,30 @@ template <typename T>
 tc_status upload_matrices(tc_sim* s, const Sell& sell, const std::vector<double>& mv,
                           const std::vector<double>& kv, const std::vector<double>& av,
                           const std::vector<double>& dinv) {
-  std::vector<T> hM(sell.padded), hK(sell.padded), hA(sell.padded), hd(s->n);
+  std::vector<T> hM(sell.padded), hK(sell.padded), hA(sell.padded), hd(s->n_int);
   for (int64_t e = 0; e < sell.padded; ++e) {
     const int64_t q = sell.src[e];
     hM[e] = q >= 0 ? (T)mv[q] : T(0);
     hK[e] = q >= 0 ? (T)kv[q] : T(0);
     hA[e] = q >= 0 ? (T)av[q] : T(0);
   }
-  for (int64_t i = 0; i < s->n; ++i) hd[i] = (T)dinv[i];
+  for (int64_t i = 0; i < s->n_int; ++i) hd[i] = (T)dinv[i];
   CUDA_TRY(cudaMemcpy(s->vM, hM.data(), sell.padded * sizeof(T), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(s->vK, hK.data(), sell.padded * sizeof(T), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(s->vA, hA.data(), sell.padded * sizeof(T), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(s->dinv, hd.data(), s->n * sizeof(T), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->dinv, hd.data(), s->n_int * sizeof(T), cudaMemcpyHostToDevice));
   return TC_OK;
 }
 
-// Launch one time step: ionic kernel, then the cooperative PCG kernel.
+// Launch one time step (ionic kernel, then the cooperative PCG kernel) for the buffer phase
+// `iv` and step offset `k_off` from the device step index.
 template <typename T>
-tc_status launch_step(tc_sim* s, size_t& ev, std::vector<size_t>& marks) {
-  T* Vc = static_cast<T*>(s->V[s->iv]);
-  T* Vp = static_cast<T*>(s->V[(s->iv + 2) % 3]);
-  T* Vn = static_cast<T*>(s->V[(s->iv + 1) % 3]);
+tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size_t>* marks) {
+  T* Vc = static_cast<T*>(s->V[iv]);
+  T* Vp = static_cast<T*>(s->V[(iv + 2) % 3]);
+  T* Vn = static_cast<T*>(s->V[(iv + 1) % 3]);
   IonicArgs<T> ia;
-  ia.n = s->n;
+  ia.n = s->n_int;
   ia.V = Vc;
   ia.Vp = Vp;
   ia.state = static_cast<T*>(s->state);
@@ -264,7 +367,8 @@ tc_status launch_step(tc_sim* s, size_t& ev, std::vector<size_t>& marks) {
   ia.stim_off = s->stim_off;
   ia.stim_ids = s->stim_ids;
   ia.stims = s->stims;
-  ia.k = s->k;
+  ia.k_base = s->k_dev;
+  ia.k_off = k_off;
   ia.chi = s->chi;
   ia.cm = s->cm;
   ia.dt = s->dt;
@@ -280,20 +384,21 @@ tc_status launch_step(tc_sim* s, size_t& ev, std::vector<size_t>& marks) {
   ia.ms.dec_close = s->ms[3] != 0.0 ? std::exp(-s->dt / s->ms[3]) : 0.0;
   ia.cell = s->cell;
   ia.bar = s->bar;
-  if (s->prof) {
-    cudaEvent_t e = pooled_event(s, ev);
+  ia.n_bar = s->n_comp;
+  if (ev) {
+    cudaEvent_t e = pooled_event(s, *ev);
     if (!e) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
     CUDA_TRY(cudaEventRecord(e, s->stream));
-    marks.push_back(ev++);
+    marks->push_back((*ev)++);
   }
-  const int ion_blocks = (int)((s->n + kIonicThreads - 1) / kIonicThreads);
+  const int ion_blocks = (int)((s->n_int + kIonicThreads - 1) / kIonicThreads);
   if (s->model == TC_MODEL_MS)
     ionic_ms_kernel<T><<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
   else
     ionic_tp06_kernel<T><<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
   CUDA_TRY(cudaGetLastError());
   PcgArgs<T> pa;
-  pa.n = s->n;
+  pa.n = s->n_int;
   pa.slice_ptr = s->slice_ptr;
   pa.col = s->col;
   pa.vM = static_cast<const T*>(s->vM);
@@ -301,6 +406,8 @@ tc_status launch_step(tc_sim* s, size_t& ev, std::vector<size_t>& marks) {
   pa.vA = static_cast<const T*>(s->vA);
   pa.dinv = static_cast<const T*>(s->dinv);
   pa.blk_slice = s->blk_slice;
+  pa.comp_of_block = s->comp_of_block;
+  pa.comp_block0 = s->comp_block0;
   pa.g1 = static_cast<const T*>(s->g1);
   pa.g2 = static_cast<const T*>(s->g2);
   pa.x = Vn;
@@ -324,22 +431,64 @@ tc_status launch_step(tc_sim* s, size_t& ev, std::vector<size_t>& marks) {
   pa.rtol = s->rtol;
   pa.max_iter = s->max_iter;
   pa.wait_limit = s->wait_limit;
-  pa.t_k = (double)s->k * s->dt;
+  pa.k_base = s->k_dev;
+  pa.k_off = k_off;
   pa.dt = s->dt;
   pa.thr = s->thr;
-  if (s->prof) {
-    CUDA_TRY(cudaEventRecord(pooled_event(s, ev), s->stream));
-    ev++;
+  if (ev) {
+    CUDA_TRY(cudaEventRecord(pooled_event(s, *ev), s->stream));
+    (*ev)++;
   }
   void* args[] = {&pa};
   CUDA_TRY(cudaLaunchCooperativeKernel(pcg_kernel(s), s->nblocks, s->pcg_threads, args, 0,
                                        s->stream));
-  if (s->prof) {
-    CUDA_TRY(cudaEventRecord(pooled_event(s, ev), s->stream));
-    ev++;
+  if (ev) {
+    CUDA_TRY(cudaEventRecord(pooled_event(s, *ev), s->stream));
+    (*ev)++;
   }
   return TC_OK;
 }
+
+tc_status launch_step_any(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size_t>* marks) {
+  return s->precision == TC_FP64 ? launch_step<double>(s, iv, k_off, ev, marks)
+                                 : launch_step<float>(s, iv, k_off, ev, marks);
+}
+
+// Capture kGraphSteps steps starting at buffer phase iv, followed by the index advance.
+tc_status capture_graph(tc_sim* s, int iv, cudaGraphExec_t* out) {
+  cudaStream_t cs;
+  CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = s->stream;
+  s->stream = cs;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  tc_status st = TC_OK;
+  if (e == cudaSuccess) {
+    for (int j = 0; j < kGraphSteps && st == TC_OK; ++j) st = launch_step_any(s, (iv + j) % 3, j, nullptr, nullptr);
+    if (st == TC_OK) {
+      tick_kernel<<<1, 1, 0, cs>>>(s->k_dev, kGraphSteps);
+      e = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && st == TC_OK) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+  }
+  s->stream = saved;
+  cudaStreamDestroy(cs);
+  if (st != TC_OK) return st;
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // clear a sticky-free capture error
+    return cuda_fail(e, "graph capture of the step loop");
+  }
+  return TC_OK;
+}
+
+struct Snapshot {
+  std::vector<void*> bufs;
+  long long k;
+  int iv;
+};
 
 }  // namespace
 
@@ -382,14 +531,18 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   s->pcg_threads = env_int("TC_PCG_THREADS", 1024) == 512 ? 512 : 1024;
   s->blocks_per_sm = std::max(1, env_int("TC_PCG_BLOCKS_PER_SM", s->pcg_threads == 1024 ? 1 : 2));
   s->sell_sigma = std::max(1, env_int("TC_SELL_SIGMA", 1024));
+  s->use_graphs = env_int("TC_GRAPHS", 1) != 0;
   Sell sell;
   std::vector<double> av, hdinv;
   try {
-    node_ordering(pat, s->sell_sigma, s->perm);
+    padded_ordering(pat, s->sell_sigma, s->perm, s->comp_rows);
+    s->n_int = (int64_t)s->perm.size();
+    s->n_comp = (int)s->comp_rows.size() - 1;
     tc_status st = build_sell(pat, s->perm, sell);
     if (st != TC_OK) return bail(st);
-    s->inv.resize(s->n);
-    for (int64_t i = 0; i < s->n; ++i) s->inv[s->perm[i]] = (int32_t)i;
+    s->inv.assign(s->n, -1);
+    for (int64_t i = 0; i < s->n_int; ++i)
+      if (s->perm[i] >= 0) s->inv[s->perm[i]] = (int32_t)i;
     // A = chi Cm M + theta dt K, entry by entry (Eq. 3): two products, then the sum
     const double c1 = chi * cm, c2 = theta * dt;
     av.resize(s->nnz);
@@ -398,9 +551,10 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
       volatile double t2 = c2 * kv[q];
       av[q] = t1 + t2;
     }
-    hdinv.resize(s->n);
-    for (int64_t i = 0; i < s->n; ++i) {
+    hdinv.assign(s->n_int, 0.0);   // dummy rows: zero inverse, so they never move
+    for (int64_t i = 0; i < s->n_int; ++i) {
       const int32_t o = s->perm[i];
+      if (o < 0) continue;
       const int32_t* cb = &pat.col[pat.row_ptr[o]];
       const int64_t len = pat.row_ptr[o + 1] - pat.row_ptr[o];
       const int64_t d = std::lower_bound(cb, cb + len, o) - cb;
@@ -419,7 +573,7 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
   if (!coop) return bail(fail(TC_ERR_CUDA, "device does not support cooperative launches"));
   tc_status st = TC_OK;
-  const int64_t n = s->n;
+  const int64_t n = s->n_int;
   const size_t E = s->esz;
 #define ALLOCB(ptr, bytes)                                 \
   do {                                                     \
@@ -443,9 +597,10 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   ALLOCB(s->vpeak, n * sizeof(double));
   ALLOCB(s->rep90, n * sizeof(double));
   ALLOCB(s->lrt, n * sizeof(double));
-  ALLOCB(s->bar, sizeof(GridBar));
+  ALLOCB(s->bar, s->n_comp * sizeof(GridBar));
   ALLOCB(s->err, sizeof(int));
-  ALLOCB(s->stats, sizeof(DevStats));
+  ALLOCB(s->stats, s->n_comp * sizeof(DevStats));
+  ALLOCB(s->k_dev, sizeof(long long));
   ALLOCB(s->stim_off, (n + 1) * sizeof(int32_t));
 #undef ALLOCB
   ce = cudaMemcpy(s->slice_ptr, sell.slice_ptr.data(), (s->nslices + 1) * sizeof(int32_t),
@@ -456,9 +611,10 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   st = precision == TC_FP64 ? upload_matrices<double>(s, sell, mv, kv, av, hdinv)
                             : upload_matrices<float>(s, sell, mv, kv, av, hdinv);
   if (st != TC_OK) return bail(st);
-  ce = cudaMemset(s->bar, 0, sizeof(GridBar));
+  ce = cudaMemset(s->bar, 0, s->n_comp * sizeof(GridBar));
   if (ce == cudaSuccess) ce = cudaMemset(s->err, 0, sizeof(int));
-  if (ce == cudaSuccess) ce = cudaMemset(s->stats, 0, sizeof(DevStats));
+  if (ce == cudaSuccess) ce = cudaMemset(s->stats, 0, s->n_comp * sizeof(DevStats));
+  if (ce == cudaSuccess) ce = cudaMemset(s->k_dev, 0, sizeof(long long));
   if (ce == cudaSuccess) ce = cudaMemset(s->stim_off, 0, (n + 1) * sizeof(int32_t));
   if (ce == cudaSuccess) ce = cudaMemset(s->act, 0, n * sizeof(double));
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemset"));
@@ -477,6 +633,7 @@ void tc_sim_destroy(tc_sim* s) {
   if (!s) return;
   cudaSetDevice(s->device);
   cudaStreamSynchronize(s->stream);
+  drop_graphs(s);
   for (auto& d : s->allocs) cudaFree(d.p);
   for (cudaEvent_t e : s->evpool) cudaEventDestroy(e);
   if (s->pinned) cudaFreeHost(s->pinned);
@@ -492,6 +649,43 @@ tc_status tc_sim_size(const tc_sim* s, int64_t* n_nodes, int64_t* nnz, int64_t* 
   if (nnz) *nnz = s->nnz;
   if (padded_nnz) *padded_nnz = s->padded;
   if (n_blocks) *n_blocks = s->nblocks;
+  return TC_OK;
+}
+
+tc_status tc_sim_layout(const tc_sim* s, int32_t* n_components, int64_t* n_internal,
+                        int32_t* pcg_threads, int32_t* blocks_per_sm) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  if (n_components) *n_components = s->n_comp;
+  if (n_internal) *n_internal = s->n_int;
+  if (pcg_threads) *pcg_threads = s->pcg_threads;
+  if (blocks_per_sm) *blocks_per_sm = s->blocks_per_sm;
+  return TC_OK;
+}
+
+tc_status tc_set_launch(tc_sim* s, int32_t pcg_threads, int32_t blocks_per_sm) {
+  clear_error();
+  if (!s || (pcg_threads != 512 && pcg_threads != 1024) || blocks_per_sm < 1)
+    return fail(TC_ERR_ARG, "pcg_threads must be 512 or 1024 and blocks_per_sm >= 1");
+  CUDA_TRY(cudaSetDevice(s->device));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  const int old_t = s->pcg_threads, old_b = s->blocks_per_sm;
+  s->pcg_threads = pcg_threads;
+  s->blocks_per_sm = blocks_per_sm;
+  tc_status st = set_partition(s);
+  if (st != TC_OK) {
+    s->pcg_threads = old_t;
+    s->blocks_per_sm = old_b;
+    set_partition(s);
+  }
+  return st;
+}
+
+tc_status tc_set_graphs(tc_sim* s, int32_t on) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  s->use_graphs = on != 0;
+  if (!s->use_graphs) drop_graphs(s);
   return TC_OK;
 }
 
@@ -521,32 +715,35 @@ tc_status tc_set_ionic(tc_sim* s, int32_t model, const double* params, int32_t n
   } else {
     return fail(TC_ERR_ARG, "unknown ionic model " + std::to_string(model));
   }
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
   const int ns = (int)rest.size();
   if (s->state && ns != s->n_states) {
     dfree(s, s->state);
     s->state = nullptr;
+    drop_graphs(s);
   }
-  if (!s->state) TRY(dalloc_bytes(s, &s->state, (size_t)ns * s->n * s->esz));
+  if (!s->state) TRY(dalloc_bytes(s, &s->state, (size_t)ns * s->n_int * s->esz));
   s->model = model;
   s->n_states = ns;
-  std::vector<double> col(s->n);
+  drop_graphs(s);   // model constants are baked into captured launches
+  std::vector<double> col(s->n_int);
   for (int j = 0; j < ns; ++j) {
     if (init_state)
-      to_internal(s, init_state + (size_t)j * s->n, col.data());
+      to_internal(s, init_state + (size_t)j * s->n, col.data(), rest[j]);
     else
       std::fill(col.begin(), col.end(), rest[j]);
-    TRY(upload_vec(s, static_cast<char*>(s->state) + (size_t)j * s->n * s->esz, col.data(), s->n));
+    TRY(upload_vec(s, static_cast<char*>(s->state) + (size_t)j * s->n_int * s->esz, col.data(), false));
   }
   std::fill(col.begin(), col.end(), v0);
   s->iv = 0;
-  TRY(upload_vec(s, s->V[0], col.data(), s->n));
-  TRY(upload_vec(s, s->V[2], col.data(), s->n));
-  std::vector<double> a0(s->n, v0 >= s->thr ? 0.0 : -1.0), m1(s->n, -1.0);
-  CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(s->rep90, m1.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(s->lrt, m1.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  TRY(upload_vec(s, s->V[0], col.data(), false));
+  TRY(upload_vec(s, s->V[2], col.data(), false));
+  std::vector<double> a0(s->n_int, v0 >= s->thr ? 0.0 : -1.0), m1(s->n_int, -1.0);
+  CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n_int * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->rep90, m1.data(), s->n_int * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->lrt, m1.data(), s->n_int * sizeof(double), cudaMemcpyHostToDevice));
   std::fill(m1.begin(), m1.end(), v0);
-  CUDA_TRY(cudaMemcpy(s->vpeak, m1.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(s->vpeak, m1.data(), s->n_int * sizeof(double), cudaMemcpyHostToDevice));
   s->v_rest = v0;
   s->k = 0;
   return TC_OK;
@@ -585,6 +782,7 @@ tc_status tc_set_solver(tc_sim* s, double atol, double rtol, int32_t max_iter) {
   s->atol = atol;
   s->rtol = rtol;
   s->max_iter = max_iter;
+  drop_graphs(s);
   return TC_OK;
 }
 
@@ -593,12 +791,13 @@ tc_status tc_set_activation_threshold(tc_sim* s, double v) {
   if (!s || !std::isfinite(v)) return fail(TC_ERR_ARG, "bad threshold");
   if (s->thr_locked) return fail(TC_ERR_STATE, "threshold is fixed once stepping has started");
   s->thr = v;
+  drop_graphs(s);
   if (s->model >= 0) {
     CUDA_TRY(cudaSetDevice(s->device));
-    std::vector<double> vcur(s->n), a0(s->n);
-    TRY(download_vec(s, s->V[s->iv], vcur.data(), s->n));
-    for (int64_t i = 0; i < s->n; ++i) a0[i] = vcur[i] >= v ? 0.0 : -1.0;
-    CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<double> vcur(s->n_int), a0(s->n_int);
+    TRY(download_vec(s, s->V[s->iv], vcur.data()));
+    for (int64_t i = 0; i < s->n_int; ++i) a0[i] = vcur[i] >= v ? 0.0 : -1.0;
+    CUDA_TRY(cudaMemcpy(s->act, a0.data(), s->n_int * sizeof(double), cudaMemcpyHostToDevice));
   }
   return TC_OK;
 }
@@ -607,6 +806,7 @@ tc_status tc_set_wait_limit(tc_sim* s, int64_t polls) {
   clear_error();
   if (!s || polls < 1) return fail(TC_ERR_ARG, "need polls >= 1");
   s->wait_limit = polls;
+  drop_graphs(s);
   return TC_OK;
 }
 
@@ -616,22 +816,59 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
   if (s->model < 0) return fail(TC_ERR_STATE, "tc_set_ionic must be called before tc_step");
   CUDA_TRY(cudaSetDevice(s->device));
   s->thr_locked = true;
-  DevStats zero{};
-  CUDA_TRY(cudaMemcpyAsync(s->stats, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream));
+  std::vector<DevStats> zero(s->n_comp);
+  CUDA_TRY(cudaMemcpyAsync(s->stats, zero.data(), s->n_comp * sizeof(DevStats),
+                           cudaMemcpyHostToDevice, s->stream));
   CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
-  CUDA_TRY(cudaMemsetAsync(s->bar, 0, sizeof(GridBar), s->stream));
+  CUDA_TRY(cudaMemsetAsync(s->bar, 0, s->n_comp * sizeof(GridBar), s->stream));
+  const long long k0 = s->k;
+  CUDA_TRY(cudaMemcpyAsync(s->k_dev, &k0, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
   size_t ev = 0;
   std::vector<size_t> marks;
-  for (int64_t st = 0; st < n_steps; ++st) {
-    TRY(s->precision == TC_FP64 ? launch_step<double>(s, ev, marks) : launch_step<float>(s, ev, marks));
-    s->iv = (s->iv + 1) % 3;
-    s->k += 1;
+  int64_t done = 0;
+  // whole groups of kGraphSteps steps replay a captured graph (not while profiling per launch)
+  if (s->use_graphs && !s->prof && n_steps >= kGraphSteps) {
+    GraphCache& g = s->graphs[s->iv];
+    if (!g.valid) {
+      tc_status st = capture_graph(s, s->iv, &g.exec);
+      if (st == TC_OK) {
+        g.valid = true;
+        g.iv = s->iv;
+      } else {
+        s->use_graphs = false;   // capture unsupported here: launch step by step instead
+        clear_error();
+      }
+    }
+    if (g.valid) {
+      for (; done + kGraphSteps <= n_steps; done += kGraphSteps)
+        CUDA_TRY(cudaGraphLaunch(g.exec, s->stream));
+    }
   }
-  DevStats ds{};
+  const int64_t rest = n_steps - done;
+  for (int64_t j = 0; j < rest; ++j)
+    TRY(launch_step_any(s, (int)((s->iv + done + j) % 3), (int)j, s->prof ? &ev : nullptr, &marks));
+  if (rest > 0) {
+    tick_kernel<<<1, 1, 0, s->stream>>>(s->k_dev, (int)rest);
+    CUDA_TRY(cudaGetLastError());
+  }
+  s->iv = (int)((s->iv + n_steps) % 3);
+  s->k += n_steps;
+  std::vector<DevStats> ds(s->n_comp);
   int herr = 0;
-  CUDA_TRY(cudaMemcpyAsync(&ds, s->stats, sizeof(ds), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(ds.data(), s->stats, s->n_comp * sizeof(DevStats),
+                           cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
+  long long iters = 0;
+  int max_it = 0, not_conv = 0;
+  double zn = 0.0, z0n = 0.0;
+  for (const DevStats& d : ds) {
+    iters += d.iters_total;
+    max_it = std::max(max_it, d.max_iters);
+    not_conv += d.not_conv;
+    zn = std::max(zn, d.last_zn);
+    z0n = std::max(z0n, d.last_z0n);
+  }
   if (s->prof) {
     for (size_t m : marks) {
       float a = 0.f, b = 0.f;
@@ -642,16 +879,16 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
       s->prof_acc.pcg_ms += b;
       s->prof_acc.pcg_launches += 1;
     }
-    s->prof_acc.pcg_iterations += ds.iters_total;
+    s->prof_acc.pcg_iterations += iters;
   }
   if (stats) {
     stats->steps = n_steps;
     stats->step_index = s->k;
-    stats->cg_iterations = ds.iters_total;
-    stats->max_iterations = ds.max_iters;
-    stats->not_converged = ds.not_conv;
-    stats->last_znorm = ds.last_zn;
-    stats->last_z0norm = ds.last_z0n;
+    stats->cg_iterations = iters;
+    stats->max_iterations = max_it;
+    stats->not_converged = not_conv;
+    stats->last_znorm = zn;
+    stats->last_z0norm = z0n;
   }
   if (herr & kErrTimeout) return fail(TC_ERR_TIMEOUT, "a grid barrier wait hit its limit");
   if (herr & kErrNan) return fail(TC_ERR_NAN, "non-finite value in the PCG solve");
@@ -662,7 +899,7 @@ static void* field_ptr(const tc_sim* s, int32_t field) {
   if (field == TC_FIELD_V) return s->V[s->iv];
   if (field == TC_FIELD_V_PREV) return s->V[(s->iv + 2) % 3];
   if (field >= TC_FIELD_STATE && field < TC_FIELD_STATE + s->n_states)
-    return static_cast<char*>(s->state) + (size_t)(field - TC_FIELD_STATE) * s->n * s->esz;
+    return static_cast<char*>(s->state) + (size_t)(field - TC_FIELD_STATE) * s->n_int * s->esz;
   return nullptr;
 }
 
@@ -674,8 +911,8 @@ tc_status tc_read_state(const tc_sim* s, int32_t field, double* dst, int64_t n) 
   const void* src = field_ptr(s, field);
   if (!src) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
   CUDA_TRY(cudaSetDevice(s->device));
-  TRY(download_vec(s, src, s->pinned, s->n));
-  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = s->pinned[i];
+  TRY(download_vec(s, src, s->pinned));
+  to_caller(s, s->pinned, dst);
   return TC_OK;
 }
 
@@ -688,8 +925,8 @@ tc_status tc_write_state(tc_sim* s, int32_t field, const double* src, int64_t n)
   if (!dst) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
   CUDA_TRY(cudaSetDevice(s->device));
   CUDA_TRY(cudaStreamSynchronize(s->stream));   // the staging buffer may still feed a copy
-  to_internal(s, src, s->pinned);
-  return upload_vec(s, dst, s->pinned, s->n);
+  to_internal(s, src, s->pinned, 0.0);
+  return upload_vec(s, dst, s->pinned, true);
 }
 
 tc_status tc_activation_times(const tc_sim* s, double v_threshold, double* dst, int64_t n) {
@@ -699,10 +936,10 @@ tc_status tc_activation_times(const tc_sim* s, double v_threshold, double* dst, 
   if (v_threshold != s->thr)
     return fail(TC_ERR_STATE, "activation times were captured for another threshold");
   CUDA_TRY(cudaSetDevice(s->device));
-  double* tmp = s->pinned;
-  CUDA_TRY(cudaMemcpyAsync(tmp, s->act, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->pinned, s->act, s->n_int * sizeof(double), cudaMemcpyDeviceToHost,
+                           s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
-  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = tmp[i];
+  to_caller(s, s->pinned, dst);
   return TC_OK;
 }
 
@@ -711,9 +948,10 @@ static tc_status read_double_field(const tc_sim* s, const double* src, double* d
   if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
   if (s->model < 0) return fail(TC_ERR_STATE, "no ionic model set");
   CUDA_TRY(cudaSetDevice(s->device));
-  CUDA_TRY(cudaMemcpyAsync(s->pinned, src, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->pinned, src, s->n_int * sizeof(double), cudaMemcpyDeviceToHost,
+                           s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
-  for (int64_t i = 0; i < s->n; ++i) dst[s->perm[i]] = s->pinned[i];
+  to_caller(s, s->pinned, dst);
   return TC_OK;
 }
 
@@ -722,6 +960,7 @@ tc_status tc_set_repolarisation_threshold(tc_sim* s, double v) {
   if (!s || !std::isfinite(v)) return fail(TC_ERR_ARG, "bad threshold");
   if (s->thr_locked) return fail(TC_ERR_STATE, "threshold is fixed once stepping has started");
   s->lrt_thr = v;
+  drop_graphs(s);
   return TC_OK;
 }
 
@@ -753,6 +992,85 @@ tc_status tc_set_step_index(tc_sim* s, int64_t k) {
   return TC_OK;
 }
 
+tc_status tc_autotune(tc_sim* s, int32_t trial_steps, int32_t* pcg_threads, int32_t* blocks_per_sm,
+                      double* best_ms_per_step) {
+  clear_error();
+  if (!s || trial_steps < 1) return fail(TC_ERR_ARG, "need a simulation and trial_steps >= 1");
+  if (s->model < 0) return fail(TC_ERR_STATE, "tc_set_ionic must be called before tc_autotune");
+  CUDA_TRY(cudaSetDevice(s->device));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  // snapshot of everything a step changes, restored after every candidate
+  struct Buf {
+    void* dev;
+    size_t bytes;
+    void* copy;
+  };
+  std::vector<Buf> bufs;
+  auto add = [&](void* p, size_t bytes) { bufs.push_back({p, bytes, nullptr}); };
+  for (int j = 0; j < 3; ++j) add(s->V[j], s->n_int * s->esz);
+  add(s->state, (size_t)s->n_states * s->n_int * s->esz);
+  for (double* p : {s->act, s->vpeak, s->rep90, s->lrt}) add(p, s->n_int * sizeof(double));
+  tc_status st = TC_OK;
+  for (auto& b : bufs) {
+    cudaError_t e = cudaMalloc(&b.copy, b.bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(b.copy, b.dev, b.bytes, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "autotune snapshot");
+      break;
+    }
+  }
+  const long long k0 = s->k;
+  const int iv0 = s->iv;
+  const bool thr_locked0 = s->thr_locked;
+  const int t0 = s->pcg_threads, b0 = s->blocks_per_sm;
+  const int cand[][2] = {{1024, 1}, {512, 1}, {512, 2}};
+  double best = 1e300;
+  int best_t = t0, best_b = b0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == TC_OK) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  for (const auto& c : cand) {
+    if (st != TC_OK) break;
+    s->pcg_threads = c[0];
+    s->blocks_per_sm = c[1];
+    if (set_partition(s) != TC_OK) {
+      clear_error();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventRecord(e0, s->stream);
+    tc_status r = tc_step(s, trial_steps, nullptr);
+    cudaEventRecord(e1, s->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r == TC_OK && ms < best) {
+      best = ms;
+      best_t = c[0];
+      best_b = c[1];
+    }
+    clear_error();
+    for (auto& b : bufs) cudaMemcpy(b.dev, b.copy, b.bytes, cudaMemcpyDeviceToDevice);
+    s->k = k0;
+    s->iv = iv0;
+    s->thr_locked = thr_locked0;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (auto& b : bufs)
+    if (b.copy) cudaFree(b.copy);
+  s->pcg_threads = best_t;
+  s->blocks_per_sm = best_b;
+  tc_status st2 = set_partition(s);
+  if (st != TC_OK) return st;
+  if (st2 != TC_OK) return st2;
+  if (pcg_threads) *pcg_threads = best_t;
+  if (blocks_per_sm) *blocks_per_sm = best_b;
+  if (best_ms_per_step) *best_ms_per_step = best / trial_steps;
+  return TC_OK;
+}
+
 static const void* op_values(const tc_sim* s, int32_t op) {
   return op == TC_OP_M ? s->vM : op == TC_OP_K ? s->vK : op == TC_OP_A ? s->vA : nullptr;
 }
@@ -770,11 +1088,11 @@ tc_status tc_apply_operator_dev(tc_sim* s, int32_t op, const void* x_dev, void* 
   const int nb = (int)std::max<int64_t>(blocks, 1);
   if (s->precision == TC_FP64)
     spmv_sell_kernel<double><<<nb, threads, 0, s->stream>>>(
-        s->n, s->nslices, s->slice_ptr, s->col, static_cast<const double*>(val),
+        s->n_int, s->nslices, s->slice_ptr, s->col, static_cast<const double*>(val),
         static_cast<const double*>(x_dev), static_cast<double*>(y_dev));
   else
     spmv_sell_kernel<float><<<nb, threads, 0, s->stream>>>(
-        s->n, s->nslices, s->slice_ptr, s->col, static_cast<const float*>(val),
+        s->n_int, s->nslices, s->slice_ptr, s->col, static_cast<const float*>(val),
         static_cast<const float*>(x_dev), static_cast<float*>(y_dev));
   CUDA_TRY(cudaGetLastError());
   return TC_OK;
@@ -787,20 +1105,20 @@ tc_status tc_apply_operator(tc_sim* s, int32_t op, const double* x, double* y, i
   if (!op_values(s, op)) return fail(TC_ERR_ARG, "unknown operator");
   CUDA_TRY(cudaSetDevice(s->device));
   void *dx = nullptr, *dy = nullptr;
-  CUDA_TRY(cudaMalloc(&dx, s->n * s->esz));
-  cudaError_t e = cudaMalloc(&dy, s->n * s->esz);
+  CUDA_TRY(cudaMalloc(&dx, s->n_int * s->esz));
+  cudaError_t e = cudaMalloc(&dy, s->n_int * s->esz);
   if (e != cudaSuccess) {
     cudaFree(dx);
     return cuda_fail(e, "cudaMalloc");
   }
-  to_internal(s, x, s->pinned);
-  tc_status st = upload_vec(s, dx, s->pinned, s->n);
+  to_internal(s, x, s->pinned, 0.0);
+  tc_status st = upload_vec(s, dx, s->pinned, false);
   if (st == TC_OK) st = tc_apply_operator_dev(s, op, dx, dy);
-  if (st == TC_OK) st = download_vec(s, dy, s->pinned, s->n);
+  if (st == TC_OK) st = download_vec(s, dy, s->pinned);
   cudaFree(dx);
   cudaFree(dy);
   if (st != TC_OK) return st;
-  for (int64_t i = 0; i < s->n; ++i) y[s->perm[i]] = s->pinned[i];
+  to_caller(s, s->pinned, y);
   return TC_OK;
 }
 
@@ -842,7 +1160,7 @@ tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_
   return TC_OK;
 }
 
-const char* tc_version(void) { return "tc_b300 0.3 (sm_103a)"; }
+const char* tc_version(void) { return "tc_b300 0.4 (sm_103a)"; }
 
 }  // extern "C"
 
@@ -907,10 +1225,10 @@ extern "C" tc_status tc_apply_operator_static(tc_sim* s, int32_t op, const doubl
   if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
   if (s->precision != TC_FP64)
     return fail(TC_ERR_ARG, "tc_apply_operator_static serves TC_FP64 simulations only");
-  if (s->n > kStaticMaxNodes)
+  if (s->n_int > kStaticMaxNodes)
     return fail(TC_ERR_ARG, "tc_apply_operator_static handles at most " +
                                 std::to_string(kStaticMaxNodes) + " nodes; this mesh has " +
-                                std::to_string(s->n) + " (use tc_apply_operator)");
+                                std::to_string(s->n_int) + " in its device layout (use tc_apply_operator)");
   const double* val = static_cast<const double*>(op_values(s, op));
   if (!val) return fail(TC_ERR_ARG, "unknown operator");
   CUDA_TRY(cudaSetDevice(s->device));
@@ -919,17 +1237,17 @@ extern "C" tc_status tc_apply_operator_static(tc_sim* s, int32_t op, const doubl
   // the simulation's page-locked staging buffer carries x in and y out
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   double* h = s->pinned;
-  for (int64_t i = 0; i < s->n; ++i) h[i] = x[s->perm[i]];
-  CUDA_TRY(cudaMemcpyAsync(scratch, h, s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  to_internal(s, x, h, 0.0);
+  CUDA_TRY(cudaMemcpyAsync(scratch, h, s->n_int * sizeof(double), cudaMemcpyHostToDevice, s->stream));
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((s->nslices * 32 + threads - 1) / threads,
                                            (int64_t)s->num_sms * 8);
   spmv_sell_static_kernel<<<(int)std::max<int64_t>(blocks, 1), threads, 0, s->stream>>>(
-      s->n, s->nslices, s->slice_ptr, s->col, val, scratch);
+      s->n_int, s->nslices, s->slice_ptr, s->col, val, scratch);
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemcpyAsync(h, scratch + kStaticMaxNodes, s->n * sizeof(double),
+  CUDA_TRY(cudaMemcpyAsync(h, scratch + kStaticMaxNodes, s->n_int * sizeof(double),
                            cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
-  for (int64_t i = 0; i < s->n; ++i) y[s->perm[i]] = h[i];
+  to_caller(s, h, y);
   return TC_OK;
 }

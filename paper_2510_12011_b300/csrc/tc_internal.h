@@ -44,11 +44,22 @@ namespace tc {
 tc_status assemble_mk(const tc_mesh& m, const double* sigma_l, const double* sigma_t,
                       int32_t n_regions, std::vector<double>& mval, std::vector<double>& kval);
 
-// Reverse Cuthill-McKee order of the pattern graph, then a stable descending sort of row
-// lengths inside windows of `sell_sigma` rows.  perm[new] = old.
-void node_ordering(const Csr& pat, int32_t sell_sigma, std::vector<int32_t>& perm);
+// Reverse Cuthill-McKee order of the pattern graph, component by component, then a stable
+// descending sort of row lengths inside windows of `sell_sigma` rows that never cross a
+// component.  perm[new] = old; comp_start (if not null) receives the first position of every
+// connected component in that order plus n at the end.
+void node_ordering(const Csr& pat, int32_t sell_sigma, std::vector<int32_t>& perm,
+                   std::vector<int64_t>* comp_start = nullptr);
 
-// SELL-C-sigma layout (C = 32) of the pattern permuted by perm (perm[new] = old).
+// Internal device order: the node ordering with every connected component padded to a multiple
+// of 32 rows by inert dummy rows, so that no 32-row SELL slice holds two components.
+// perm_ext[internal] = caller index or -1 (dummy); comp_rows[c] = first internal row of
+// component c, comp_rows[n_comp] = internal row count.
+void padded_ordering(const Csr& pat, int32_t sell_sigma, std::vector<int32_t>& perm_ext,
+                     std::vector<int64_t>& comp_rows);
+
+// SELL-C-sigma layout (C = 32) of the pattern permuted by perm (perm[new] = old, or -1 for a
+// dummy row, which gets no entries).
 struct Sell {
   int64_t n = 0, nslices = 0, padded = 0;
   std::vector<int32_t> slice_ptr;   // nslices+1, offsets in entries (multiples of 32)

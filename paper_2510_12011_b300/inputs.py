@@ -170,8 +170,8 @@ class Workload:
     """One monodomain run: mesh, tissue constants, time stepping, solver and stimuli."""
     name: str
     mesh: Mesh
-    sigma_l: float            # S/m
-    sigma_t: float            # S/m
+    sigma_l: object           # S/m, a scalar or one value per region
+    sigma_t: object           # S/m, a scalar or one value per region
     chi: float                # 1/mm
     cm: float                 # uF/mm^2
     theta: float
@@ -219,6 +219,73 @@ def slab_custom(lx, ly, lz, h, jitter=0.0, seed=0, fibre="x", dt=0.01, model="ms
     st = [Stimulus(corner_nodes(m, stim_mm), 0.0, 2.0, 0.5)]
     return Workload(f"slab{lx:g}x{ly:g}x{lz:g}_h{h:g}_{model}", m, 0.17, 0.019, 140.0, 0.01, 0.5,
                     dt, t_end, model, stimuli=st, atol=atol, rtol=rtol, max_iter=max_iter)
+
+
+@dataclass
+class Batch:
+    """Several independent slab workloads joined into one mesh of disconnected components.
+
+    Region r of the joined mesh is instance r (its conductivities sit at index r of the
+    workload's sigma arrays); node_offset[r] is the first node of instance r."""
+    workload: Workload
+    instances: list
+    node_offset: np.ndarray
+
+
+def join_workloads(parts, name="batch", gap_mm=1.0) -> Batch:
+    """Join workloads that share dt, chi, Cm, theta, model and solver settings into one mesh
+    (instances placed side by side along x with a gap, so they share no node)."""
+    xyz, tets, fib, reg, lat, stims, offs = [], [], [], [], [], [], []
+    off, x0 = 0, 0.0
+    for r, w in enumerate(parts):
+        m = w.mesh
+        p = m.xyz.copy()
+        p[:, 0] += x0
+        x0 = p[:, 0].max() + gap_mm
+        xyz.append(p)
+        tets.append(m.tets + off)
+        fib.append(m.fibres)
+        reg.append(np.full(m.n_tets, r, dtype=np.int32))
+        lat.append(m.lattice)
+        for st in w.stimuli:
+            stims.append(Stimulus(np.asarray(st.nodes, dtype=np.int32) + off, st.start, st.duration,
+                                  st.intensity))
+        offs.append(off)
+        off += m.n_nodes
+    w0 = parts[0]
+    mesh = Mesh(np.concatenate(xyz), np.concatenate(tets).astype(np.int32), np.concatenate(fib),
+                np.concatenate(reg), np.concatenate(lat), (0, 0, 0), w0.mesh.h)
+    sl = np.array([float(np.atleast_1d(w.sigma_l)[0]) for w in parts])
+    st_ = np.array([float(np.atleast_1d(w.sigma_t)[0]) for w in parts])
+    w = Workload(name, mesh, sl, st_, w0.chi, w0.cm, w0.theta, w0.dt, w0.t_end, w0.model,
+                 ms=w0.ms, stimuli=stims, atol=w0.atol, rtol=w0.rtol, max_iter=w0.max_iter,
+                 v_threshold=w0.v_threshold, tp06_cell=w0.tp06_cell)
+    return Batch(w, list(parts), np.array(offs, dtype=np.int64))
+
+
+def batched_slabs(count: int = 64, seed: int = 4, h: float = 0.25, t_end: float = 200.0) -> Batch:
+    """Batch of `count` uneven slabs: dims U(10,40) x U(5,16) x U(2,6) mm (rounded to h),
+    conductivities log-uniform in 0.5x..2x of the small slab's, fibres along x, Mitchell-
+    Schaeffer, dt = 0.01 ms, one 1 mm stimulus around a random boundary node per slab."""
+    u = uniform01(seed, np.arange(8 * count, dtype=np.uint64)).reshape(count, 8)
+    parts = []
+    for i in range(count):
+        lx = max(h, round((10.0 + 30.0 * u[i, 0]) / h) * h)
+        ly = max(h, round((5.0 + 11.0 * u[i, 1]) / h) * h)
+        lz = max(h, round((2.0 + 4.0 * u[i, 2]) / h) * h)
+        m = slab_mesh(lx, ly, lz, h)
+        dims = np.array(m.shape)
+        on_face = np.any((m.lattice == 0) | (m.lattice == dims - 1), axis=1)
+        bnodes = np.nonzero(on_face)[0]
+        site = bnodes[int(u[i, 3] * bnodes.size) % bnodes.size]
+        d = np.abs(m.lattice - m.lattice[site]).max(axis=1) * h
+        nodes = np.nonzero(d <= 1.0 + 1e-9)[0].astype(np.int32)
+        sl = 0.17 * np.exp(np.log(0.5) + np.log(4.0) * u[i, 4])
+        st = 0.019 * np.exp(np.log(0.5) + np.log(4.0) * u[i, 5])
+        parts.append(Workload(f"slab{i}", m, sl, st, 140.0, 0.01, 0.5, 0.01, t_end, "ms",
+                              stimuli=[Stimulus(nodes, 0.0, 2.0, 0.5)], atol=1e-5, rtol=1e-5,
+                              max_iter=100))
+    return join_workloads(parts, name=f"batch{count}_slabs_h{h:g}_ms")
 
 
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:

@@ -62,6 +62,11 @@ _SIGS = {
     "tc_assemble": [_P, _D, _D, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
                     C.c_int32, _P, C.POINTER(_P)],
     "tc_sim_size": [_P, _I64, _I64, _I64, _I32],
+    "tc_sim_layout": [_P, _I32, _I64, _I32, _I32],
+    "tc_set_launch": [_P, C.c_int32, C.c_int32],
+    "tc_autotune": [_P, C.c_int32, _I32, _I32, _D],
+    "tc_set_graphs": [_P, C.c_int32],
+    "tc_mesh_layout_size": [_P, _I32, _I64],
     "tc_set_ionic": [_P, C.c_int32, _D, C.c_int32, _D],
     "tc_add_stimulus": [_P, _I32, C.c_int64, C.c_double, C.c_double, C.c_double],
     "tc_set_solver": [_P, C.c_double, C.c_double, C.c_int32],
@@ -177,9 +182,14 @@ class Mesh:
                                       col.ctypes.data_as(_I32), _d(mv), _d(kv)))
         return rp, col, mv, kv
 
+    def layout_size(self):
+        nc, ni = C.c_int32(), C.c_int64()
+        _check(lib().tc_mesh_layout_size(self._h, C.byref(nc), C.byref(ni)))
+        return nc.value, ni.value
+
     def ordering(self, sell_sigma=1):
         perm = np.empty(self.n_nodes, dtype=np.int32)
-        sw = np.empty((self.n_nodes + 31) // 32, dtype=np.int32)
+        sw = np.empty(self.layout_size()[1] // 32, dtype=np.int32)
         _check(lib().tc_mesh_ordering(self._h, sell_sigma, perm.ctypes.data_as(_I32),
                                       sw.ctypes.data_as(_I32)))
         return perm, sw
@@ -289,6 +299,23 @@ class Simulation:
         nb = C.c_int32()
         _check(lib().tc_sim_size(self._h, C.byref(n), C.byref(nnz), C.byref(pad), C.byref(nb)))
         return {"n_nodes": n.value, "nnz": nnz.value, "padded_nnz": pad.value, "n_blocks": nb.value}
+
+    def layout(self):
+        nc, ni, th, bps = C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32()
+        _check(lib().tc_sim_layout(self._h, C.byref(nc), C.byref(ni), C.byref(th), C.byref(bps)))
+        return {"n_components": nc.value, "n_internal": ni.value, "pcg_threads": th.value,
+                "blocks_per_sm": bps.value}
+
+    def set_launch(self, pcg_threads, blocks_per_sm):
+        _check(lib().tc_set_launch(self._h, pcg_threads, blocks_per_sm))
+
+    def autotune(self, trial_steps=20):
+        th, bps, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib().tc_autotune(self._h, trial_steps, C.byref(th), C.byref(bps), C.byref(ms)))
+        return {"pcg_threads": th.value, "blocks_per_sm": bps.value, "ms_per_step": ms.value}
+
+    def set_graphs(self, on=True):
+        _check(lib().tc_set_graphs(self._h, int(bool(on))))
 
     def set_profiling(self, on=True):
         _check(lib().tc_set_profiling(self._h, int(bool(on))))

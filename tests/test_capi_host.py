@@ -133,3 +133,25 @@ def test_negative_orientation_accepted():
     b = tc.Mesh(m.xyz, flipped).matrices(0.17, 0.019)
     for x, y in zip(a, b):
         assert np.allclose(x, y, rtol=1e-14, atol=0)
+
+
+def test_component_layout_of_a_joined_mesh():
+    parts = [I.slab_custom(1.0 + i, 1.0, 0.5, 0.25) for i in range(3)]
+    b = I.join_workloads(parts)
+    mesh = tc.Mesh.from_inputs(b.workload.mesh)
+    nc, n_int = mesh.layout_size()
+    sizes = [w.mesh.n_nodes for w in parts]
+    assert nc == 3 and n_int == sum((s + 31) // 32 * 32 for s in sizes)
+    perm, sw = mesh.ordering(1)
+    assert np.array_equal(np.sort(perm), np.arange(sum(sizes)))
+    assert sw.size == n_int // 32
+    # the internal order keeps every component contiguous (in some order of components)
+    comp = np.repeat(np.arange(3), sizes)
+    k, seen = 0, set()
+    while k < perm.size:
+        c = comp[perm[k]]
+        assert c not in seen
+        seen.add(c)
+        assert np.all(comp[perm[k:k + sizes[c]]] == c)
+        k += sizes[c]
+    assert seen == {0, 1, 2}

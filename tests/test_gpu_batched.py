@@ -1,0 +1,101 @@
+"""Batched form: several meshes (disconnected components) in one simulation, each with its
+own PCG, stepped by one cooperative launch per step; CUDA-graph replay of the step loop;
+launch-shape autotuning.  A batch must reproduce independent runs of its instances."""
+import numpy as np
+import pytest
+
+from oracle.monodomain import Monodomain
+from paper_2510_12011_b300 import inputs as I
+from paper_2510_12011_b300 import tc
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_batch():
+    dims = [(3.0, 2.0, 1.0, 0.25, 0.17, 0.019), (2.0, 1.0, 0.75, 0.25, 0.3, 0.05),
+            (4.0, 1.5, 1.0, 0.25, 0.1, 0.012), (1.0, 1.0, 0.5, 0.25, 0.2, 0.03)]
+    parts = []
+    for i, (lx, ly, lz, h, sl, st) in enumerate(dims):
+        w = I.slab_custom(lx, ly, lz, h, jitter=0.1, seed=20 + i, rtol=1e-10, t_end=3.0)
+        w.sigma_l, w.sigma_t = sl, st
+        w.stimuli = [I.Stimulus(w.stimuli[0].nodes, 0.1 * i, 1.5, 0.6)]
+        parts.append(w)
+    return I.join_workloads(parts)
+
+
+@pytest.fixture(scope="module")
+def batch_run():
+    b = _small_batch()
+    g = tc.from_workload(b.workload)
+    assert g.layout()["n_components"] == 4
+    st = g.step(300)
+    return b, g, st
+
+
+def test_batch_matches_oracle_per_instance(batch_run):
+    b, g, st = batch_run
+    V, act = g.read(), g.activation_times()
+    for w, off in zip(b.instances, b.node_offset):
+        o = Monodomain(w).run(300)
+        n = w.mesh.n_nodes
+        assert np.abs(V[off:off + n] - o.V).max() <= 1e-8
+        assert np.abs(act[off:off + n] - o.act).max() <= 1e-6
+    assert st["not_converged"] == 0
+
+
+def test_batch_matches_single_runs(batch_run):
+    b, g, st = batch_run
+    V = g.read()
+    total = 0
+    for w, off in zip(b.instances, b.node_offset):
+        s1 = tc.from_workload(w)
+        st1 = s1.step(300)
+        total += st1["cg_iterations"]
+        assert np.abs(V[off:off + w.mesh.n_nodes] - s1.read()).max() <= 1e-10
+    assert st["cg_iterations"] == total   # every instance stops on its own test
+
+
+def test_graph_replay_equals_direct_launches():
+    w = I.slab_small_ms()
+    a = tc.from_workload(w)
+    a.set_graphs(True)
+    b = tc.from_workload(w)
+    b.set_graphs(False)
+    for n in (95, 31, 64):   # graph groups of 30 plus remainders, across buffer phases
+        sa, sb = a.step(n), b.step(n)
+        assert sa["cg_iterations"] == sb["cg_iterations"]
+    assert np.array_equal(a.read(), b.read())
+    assert np.array_equal(a.activation_times(), b.activation_times())
+    assert a.step_index == b.step_index == 190
+
+
+def test_autotune_restores_state_and_picks_a_shape():
+    w = I.slab_custom(12.0, 6.0, 3.0, 0.25, t_end=1.0)
+    a = tc.from_workload(w)
+    a.step(10)
+    v10 = a.read()
+    res = a.autotune(5)
+    assert res["pcg_threads"] in (512, 1024) and res["ms_per_step"] > 0
+    assert np.array_equal(a.read(), v10) and a.step_index == 10
+    lay = a.layout()
+    assert (lay["pcg_threads"], lay["blocks_per_sm"]) == (res["pcg_threads"], res["blocks_per_sm"])
+    a.step(20)
+    ref = tc.from_workload(w)
+    ref.step(30)
+    assert np.abs(a.read() - ref.read()).max() <= 1e-9
+
+
+def test_full_batch_steps_in_fp32():
+    # the 64-slab batch (5.3 M nodes): after 3 ms every instance has activated around its own
+    # stimulus site, and nowhere else yet
+    b = I.batched_slabs(t_end=3.0)
+    g = tc.from_workload(b.workload, precision=tc.TC_FP32)
+    assert g.layout()["n_components"] == 64
+    st = g.step(300)
+    assert st["not_converged"] == 0
+    act = g.activation_times()
+    for w, off in zip(b.instances, b.node_offset):
+        nodes = w.stimuli[0].nodes + off
+        a = act[off:off + w.mesh.n_nodes]
+        assert np.mean(act[nodes] >= 0.0) > 0.5
+        assert 0 < np.count_nonzero(a >= 0.0) < a.size
