@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["large_tp06", "large_ms", "small_ms"], default="large_tp06")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=600)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -228,6 +230,45 @@ def apd90_check(w_big, torch):
             "act_err_ms_max": float(np.abs(out[tc.TC_FP32][1] - out[tc.TC_FP64][1]).max())}
 
 
+def batched_form(steps, stream, torch):
+    """The batched form: 64 uneven slabs (5.3 M nodes) as independent problems in one
+    simulation, FP32, launch shape by the autotuner, step loop by CUDA-graph replay (also timed
+    with host launches for comparison)."""
+    from paper_2510_12011_b300 import tc
+    b = I.batched_slabs()
+    w = b.workload
+    t0 = time.perf_counter()
+    sim = tc.from_workload(w, stream=stream.cuda_stream, precision=tc.TC_FP32)
+    setup_s = time.perf_counter() - t0
+    tune = sim.autotune(20)
+    out = {"workload": w.name, "instances": len(b.instances), "n_nodes": w.mesh.n_nodes,
+           "instance_nodes_min": int(min(x.mesh.n_nodes for x in b.instances)),
+           "instance_nodes_max": int(max(x.mesh.n_nodes for x in b.instances)),
+           "dtype": "f32 (FP64 reductions)", "dt_ms": w.dt, "autotune": tune,
+           "setup_s": setup_s}
+    for graphs in (True, False):
+        sim.set_graphs(graphs)
+        tc.set_model(sim, w)
+        sim.step(30)
+        tc.set_model(sim, w)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        key = "graph" if graphs else "host_launches"
+        out[key] = {"value": w.mesh.n_nodes * steps / (ms * 1e-3), "unit": "node-steps/s",
+                    "ms_per_step": ms / steps, "steps": steps,
+                    "mean_cg_iterations_per_instance": st["cg_iterations"] / steps / len(b.instances),
+                    "not_converged": st["not_converged"]}
+    out["value"] = out["graph"]["value"]
+    sim.close()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2510_12011_b300 import tc
@@ -356,6 +397,10 @@ def run_ours(args):
         if w.model == "tp06":
             fp32["apd90"] = apd90_check(w, torch)
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_form(min(args.batched_steps, max(K, 30)), stream, torch)
+
     if rank != 0:
         return
     out = {
@@ -382,6 +427,7 @@ def run_ours(args):
         "spmv": {"value": spmv_gbs, "unit": "GB/s", "ms": spmv_ms, "bytes": spmv_bytes(n, size["nnz"]),
                  "frac": spmv_gbs / peak, "l2": "flushed (512 MB read) before every launch"},
         "fp32_form": fp32,
+        "batched_form": batched,
         "e2e": e2e,
         "gpu_launches": prof["ionic_launches"] + prof["pcg_launches"],
         "clocks": clk,

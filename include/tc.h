@@ -61,6 +61,7 @@ typedef struct {
   int32_t not_converged;  /* steps whose PCG stopped at max_iter (Algorithm 1 just stops) */
   double last_znorm;      /* ||z|| when the last step's PCG stopped                      */
   double last_z0norm;     /* ||z_0|| of the last step's PCG                              */
+  int64_t graph_steps;    /* steps of this call replayed from captured CUDA graphs       */
 } tc_step_stats;
 
 /* Accumulated device time per kernel while profiling is on (tc_set_profiling). */
@@ -245,6 +246,72 @@ tc_status tc_set_wait_limit(tc_sim* sim, int64_t polls);
  * (table-driven, Tang 1989) and the CUDA library exp at the host inputs x[n]; y_fast[n] and
  * y_ref[n] receive the two results (host arrays).  Diagnostics; allocates 24 n bytes. */
 tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_t n);
+
+/* ---- learned ionic surrogate --------------------------------------------------------
+ * A multilayer perceptron (20 -> 4 x 256 SiLU -> 19; BF16 weights and activations, FP32
+ * accumulation, FP32 master weights) that maps a TP06 cell's (18 states, V, window-mean
+ * stimulus current in pA/pF) to its 18 states and V after a window of ionic steps.  Inputs are
+ * normalized as (x - in_mean)/in_scale; the network predicts the normalized change
+ * ((y - x) - out_mean)/out_scale.  Forward passes run on the tensor cores (tcgen05, all layers
+ * fused in one kernel); training runs that forward pass, a backward pass and Adam on the GPU.
+ * Parameter vector: per layer W^T [out][in] (row-major, widths padded to 32/256) then the bias. */
+typedef struct tc_mlp tc_mlp;
+typedef struct { int32_t gemm; int64_t n_params; int64_t adam_steps; } tc_mlp_diag;
+
+tc_status tc_mlp_create(uint64_t seed, tc_mlp** out);
+void tc_mlp_destroy(tc_mlp* mlp);
+tc_status tc_mlp_n_params(const tc_mlp* mlp, int64_t* n);
+tc_status tc_mlp_get_params(const tc_mlp* mlp, float* host, int64_t n);
+tc_status tc_mlp_set_params(tc_mlp* mlp, const float* host, int64_t n);
+/* normalization: in_mean[20], in_scale[20], out_mean[19], out_scale[19] (n = 78) */
+tc_status tc_mlp_set_normalization(tc_mlp* mlp, const float* host, int64_t n);
+/* tc_mlp_fit_normalization: set the normalization from a device training set (x [n][20]
+ * features, y [n][19] next states, FP32): means and standard deviations of the features and of
+ * the changes y - x[:19]; a constant column gets scale 1.  tc_mlp_get_normalization copies the
+ * current 78 values out. */
+tc_status tc_mlp_fit_normalization(tc_mlp* mlp, const float* x_dev, const float* y_dev, int64_t n);
+tc_status tc_mlp_get_normalization(const tc_mlp* mlp, float* host, int64_t n);
+/* 0 = tensor cores (tcgen05, default), 1 = SIMT reference kernels */
+tc_status tc_mlp_set_gemm(tc_mlp* mlp, int32_t impl);
+/* forward pass of normalized inputs x [n][20] -> normalized outputs y [n][19] (host arrays) */
+tc_status tc_mlp_forward(tc_mlp* mlp, const float* x, int64_t n, float* y);
+/* mean squared error over the 19 outputs of normalized targets t [n][19], and its gradient
+ * with respect to every parameter (host arrays), as one training step computes them */
+tc_status tc_mlp_gradients(tc_mlp* mlp, const float* x, const float* t, int64_t n, float* grads, float* loss);
+/* train on device arrays x [n][20] (raw features) and y [n][19] (raw next states): epochs of
+ * shuffled mini-batches, Adam (beta 0.9/0.999); loss_history[epochs] receives the mean batch loss */
+tc_status tc_mlp_train(tc_mlp* mlp, const float* x_dev, const float* y_dev, int64_t n, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, void* cuda_stream, float* loss_history);
+tc_status tc_mlp_diagnostics(const tc_mlp* mlp, tc_mlp_diag* out);
+
+/* tc_tp06_window: the exact model over a window, for data generation and as the judge of the
+ * surrogate: from in [19][n] (18 states then V, device FP32) and a constant stimulus istim [n]
+ * (pA/pF, or NULL), nsub split steps of the single cell (Eq. 2 with V advanced by forward Euler);
+ * out [19][n].  precision TC_FP64 or TC_FP32 arithmetic. */
+tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n, double dt, int32_t nsub,
+                         int32_t cell, int32_t precision, float* out_dev, void* cuda_stream);
+
+/* tc_set_surrogate: attach (mlp != NULL) or detach the surrogate to a TC_FP32 TP06 simulation.
+ * Every `window` steps each node's surrogate prediction is checked (finite, concentrations > 0,
+ * gates in [0,1] within 0.01, |V' - V| <= dv_max over the window, |dV/dt| <= dvdt_max on the
+ * step before); nodes that pass take the predicted states at once and use the window's
+ * effective ionic current I_stim - (V' - V)/(window dt) in every step of the window; all other
+ * nodes take the exact model step by step.  The network is not owned; keep it alive. */
+tc_status tc_set_surrogate(tc_sim* sim, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max);
+/* tc_surrogate_sample: append training pairs drawn from the simulation's current state (TP06,
+ * either precision) to device arrays x_dev [capacity][20] and y_dev [capacity][19].  For a
+ * sampled node, x = (18 states, V, stimulus current averaged over the next `window` steps in
+ * pA/pF) as FP32 and y = the exact single cell's 18 states and V after `window` steps from x,
+ * computed in FP64.  A real node is sampled unless |V^k - V^{k-1}| > dvdt_keep dt (when
+ * dvdt_keep > 0) or its exact window changes V by more than dv_keep mV (when dv_keep > 0); a
+ * node within rest_band mV of the resting potential is kept only with probability rest_keep (a
+ * counter-based draw from seed, the step index and the node).  Pairs are written in internal
+ * node order from *count on; *count is advanced and stops at capacity. */
+tc_status tc_surrogate_sample(tc_sim* sim, int32_t window, double rest_band, double rest_keep, double dv_keep,
+                              double dvdt_keep, uint64_t seed, float* x_dev, float* y_dev, int64_t capacity,
+                              int64_t* count);
+/* node-windows handled by the surrogate and by the exact fallback since tc_set_surrogate */
+tc_status tc_surrogate_usage(const tc_sim* sim, int64_t* surrogate_node_windows, int64_t* exact_node_windows);
 
 /* Thread-local message of the last error ("" if none). */
 const char* tc_last_error(void);

@@ -54,7 +54,7 @@ inline void tp06_rest_state(int /*cell*/, double* u, double* v0) {
 // instructions against roughly twice that for the library exp, which matters where FP64 issue
 // is scarce.  |x| >= 700 and NaN go to the library exp.
 // 2^(j/64) = kExp2Hi[j] + kExp2Lo[j], j = 0..63 (computed to 60 digits and split)
-__constant__ double kExp2Hi[64] = {
+static __constant__ double kExp2Hi[64] = {
     0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0,
     0x1.0874518759bc8p+0, 0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0,
     0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0, 0x1.172b83c7d517bp+0,
@@ -78,7 +78,7 @@ __constant__ double kExp2Hi[64] = {
     0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0,
     0x1.fa7c1819e90d8p+0,
 };
-__constant__ double kExp2Lo[64] = {
+static __constant__ double kExp2Lo[64] = {
     0x0.0p+0, -0x1.19083535b085dp-56, 0x1.d73e2a475b465p-55,
     0x1.186be4bb284ffp-57, 0x1.8a62e4adc610bp-54, 0x1.03a1727c57b53p-59,
     -0x1.6c51039449b3ap-54, -0x1.32fbf9af1369ep-54, -0x1.19041b9d78a76p-55,
@@ -102,8 +102,8 @@ __constant__ double kExp2Lo[64] = {
     -0x1.e9c23179c2893p-54, 0x1.dc7f486a4b6b0p-54, 0x1.9d3e12dd8a18bp-54,
     0x1.74853f3a5931ep-55,
 };
-__shared__ double s_exp2_hi[64];
-__shared__ double s_exp2_lo[64];
+static __shared__ double s_exp2_hi[64];
+static __shared__ double s_exp2_lo[64];
 
 __device__ __forceinline__ void exp2_table_init() {
   if (threadIdx.x < 64) {
@@ -229,21 +229,13 @@ __device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dt) {
   return inf + (u - inf) * mexp(-dt * rate);
 }
 
+// One operator-split step of a single cell: u (18 states, in/out) advances from (V, u^k) to
+// u^{k+1}; returns I_ion(V, u^{k+1}) in pA/pF.
 template <typename T>
-__global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
+__device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   using namespace tp06;
-  exp2_table_init();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < a.n_bar) a.bar[i].count = 0u;
-  if (i >= a.n) return;
-  const int64_t n = a.n;
-  const T V = a.V[i], Vp = a.Vp[i];
-  const T dt = T(a.dt);
-  T u[kTP06States];
-#pragma unroll
-  for (int j = 0; j < kTP06States; ++j) u[j] = a.state[j * n + i];
   const Tp06VFactors<T> vf = tp06_vfactors(V);
-  const Tp06Currents<T> c = tp06_currents(V, u, a.cell, vf);
+  const Tp06Currents<T> c = tp06_currents(V, u, cell, vf);
 
   // concentrations and Rbar: forward Euler from the rates at (V^k, u^k)
   T un[kTP06States];
@@ -319,7 +311,7 @@ __global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
     const T vr = V + T(40);
     un[17] = rl(u[17], rinf, T(9.5) * mexp(-vr * vr / T(1800)) + T(0.8), dt);
     T sinf, ts;
-    if (a.cell == 0) {
+    if (cell == 0) {
       sinf = T(1) / (T(1) + mexp((V + T(28)) / T(5)));
       const T vs = V + T(67);
       ts = T(1000) * mexp(-vs * vs / T(1000)) + T(8);
@@ -349,15 +341,61 @@ __global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
     un[15] = rl(u[15], T(0.6) / (T(1) + cs2) + T(0.4), T(80) / (T(1) + cs2) + T(2), dt);
   }
 #pragma unroll
-  for (int j = 0; j < kTP06States; ++j) a.state[j * n + i] = un[j];
-  // I_ion(V^k, u^{k+1}) in uA/mm^2
-  const T iion = T(a.cm) * tp06_currents(V, un, a.cell, vf).total();
+  for (int j = 0; j < kTP06States; ++j) u[j] = un[j];
+  return tp06_currents(V, u, cell, vf).total();
+}
+
+// (a1) Ionic update of the tissue, TP06.  With a learned surrogate attached, nodes flagged for it
+// carry the window's effective current instead (their states already hold the surrogate's
+// end-of-window prediction); all other nodes take the exact step.
+template <typename T>
+__global__ void __launch_bounds__(256) ionic_tp06_kernel(const IonicArgs<T> a) {
+  exp2_table_init();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n_bar) a.bar[i].count = 0u;
+  if (i >= a.n) return;
+  const int64_t n = a.n;
+  const T V = a.V[i], Vp = a.Vp[i];
+  T iion;
+  if (a.sur_flag && a.sur_flag[i]) {
+    iion = T(a.cm) * T(a.sur_iion[i]);
+  } else {
+    T u[kTP06States];
+#pragma unroll
+    for (int j = 0; j < kTP06States; ++j) u[j] = a.state[j * n + i];
+    iion = T(a.cm) * tp06_cell_step(V, u, a.cell, T(a.dt));
+#pragma unroll
+    for (int j = 0; j < kTP06States; ++j) a.state[j * n + i] = u[j];
+  }
   const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, *a.k_base + a.k_off));
   rhs_epilogue(a, i, V, Vp, iion, is);
 }
 
+// Exact single-cell windows: from (u, V) with a constant stimulus (pA/pF), nsub split steps of
+// the cell (states as in the tissue step, then V += dt (I_stim - I_ion)).  Inputs and outputs are
+// [19][n] FP32 (18 states, then V); the arithmetic is in T.
+template <typename T>
+__global__ void __launch_bounds__(256) tp06_window_kernel(int64_t n, const float* in, const float* istim,
+                                                        float* out, int cell, double dt, int nsub) {
+  exp2_table_init();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T u[kTP06States];
+#pragma unroll
+  for (int j = 0; j < kTP06States; ++j) u[j] = T(in[j * n + i]);
+  T V = T(in[kTP06States * n + i]);
+  const T is = istim ? T(istim[i]) : T(0);
+  for (int k = 0; k < nsub; ++k) {
+    const T iion = tp06_cell_step(V, u, cell, T(dt));
+    V = V + T(dt) * (is - iion);
+  }
+#pragma unroll
+  for (int j = 0; j < kTP06States; ++j) out[j * n + i] = float(u[j]);
+  out[kTP06States * n + i] = float(V);
+}
+
 // Self-test of exp_tang against the library exp on device (diagnostics of the ABI).
-__global__ void __launch_bounds__(256) exp_selftest_kernel(int64_t n, const double* x, double* y_fast,
+static __global__ void __launch_bounds__(256) exp_selftest_kernel(int64_t n, const double* x, double* y_fast,
                                                            double* y_ref) {
   exp2_table_init();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

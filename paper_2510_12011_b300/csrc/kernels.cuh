@@ -69,6 +69,8 @@ struct IonicArgs {
   int cell;               // TP06 cell type
   GridBar* bar;           // per-component barrier words, zeroed here for the PCG launch that
   int n_bar;              // follows on the stream
+  const uint8_t* sur_flag;   // learned-surrogate nodes of the current window (or null)
+  const float* sur_iion;     // their effective ionic current over the window, pA/pF
 };
 
 template <typename T>
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs<T> a) {
 }
 
 // Advances the device step index after a group of steps (the last node of a captured graph).
-__global__ void tick_kernel(long long* k_base, int add) { *k_base += add; }
+static __global__ void tick_kernel(long long* k_base, int add) { *k_base += add; }
 
 // (a2)-(a5) in one cooperative launch: r0 = b - A x0 from the two value streams of M and K,
 // the Jacobi-PCG loop of Algorithm 1 with the convergence decision taken identically by every

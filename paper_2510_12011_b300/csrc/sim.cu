@@ -18,6 +18,8 @@
 
 #include "ionic_tp06.cuh"
 #include "kernels.cuh"
+#include "mlp.cuh"
+#include "surrogate.h"
 #include "tc_internal.h"
 
 using namespace tc;
@@ -100,6 +102,15 @@ struct tc_sim {
   std::vector<Dev> allocs;
   double* pinned = nullptr;   // n_int doubles of page-locked staging for host reads/writes
   void* pinned_t = nullptr;   // n_int elements of the device type, page-locked
+  // learned ionic surrogate (not owned)
+  tc_mlp* sur = nullptr;
+  int sur_window = 10;
+  float sur_dv_max = 2.0f, sur_dvdt_max = 1.0f;
+  uint8_t* sur_flag = nullptr;
+  float *sur_iion = nullptr, *sur_raw = nullptr, *sur_zout = nullptr;
+  __nv_bfloat16* sur_a0 = nullptr;
+  unsigned long long* sur_counts = nullptr;
+  int* sur_err = nullptr;
 };
 
 namespace {
@@ -385,6 +396,8 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   ia.cell = s->cell;
   ia.bar = s->bar;
   ia.n_bar = s->n_comp;
+  ia.sur_flag = s->sur ? s->sur_flag : nullptr;
+  ia.sur_iion = s->sur ? s->sur_iion : nullptr;
   if (ev) {
     cudaEvent_t e = pooled_event(s, *ev);
     if (!e) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
@@ -454,7 +467,37 @@ tc_status launch_step_any(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<
                                  : launch_step<float>(s, iv, k_off, ev, marks);
 }
 
-// Capture kGraphSteps steps starting at buffer phase iv, followed by the index advance.
+// Surrogate inference at the start of a window: step *k_dev + k_off at buffer phase iv.
+tc_status launch_surrogate(tc_sim* s, int iv, int k_off) {
+  SurrogateStep q;
+  q.n = s->n_int;
+  q.state = static_cast<float*>(s->state);
+  q.V = static_cast<const float*>(s->V[iv]);
+  q.Vprev = static_cast<const float*>(s->V[(iv + 2) % 3]);
+  q.dinv = static_cast<const float*>(s->dinv);
+  q.stim_off = s->stim_off;
+  q.stim_ids = s->stim_ids;
+  q.stims = s->stims;
+  q.k_base = s->k_dev;
+  q.k_off = k_off;
+  q.win = s->sur_window;
+  q.cm = s->cm;
+  q.dt = s->dt;
+  q.dv_max = s->sur_dv_max;
+  q.dvdt_max = s->sur_dvdt_max;
+  q.a0 = s->sur_a0;
+  q.raw = s->sur_raw;
+  q.zout = s->sur_zout;
+  q.flag = s->sur_flag;
+  q.iion = s->sur_iion;
+  q.counts = s->sur_counts;
+  q.err = s->sur_err;
+  return surrogate_infer(s->sur, q, s->stream);
+}
+
+// Capture kGraphSteps steps starting at buffer phase iv, followed by the index advance.  With
+// the surrogate attached the group starts on a window boundary and kGraphSteps is a multiple of
+// the window, so the inference sits at fixed offsets inside the graph.
 tc_status capture_graph(tc_sim* s, int iv, cudaGraphExec_t* out) {
   cudaStream_t cs;
   CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -463,7 +506,10 @@ tc_status capture_graph(tc_sim* s, int iv, cudaGraphExec_t* out) {
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   tc_status st = TC_OK;
   if (e == cudaSuccess) {
-    for (int j = 0; j < kGraphSteps && st == TC_OK; ++j) st = launch_step_any(s, (iv + j) % 3, j, nullptr, nullptr);
+    for (int j = 0; j < kGraphSteps && st == TC_OK; ++j) {
+      if (s->sur && j % s->sur_window == 0) st = launch_surrogate(s, (iv + j) % 3, j);
+      if (st == TC_OK) st = launch_step_any(s, (iv + j) % 3, j, nullptr, nullptr);
+    }
     if (st == TC_OK) {
       tick_kernel<<<1, 1, 0, cs>>>(s->k_dev, kGraphSteps);
       e = cudaGetLastError();
@@ -489,6 +535,185 @@ struct Snapshot {
   long long k;
   int iv;
 };
+
+// ---- training pairs for the learned surrogate, drawn from the tissue's current state ----------
+
+template <typename T>
+struct SampleArgs {
+  int64_t n;
+  const T* state;               // [18][n]
+  const T* V;                   // V^k
+  const T* Vp;                  // V^{k-1}
+  const T* dinv;                // 0 on padding rows
+  const int32_t *stim_off, *stim_ids;
+  const StimDev* stims;
+  long long k0;
+  int win, cell;
+  double cm, dt, v_rest, rest_band, rest_keep, dv_keep, dvdt_keep;
+  uint64_t seed;
+  uint8_t* keep;                // [n] decision of the first pass
+  uint32_t* blk_count;          // [blocks]
+  const uint32_t* blk_off;      // [blocks + 1] exclusive offsets, total last
+  float* x;                     // [capacity][20]
+  float* y;                     // [capacity][19]
+  int64_t base, capacity;
+};
+
+// Features of node i (18 states, V, stimulus averaged over the window in pA/pF) as the FP32
+// values the network sees, and the exact cell's state after the window from them, in FP64.
+template <typename T>
+__device__ __forceinline__ void sample_window(const SampleArgs<T>& a, int64_t i, float* f, double* u, double& V) {
+  const int64_t n = a.n;
+  for (int j = 0; j < kTP06States; ++j) f[j] = (float)a.state[j * n + i];
+  f[18] = (float)a.V[i];
+  double is = 0.0;
+  for (int s = 0; s < a.win; ++s) is += stimulus_at(a.stim_off, a.stim_ids, a.stims, i, a.k0 + s);
+  f[19] = (float)(is / a.win / a.cm);
+  for (int j = 0; j < kTP06States; ++j) u[j] = (double)f[j];
+  V = (double)f[18];
+  for (int s = 0; s < a.win; ++s) {
+    const double iion = tp06_cell_step(V, u, a.cell, a.dt);
+    V += a.dt * ((double)f[19] - iion);
+  }
+}
+
+// A node is sampled unless it is a padding row, moved faster than dvdt_keep on the step before
+// the window (when dvdt_keep > 0), or its exact window changes V by more than dv_keep (when
+// dv_keep > 0) - the windows a deployed surrogate hands to the exact model anyway; a node within
+// rest_band of the resting potential is kept only with probability rest_keep, by a counter-based
+// draw (resting cells dominate a tissue and carry little information about the dynamics).
+template <typename T>
+__global__ void __launch_bounds__(256) sample_select_kernel(const SampleArgs<T> a) {
+  exp2_table_init();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool keep = i < a.n && a.dinv[i] != T(0);
+  if (keep && a.dvdt_keep > 0) keep = fabs((double)a.V[i] - (double)a.Vp[i]) <= a.dvdt_keep * a.dt;
+  if (keep && fabs((double)a.V[i] - a.v_rest) <= a.rest_band) {
+    uint64_t z = a.seed + (uint64_t)a.k0 * 0xD1B54A32D192ED03ull + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    keep = (double)(z >> 11) * (1.0 / 9007199254740992.0) < a.rest_keep;
+  }
+  if (keep && a.dv_keep > 0) {
+    float f[20];
+    double u[kTP06States], V;
+    sample_window(a, i, f, u, V);
+    keep = fabs(V - (double)f[18]) <= a.dv_keep;
+  }
+  if (i < a.n) a.keep[i] = keep ? 1 : 0;
+  const int c = __syncthreads_count(keep);
+  if (threadIdx.x == 0) a.blk_count[blockIdx.x] = (uint32_t)c;
+}
+
+// Exclusive scan of the per-block counts (one block; fixed order).
+__global__ void __launch_bounds__(1024) sample_scan_kernel(int nb, const uint32_t* cnt, uint32_t* off) {
+  __shared__ uint32_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (nb + 1023) / 1024;
+  const int lo = min(nb, t * per), hi = min(nb, lo + per);
+  uint32_t s = 0;
+  for (int b = lo; b < hi; ++b) s += cnt[b];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
+    for (int j = 0; j < 1024; ++j) {
+      const uint32_t v = part[j];
+      part[j] = run;
+      run += v;
+    }
+    off[nb] = run;
+  }
+  __syncthreads();
+  uint32_t run = part[t];
+  for (int b = lo; b < hi; ++b) {
+    off[b] = run;
+    run += cnt[b];
+  }
+}
+
+// Kept nodes write their pair at base + (rank among kept nodes in internal order).
+template <typename T>
+__global__ void __launch_bounds__(256) sample_write_kernel(const SampleArgs<T> a) {
+  exp2_table_init();
+  __shared__ uint32_t warp_base[8];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool keep = i < a.n && a.keep[i];
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_base[w] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t v = warp_base[j];
+      warp_base[j] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  if (!keep) return;
+  const int64_t pos = a.base + a.blk_off[blockIdx.x] + warp_base[w] + __popc(m & ((1u << lane) - 1u));
+  if (pos >= a.capacity) return;
+  float f[20];
+  double u[kTP06States], V;
+  sample_window(a, i, f, u, V);
+  float* xr = a.x + pos * 20;
+  for (int j = 0; j < 20; ++j) xr[j] = f[j];
+  float* yr = a.y + pos * 19;
+  for (int j = 0; j < kTP06States; ++j) yr[j] = (float)u[j];
+  yr[18] = (float)V;
+}
+
+template <typename T>
+tc_status surrogate_sample_t(tc_sim* s, int win, double rest_band, double rest_keep, double dv_keep,
+                             double dvdt_keep, uint64_t seed, float* x, float* y, int64_t capacity,
+                             int64_t* count) {
+  const int64_t n = s->n_int;
+  const int nb = (int)((n + 255) / 256);
+  uint32_t* cnt = nullptr;
+  const size_t words = (size_t)(2 * nb + 1) + (size_t)(n + 3) / 4;
+  CUDA_TRY(cudaMallocAsync(&cnt, words * sizeof(uint32_t), s->stream));
+  SampleArgs<T> a{};
+  a.n = n;
+  a.state = static_cast<const T*>(s->state);
+  a.V = static_cast<const T*>(s->V[s->iv]);
+  a.Vp = static_cast<const T*>(s->V[(s->iv + 2) % 3]);
+  a.dinv = static_cast<const T*>(s->dinv);
+  a.stim_off = s->stim_off;
+  a.stim_ids = s->stim_ids;
+  a.stims = s->stims;
+  a.k0 = s->k;
+  a.win = win;
+  a.cell = s->cell;
+  a.cm = s->cm;
+  a.dt = s->dt;
+  a.v_rest = s->v_rest;
+  a.rest_band = rest_band;
+  a.rest_keep = rest_keep;
+  a.dv_keep = dv_keep;
+  a.dvdt_keep = dvdt_keep;
+  a.seed = seed;
+  a.blk_count = cnt;
+  a.blk_off = cnt + nb;
+  a.keep = reinterpret_cast<uint8_t*>(cnt + 2 * nb + 1);
+  a.x = x;
+  a.y = y;
+  a.base = *count;
+  a.capacity = capacity;
+  sample_select_kernel<T><<<nb, 256, 0, s->stream>>>(a);
+  sample_scan_kernel<<<1, 1024, 0, s->stream>>>(nb, cnt, cnt + nb);
+  sample_write_kernel<T><<<nb, 256, 0, s->stream>>>(a);
+  uint32_t total = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, cnt + 2 * nb, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaFreeAsync(cnt, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate sampling");
+  *count = std::min<int64_t>(capacity, *count + (int64_t)total);
+  return TC_OK;
+}
 
 }  // namespace
 
@@ -825,32 +1050,49 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
   CUDA_TRY(cudaMemcpyAsync(s->k_dev, &k0, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
   size_t ev = 0;
   std::vector<size_t> marks;
-  int64_t done = 0;
-  // whole groups of kGraphSteps steps replay a captured graph (not while profiling per launch)
-  if (s->use_graphs && !s->prof && n_steps >= kGraphSteps) {
-    GraphCache& g = s->graphs[s->iv];
+  int64_t done = 0, graph_steps = 0;
+  // steps done .. done + cnt - 1 launched one by one, then the device index advanced
+  auto single_steps = [&](int64_t cnt) -> tc_status {
+    for (int64_t j = 0; j < cnt; ++j) {
+      const int ivj = (int)((s->iv + done + j) % 3);
+      const long long kj = s->k + done + j;
+      if (s->sur && kj % s->sur_window == 0) TRY(launch_surrogate(s, ivj, (int)j));
+      TRY(launch_step_any(s, ivj, (int)j, s->prof ? &ev : nullptr, &marks));
+    }
+    if (cnt > 0) {
+      tick_kernel<<<1, 1, 0, s->stream>>>(s->k_dev, (int)cnt);
+      CUDA_TRY(cudaGetLastError());
+    }
+    done += cnt;
+    return TC_OK;
+  };
+  // whole groups of kGraphSteps steps replay a captured graph (not while profiling per launch;
+  // with the surrogate only when the window divides the group, after steps up to a boundary)
+  const bool graphs = s->use_graphs && !s->prof && (!s->sur || kGraphSteps % s->sur_window == 0);
+  const int64_t lead = s->sur ? (s->sur_window - s->k % s->sur_window) % s->sur_window : 0;
+  if (graphs && n_steps >= lead + kGraphSteps) {
+    if (s->sur) TRY(surrogate_prepare(s->sur, s->n_int));
+    TRY(single_steps(lead));
+    const int iv0 = (int)((s->iv + done) % 3);
+    GraphCache& g = s->graphs[iv0];
     if (!g.valid) {
-      tc_status st = capture_graph(s, s->iv, &g.exec);
+      tc_status st = capture_graph(s, iv0, &g.exec);
       if (st == TC_OK) {
         g.valid = true;
-        g.iv = s->iv;
+        g.iv = iv0;
       } else {
         s->use_graphs = false;   // capture unsupported here: launch step by step instead
         clear_error();
       }
     }
     if (g.valid) {
-      for (; done + kGraphSteps <= n_steps; done += kGraphSteps)
+      for (; done + kGraphSteps <= n_steps; done += kGraphSteps) {
         CUDA_TRY(cudaGraphLaunch(g.exec, s->stream));
+        graph_steps += kGraphSteps;
+      }
     }
   }
-  const int64_t rest = n_steps - done;
-  for (int64_t j = 0; j < rest; ++j)
-    TRY(launch_step_any(s, (int)((s->iv + done + j) % 3), (int)j, s->prof ? &ev : nullptr, &marks));
-  if (rest > 0) {
-    tick_kernel<<<1, 1, 0, s->stream>>>(s->k_dev, (int)rest);
-    CUDA_TRY(cudaGetLastError());
-  }
+  TRY(single_steps(n_steps - done));
   s->iv = (int)((s->iv + n_steps) % 3);
   s->k += n_steps;
   std::vector<DevStats> ds(s->n_comp);
@@ -889,9 +1131,77 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
     stats->not_converged = not_conv;
     stats->last_znorm = zn;
     stats->last_z0norm = z0n;
+    stats->graph_steps = graph_steps;
   }
   if (herr & kErrTimeout) return fail(TC_ERR_TIMEOUT, "a grid barrier wait hit its limit");
   if (herr & kErrNan) return fail(TC_ERR_NAN, "non-finite value in the PCG solve");
+  if (s->sur) {
+    int serr = 0;
+    CUDA_TRY(cudaMemcpy(&serr, s->sur_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (serr) return fail(TC_ERR_TIMEOUT, "a tensor-core wait of the surrogate hit its limit");
+  }
+  return TC_OK;
+}
+
+tc_status tc_set_surrogate(tc_sim* s, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  if (!mlp) {
+    if (s->sur) drop_graphs(s);   // captured groups hold the surrogate's launches
+    s->sur = nullptr;
+    return TC_OK;
+  }
+  if (s->precision != TC_FP32 || s->model != TC_MODEL_TP06)
+    return fail(TC_ERR_ARG, "the learned surrogate serves TC_FP32 simulations of TP06");
+  if (window < 1 || !(dv_max > 0) || !(dvdt_max > 0))
+    return fail(TC_ERR_ARG, "need window >= 1, dv_max > 0, dvdt_max > 0");
+  CUDA_TRY(cudaSetDevice(s->device));
+  if (!s->sur_flag) {
+    const int64_t n = s->n_int;
+    TRY(dalloc(s, &s->sur_flag, n));
+    TRY(dalloc(s, &s->sur_iion, n));
+    TRY(dalloc(s, &s->sur_raw, 20 * n));
+    TRY(dalloc(s, &s->sur_zout, 32 * n));
+    TRY(dalloc(s, &s->sur_a0, (size_t)kMlpIn0 * n));
+    TRY(dalloc(s, &s->sur_counts, 2));
+    TRY(dalloc(s, &s->sur_err, 1));
+    CUDA_TRY(cudaMemset(s->sur_flag, 0, n));
+  }
+  CUDA_TRY(cudaMemset(s->sur_counts, 0, 2 * sizeof(unsigned long long)));
+  CUDA_TRY(cudaMemset(s->sur_err, 0, sizeof(int)));
+  s->sur = mlp;
+  s->sur_window = window;
+  s->sur_dv_max = (float)dv_max;
+  s->sur_dvdt_max = (float)dvdt_max;
+  drop_graphs(s);
+  return TC_OK;
+}
+
+tc_status tc_surrogate_sample(tc_sim* s, int32_t window, double rest_band, double rest_keep, double dv_keep,
+                              double dvdt_keep, uint64_t seed, float* x_dev, float* y_dev, int64_t capacity,
+                              int64_t* count) {
+  clear_error();
+  if (!s || !x_dev || !y_dev || !count) return fail(TC_ERR_ARG, "null argument");
+  if (s->model != TC_MODEL_TP06) return fail(TC_ERR_STATE, "sampling needs the TP06 model");
+  if (window < 1 || !(rest_band >= 0) || !(rest_keep >= 0 && rest_keep <= 1) || !(dv_keep >= 0) ||
+      !(dvdt_keep >= 0) || capacity < 0 || *count < 0 || *count > capacity)
+    return fail(TC_ERR_ARG, "bad sampling arguments");
+  if (*count == capacity) return TC_OK;
+  CUDA_TRY(cudaSetDevice(s->device));
+  return s->precision == TC_FP64
+             ? surrogate_sample_t<double>(s, window, rest_band, rest_keep, dv_keep, dvdt_keep, seed, x_dev, y_dev,
+                                          capacity, count)
+             : surrogate_sample_t<float>(s, window, rest_band, rest_keep, dv_keep, dvdt_keep, seed, x_dev, y_dev,
+                                         capacity, count);
+}
+
+tc_status tc_surrogate_usage(const tc_sim* s, int64_t* surrogate_node_windows, int64_t* exact_node_windows) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  unsigned long long c[2] = {0, 0};
+  if (s->sur_counts) CUDA_TRY(cudaMemcpy(c, s->sur_counts, sizeof(c), cudaMemcpyDeviceToHost));
+  if (surrogate_node_windows) *surrogate_node_windows = (int64_t)c[0];
+  if (exact_node_windows) *exact_node_windows = (int64_t)c[1];
   return TC_OK;
 }
 

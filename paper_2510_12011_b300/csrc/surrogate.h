@@ -1,0 +1,44 @@
+// Internal interface between the simulation (sim.cu) and the learned surrogate (mlp.cu).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/tc.h"
+#include "kernels.cuh"
+
+namespace tc {
+
+// One window start of the surrogate inside a TP06 FP32 simulation.
+struct SurrogateStep {
+  int64_t n;                    // internal rows
+  float* state;                 // [18][n] TP06 states (written for nodes that pass the check)
+  const float* V;               // V^k
+  const float* Vprev;           // V^{k-1}
+  const float* dinv;            // 0 on padding rows (neither flagged nor counted)
+  const int32_t* stim_off;
+  const int32_t* stim_ids;
+  const StimDev* stims;
+  const long long* k_base;      // device step index of the launch group
+  int k_off;                    // first step of the window = *k_base + k_off
+  int win;                      // steps per window
+  double cm, dt;
+  float dv_max, dvdt_max;       // the check: |V' - V| over the window, |dV/dt| before it
+  __nv_bfloat16* a0;            // [n][64] scratch (split-BF16 inputs)
+  float* raw;                   // [20][n] scratch
+  float* zout;                  // [n][32] scratch
+  uint8_t* flag;                // [n] 1 = surrogate node for this window
+  float* iion;                  // [n] effective ionic current over the window, pA/pF
+  unsigned long long* counts;   // [2] surrogate / exact node-windows
+  int* err;                     // tensor-core wait failures
+};
+
+tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st);
+
+// Everything surrogate_infer needs that must not happen inside a stream capture (workspace
+// allocation, kernel attributes), done ahead for n rows.
+tc_status surrogate_prepare(tc_mlp* m, int64_t n);
+
+}  // namespace tc

@@ -288,6 +288,51 @@ def batched_slabs(count: int = 64, seed: int = 4, h: float = 0.25, t_end: float 
     return join_workloads(parts, name=f"batch{count}_slabs_h{h:g}_ms")
 
 
+def _site_nodes(m: Mesh, site: int, radius_mm: float) -> np.ndarray:
+    """Nodes within radius_mm (max-norm on the unjittered lattice) of node `site`."""
+    d = np.abs(m.lattice - m.lattice[site]).max(axis=1) * m.h
+    return np.nonzero(d <= radius_mm + 1e-9)[0].astype(np.int32)
+
+
+def _boundary_site(m: Mesh, u: float) -> int:
+    dims = np.array(m.shape)
+    on_face = np.any((m.lattice == 0) | (m.lattice == dims - 1), axis=1)
+    b = np.nonzero(on_face)[0]
+    return int(b[int(u * b.size) % b.size])
+
+
+def surrogate_training_slabs(count: int = 4, seed: int = 21, h: float = 0.25,
+                             t_end: float = 600.0) -> list:
+    """TP06 (epicardial) slabs that supply the learned surrogate's training pairs.
+
+    Each is 16x8x3 mm at spacing h with jitter U(+-0.15h) (seed + slab index) and fibres
+    rotating -60..+60 deg through the depth; both conductivities are scaled by U(0.7, 1.3); an
+    S1 (2 ms at 0.5 uA/mm^2) around a seeded boundary site at t = 0 and an S2 (2 ms at
+    1.0 uA/mm^2) around another seeded site at U(320, 420) ms, whose premature beat (or block)
+    widens the range of states.  dt = 0.02 ms; solver tolerances as in the large slab."""
+    u = uniform01(seed, np.arange(6 * count, dtype=np.uint64)).reshape(count, 6)
+    out = []
+    for i in range(count):
+        m = slab_mesh(16.0, 8.0, 3.0, h, jitter=0.15, seed=seed + i, fibre="rotating")
+        g = 0.7 + 0.6 * u[i, 0]
+        s1 = _site_nodes(m, _boundary_site(m, u[i, 1]), 1.0)
+        s2 = _site_nodes(m, _boundary_site(m, u[i, 2]), 1.0)
+        t2 = 320.0 + 100.0 * u[i, 3]
+        out.append(Workload(f"tp06_train{i}", m, 0.17 * g, 0.019 * g, 140.0, 0.01, 0.5, 0.02, t_end,
+                            "tp06", stimuli=[Stimulus(s1, 0.0, 2.0, 0.5), Stimulus(s2, t2, 2.0, 1.0)],
+                            atol=1e-5, rtol=1e-5, max_iter=100))
+    return out
+
+
+def surrogate_test_slab(h: float = 0.25, t_end: float = 400.0) -> Workload:
+    """A TP06 slab the surrogate never saw: 20x8x3 mm at spacing h, jitter U(+-0.15h) seed 9,
+    rotating fibres, nominal conductivities, 1 mm corner S1 (2 ms at 0.5 uA/mm^2), dt = 0.02 ms."""
+    m = slab_mesh(20.0, 8.0, 3.0, h, jitter=0.15, seed=9, fibre="rotating")
+    return Workload(f"tp06_slab20x8x3_h{h:g}", m, 0.17, 0.019, 140.0, 0.01, 0.5, 0.02, t_end, "tp06",
+                    stimuli=[Stimulus(corner_nodes(m, 1.0), 0.0, 2.0, 0.5)], atol=1e-5, rtol=1e-5,
+                    max_iter=100)
+
+
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """Seeded uniform vector for operator tests."""
     return lo + (hi - lo) * uniform01(seed, np.arange(n, dtype=np.uint64))

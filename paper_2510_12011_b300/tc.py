@@ -35,7 +35,7 @@ class TcError(RuntimeError):
 class StepStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("step_index", C.c_int64), ("cg_iterations", C.c_int64),
                 ("max_iterations", C.c_int32), ("not_converged", C.c_int32),
-                ("last_znorm", C.c_double), ("last_z0norm", C.c_double)]
+                ("last_znorm", C.c_double), ("last_z0norm", C.c_double), ("graph_steps", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -88,8 +88,27 @@ _SIGS = {
     "tc_reset_profile": [_P],
     "tc_set_wait_limit": [_P, C.c_int64],
     "tc_selftest_exp": [_D, _D, _D, C.c_int64],
+    "tc_mlp_create": [C.c_uint64, C.POINTER(_P)],
+    "tc_mlp_n_params": [_P, _I64],
+    "tc_mlp_get_params": [_P, C.POINTER(C.c_float), C.c_int64],
+    "tc_mlp_set_params": [_P, C.POINTER(C.c_float), C.c_int64],
+    "tc_mlp_set_normalization": [_P, C.POINTER(C.c_float), C.c_int64],
+    "tc_mlp_set_gemm": [_P, C.c_int32],
+    "tc_mlp_fit_normalization": [_P, _P, _P, C.c_int64],
+    "tc_mlp_get_normalization": [_P, C.POINTER(C.c_float), C.c_int64],
+    "tc_mlp_forward": [_P, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_float)],
+    "tc_mlp_gradients": [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64,
+                         C.POINTER(C.c_float), C.POINTER(C.c_float)],
+    "tc_mlp_train": [_P, _P, _P, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, _P,
+                     C.POINTER(C.c_float)],
+    "tc_mlp_diagnostics": [_P, _P],
+    "tc_tp06_window": [_P, _P, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_int32, _P, _P],
+    "tc_set_surrogate": [_P, _P, C.c_int32, C.c_double, C.c_double],
+    "tc_surrogate_usage": [_P, _I64, _I64],
+    "tc_surrogate_sample": [_P, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64, _P, _P,
+                            C.c_int64, _I64],
 }
-_VOID = {"tc_mesh_destroy": [_P], "tc_sim_destroy": [_P]}
+_VOID = {"tc_mesh_destroy": [_P], "tc_sim_destroy": [_P], "tc_mlp_destroy": [_P]}
 _STR = {"tc_last_error": [], "tc_version": []}
 
 _lib = None
@@ -317,6 +336,25 @@ class Simulation:
     def set_graphs(self, on=True):
         _check(lib().tc_set_graphs(self._h, int(bool(on))))
 
+    def set_surrogate(self, mlp, window=10, dv_max=2.0, dvdt_max=1.0):
+        """Attach a trained Mlp (or None to detach) as the learned ionic surrogate."""
+        _check(lib().tc_set_surrogate(self._h, None if mlp is None else mlp._h, window, dv_max, dvdt_max))
+        self._mlp = mlp
+
+    def surrogate_sample(self, x_dev, y_dev, capacity, count, window=10, rest_band=1.0, rest_keep=0.05,
+                         dv_keep=0.0, dvdt_keep=0.0, seed=0):
+        """Append training pairs from the current state to device arrays [capacity][20] and
+        [capacity][19] (pointers); returns the new count."""
+        c = C.c_int64(count)
+        _check(lib().tc_surrogate_sample(self._h, window, rest_band, rest_keep, dv_keep, dvdt_keep, seed,
+                                         _P(x_dev), _P(y_dev), capacity, C.byref(c)))
+        return c.value
+
+    def surrogate_usage(self):
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().tc_surrogate_usage(self._h, C.byref(a), C.byref(b)))
+        return {"surrogate": a.value, "exact": b.value}
+
     def set_profiling(self, on=True):
         _check(lib().tc_set_profiling(self._h, int(bool(on))))
 
@@ -344,6 +382,88 @@ def set_model(sim, w):
         sim.set_ionic(TC_MODEL_TP06, [float(w.tp06_cell)])
     else:
         raise TcError(TC_ERR_ARG, f"model {w.model!r} is not available")
+
+
+_F = C.POINTER(C.c_float)
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a if shape is None else a.reshape(shape)
+
+
+class Mlp:
+    """tc_mlp: the learned ionic surrogate's network (device-resident)."""
+    N_IN, N_OUT = 20, 19
+    GEMM_TC, GEMM_SIMT = 0, 1
+
+    def __init__(self, seed=0):
+        h = _P()
+        _check(lib().tc_mlp_create(seed, C.byref(h)))
+        self._h = h
+        n = C.c_int64()
+        _check(lib().tc_mlp_n_params(self._h, C.byref(n)))
+        self.n_params = n.value
+
+    def params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().tc_mlp_get_params(self._h, out.ctypes.data_as(_F), out.size))
+        return out
+
+    def set_params(self, p):
+        p = _f32(p)
+        _check(lib().tc_mlp_set_params(self._h, p.ctypes.data_as(_F), p.size))
+
+    def set_normalization(self, in_mean, in_scale, out_mean, out_scale):
+        v = _f32(np.concatenate([in_mean, in_scale, out_mean, out_scale]))
+        _check(lib().tc_mlp_set_normalization(self._h, v.ctypes.data_as(_F), v.size))
+
+    def fit_normalization(self, x_dev, y_dev, n):
+        """Normalization from a device training set (pointers to [n][20] and [n][19] FP32)."""
+        _check(lib().tc_mlp_fit_normalization(self._h, _P(x_dev), _P(y_dev), n))
+
+    def normalization(self):
+        v = np.empty(2 * self.N_IN + 2 * self.N_OUT, dtype=np.float32)
+        _check(lib().tc_mlp_get_normalization(self._h, v.ctypes.data_as(_F), v.size))
+        return v
+
+    def set_gemm(self, impl):
+        _check(lib().tc_mlp_set_gemm(self._h, impl))
+
+    def forward(self, x):
+        x = _f32(x).reshape(-1, self.N_IN)
+        y = np.empty((x.shape[0], self.N_OUT), dtype=np.float32)
+        _check(lib().tc_mlp_forward(self._h, x.ctypes.data_as(_F), x.shape[0], y.ctypes.data_as(_F)))
+        return y
+
+    def gradients(self, x, t):
+        x = _f32(x).reshape(-1, self.N_IN)
+        t = _f32(t).reshape(-1, self.N_OUT)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = C.c_float()
+        _check(lib().tc_mlp_gradients(self._h, x.ctypes.data_as(_F), t.ctypes.data_as(_F), x.shape[0],
+                                      g.ctypes.data_as(_F), C.byref(loss)))
+        return loss.value, g
+
+    def train(self, x_dev, y_dev, n, epochs, batch, lr, seed=0, stream=None):
+        """x_dev, y_dev: device pointers of [n][20] and [n][19] FP32 (e.g. torch data_ptr())."""
+        hist = np.zeros(epochs, dtype=np.float32)
+        _check(lib().tc_mlp_train(self._h, _P(x_dev), _P(y_dev), n, epochs, batch, lr, seed,
+                                  None if stream is None else _P(int(stream)), hist.ctypes.data_as(_F)))
+        return hist
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tc_mlp_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def tp06_window(in_ptr, istim_ptr, n, dt, nsub, cell, precision=TC_FP64, out_ptr=None, stream=None):
+    """Exact single-cell windows on device arrays ([19][n] in and out, istim [n] or None)."""
+    _check(lib().tc_tp06_window(_P(in_ptr), None if istim_ptr is None else _P(istim_ptr), n, dt, nsub, cell,
+                                precision, _P(out_ptr), None if stream is None else _P(int(stream))))
 
 
 def selftest_exp(x):

@@ -1,0 +1,100 @@
+"""The surrogate's network on the GPU: the tensor-core (tcgen05) forward pass against the SIMT
+reference, forward values and gradients against the FP64 oracle with the same BF16 rounding
+points, the exact single-cell window against the oracle, and a short training run."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from oracle import tp06 as otp06
+from paper_2510_12011_b300 import tc
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(seed=0):
+    rng = np.random.default_rng(seed)
+    offs, total = omlp.layout()
+    p = np.zeros(total)
+    for l, (w, b) in enumerate(offs):
+        fan = omlp.WIDTHS[l] + omlp.WIDTHS[l + 1]
+        W = rng.uniform(-1, 1, (omlp.WIDTHS[l + 1], omlp.WIDTHS[l])) * np.sqrt(6.0 / fan)
+        if l == 0:
+            W[:, omlp.N_IN:] = 0.0
+        if l == 4:
+            W[omlp.N_OUT:, :] = 0.0
+        p[w:b] = W.ravel()
+        bias = rng.normal(0, 0.1, omlp.WIDTHS[l + 1])
+        if l == 4:
+            bias[omlp.N_OUT:] = 0.0
+        p[b:b + omlp.WIDTHS[l + 1]] = bias
+    return p.astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def net():
+    m = tc.Mlp(seed=3)
+    m.set_params(_params())
+    return m
+
+
+def test_tensor_core_forward_matches_simt(net):
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(1000, 20)).astype(np.float32)    # 7 full 128-row tiles and a tail
+    net.set_gemm(tc.Mlp.GEMM_SIMT)
+    y_ref = net.forward(x)
+    net.set_gemm(tc.Mlp.GEMM_TC)
+    y_tc = net.forward(x)
+    err = np.linalg.norm(y_tc - y_ref) / np.linalg.norm(y_ref)
+    assert err < 1e-2, err
+    assert np.abs(y_tc - y_ref).max() < 0.05 * np.abs(y_ref).max()
+
+
+def test_forward_and_gradients_match_oracle(net):
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(300, 20)).astype(np.float32)
+    t = rng.normal(size=(300, 19)).astype(np.float32)
+    p = net.params().astype(np.float64)
+    y_o, _ = omlp.forward(p, x.astype(np.float64), bf=True)
+    for impl in (tc.Mlp.GEMM_TC, tc.Mlp.GEMM_SIMT):
+        net.set_gemm(impl)
+        y = net.forward(x)
+        assert np.linalg.norm(y - y_o) / np.linalg.norm(y_o) < 1e-2
+        loss, g = net.gradients(x, t)
+        loss_o, g_o = omlp.loss_and_grads(p, x.astype(np.float64), t.astype(np.float64), bf=True)
+        assert abs(loss - loss_o) <= 1e-3 * loss_o
+        assert np.linalg.norm(g - g_o) / np.linalg.norm(g_o) < 2e-2
+    net.set_gemm(tc.Mlp.GEMM_TC)
+
+
+def test_window_matches_oracle():
+    import torch
+    n = 64
+    V, u = otp06.rest(n)
+    V = np.linspace(-86.0, 30.0, n)
+    istim = np.where(np.arange(n) % 4 == 0, 20.0, 0.0)
+    # [19][n] row-major: the entry point reads raw pointers, so the layout must be C order
+    inp = np.ascontiguousarray(np.concatenate([u.T, V[None, :]], axis=0), dtype=np.float32)
+    x = torch.tensor(inp, device="cuda")
+    assert x.is_contiguous()
+    s = torch.tensor(istim.astype(np.float32), device="cuda")
+    out = torch.empty_like(x)
+    tc.tp06_window(x.data_ptr(), s.data_ptr(), n, 0.02, 10, 2, tc.TC_FP64, out.data_ptr())
+    got = out.cpu().numpy().astype(np.float64)
+    uw, Vw = omlp.window(inp[:18].T.astype(np.float64), inp[18].astype(np.float64),
+                         istim.astype(np.float32).astype(np.float64), 0.02, 10, 2)
+    assert np.allclose(got[18], Vw, rtol=1e-6, atol=1e-5)
+    assert np.allclose(got[:18].T, uw, rtol=1e-6, atol=1e-9)
+
+
+def test_short_training_reduces_loss():
+    import torch
+    rng = np.random.default_rng(7)
+    n = 20000
+    x = rng.normal(size=(n, 20)).astype(np.float32)
+    y = (x[:, :19] + 0.1 * np.tanh(x[:, :19] * x[:, 1:20])).astype(np.float32)   # a smooth map
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.tensor(y, device="cuda")
+    m = tc.Mlp(seed=11)
+    m.set_normalization(np.zeros(20), np.ones(20), np.zeros(19), 0.1 * np.ones(19))
+    hist = m.train(xd.data_ptr(), yd.data_ptr(), n, epochs=6, batch=512, lr=2e-3)
+    assert np.all(np.isfinite(hist)) and hist[-1] < 0.3 * hist[0], hist

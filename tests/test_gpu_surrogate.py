@@ -1,0 +1,161 @@
+"""The learned ionic surrogate inside the monodomain step: training pairs drawn from the tissue
+against the FP64 oracle's single-cell window, the normalization fit against its definition, the
+exact fallback, and a trained network against the exact model on a slab it never saw."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2510_12011_b300 import inputs, surrogate, tc
+
+pytestmark = pytest.mark.gpu
+
+
+def _tp06_small(t_end=40.0):
+    w = inputs.slab_custom(10.0, 4.0, 2.0, 0.5, model="tp06", dt=0.02, t_end=t_end, rtol=1e-5, atol=1e-5,
+                           max_iter=100)
+    w.tp06_cell = 2
+    return w
+
+
+def test_sampled_pairs_are_exact_windows():
+    import torch
+    w = _tp06_small()
+    sim = tc.from_workload(w, precision=tc.TC_FP32)
+    sim.step(400)                       # 8 ms: the wave is crossing the slab
+    n = w.mesh.n_nodes
+    x = torch.zeros((2 * n, 20), device="cuda")
+    y = torch.zeros((2 * n, 19), device="cuda")
+    cnt = sim.surrogate_sample(x.data_ptr(), y.data_ptr(), 2 * n, 0, window=10, rest_band=0.0, rest_keep=1.0)
+    assert cnt == n                     # every real node, once
+    V = np.sort(sim.read(tc.TC_FIELD_V).astype(np.float32))
+    xs, ys = x[:cnt].cpu().numpy(), y[:cnt].cpu().numpy()
+    assert np.array_equal(np.sort(xs[:, 18]), V)
+    assert np.all(xs[:, 19] == 0.0)     # the stimulus is over at 8 ms
+    # targets = the oracle's exact FP64 window from the same FP32 starting point
+    rows = np.random.default_rng(0).choice(cnt, 200, replace=False)
+    u0 = xs[rows, :18].astype(np.float64)
+    V0 = xs[rows, 18].astype(np.float64)
+    uw, Vw = omlp.window(u0, V0, np.zeros(rows.size), 0.02, 10, 2)
+    assert np.allclose(ys[rows, 18], Vw, rtol=2e-6, atol=2e-5)
+    assert np.allclose(ys[rows, :18], uw, rtol=2e-6, atol=1e-9)
+    # capacity bounds the count; rest nodes are subsampled
+    c2 = sim.surrogate_sample(x.data_ptr(), y.data_ptr(), cnt + 10, cnt, rest_band=0.0, rest_keep=1.0)
+    assert c2 == cnt + 10
+    sim.close()
+
+
+def test_sampling_filter_bounds_the_window_change():
+    import torch
+    w = _tp06_small()
+    sim = tc.from_workload(w, precision=tc.TC_FP32)
+    sim.step(150)                       # 3 ms: upstrokes under way near the stimulus
+    n = w.mesh.n_nodes
+    x = torch.zeros((n, 20), device="cuda")
+    y = torch.zeros((n, 19), device="cuda")
+    c_all = sim.surrogate_sample(x.data_ptr(), y.data_ptr(), n, 0, rest_band=0.0, rest_keep=1.0)
+    d_all = (y[:c_all, 18] - x[:c_all, 18]).abs().cpu().numpy()
+    c = sim.surrogate_sample(x.data_ptr(), y.data_ptr(), n, 0, rest_band=0.0, rest_keep=1.0, dv_keep=2.0)
+    d = (y[:c, 18] - x[:c, 18]).abs().cpu().numpy()
+    assert c == int((d_all <= 2.0).sum()) and c < c_all
+    assert d.max() <= 2.0
+    sim.close()
+
+
+def test_sampling_keeps_fraction_of_rest():
+    import torch
+    w = _tp06_small()
+    sim = tc.from_workload(w, precision=tc.TC_FP32)
+    n = w.mesh.n_nodes
+    x = torch.zeros((n, 20), device="cuda")
+    y = torch.zeros((n, 19), device="cuda")
+    c = sim.surrogate_sample(x.data_ptr(), y.data_ptr(), n, 0, rest_band=1.0, rest_keep=0.25, seed=3)
+    assert 0.15 * n < c < 0.35 * n      # at rest every node is rest-like
+    c_again = sim.surrogate_sample(x.data_ptr(), y.data_ptr(), n, 0, rest_band=1.0, rest_keep=0.25, seed=3)
+    assert c_again == c                 # counter-based draw: reproducible
+    sim.close()
+
+
+def test_normalization_fit_matches_definition():
+    import torch
+    rng = np.random.default_rng(1)
+    xh = rng.normal(size=(5000, 20)).astype(np.float32) * np.linspace(0.1, 10, 20).astype(np.float32) + 3
+    xh[:, 19] = 0.0                                               # a constant column
+    yh = (xh[:, :19] + rng.normal(size=(5000, 19)) * 0.01 + 0.5).astype(np.float32)
+    m = tc.Mlp(seed=1)
+    x, y = torch.tensor(xh, device="cuda"), torch.tensor(yh, device="cuda")
+    m.fit_normalization(x.data_ptr(), y.data_ptr(), 5000)
+    v = m.normalization()
+    d = yh.astype(np.float64) - xh[:, :19].astype(np.float64)
+    sd_in = xh.astype(np.float64).std(axis=0)
+    sd_in[19] = 1.0
+    assert np.allclose(v[:20], xh.astype(np.float64).mean(axis=0), rtol=1e-6, atol=1e-6)
+    assert np.allclose(v[20:40], sd_in, rtol=1e-5)
+    assert np.allclose(v[40:59], d.mean(axis=0), rtol=1e-5, atol=1e-7)
+    assert np.allclose(v[59:78], d.std(axis=0), rtol=1e-4)
+
+
+def test_rejected_predictions_fall_back_to_the_exact_model():
+    w = _tp06_small(t_end=20.0)
+    m = tc.Mlp(seed=2)
+    # an output offset of +50 mV on V makes every prediction fail the |V' - V| <= dv_max check
+    norm = np.concatenate([np.zeros(20), np.ones(20), np.zeros(19), np.ones(19)])
+    norm[40 + 18] = 50.0
+    m.set_normalization(norm[:20], norm[20:40], norm[40:59], norm[59:78])
+    ref = tc.from_workload(w, precision=tc.TC_FP32)
+    sur = tc.from_workload(w, precision=tc.TC_FP32)
+    sur.set_surrogate(m, window=10, dv_max=2.0, dvdt_max=1.0)
+    ref.step(w.n_steps)
+    sur.step(w.n_steps)
+    assert np.array_equal(ref.read(tc.TC_FIELD_V), sur.read(tc.TC_FIELD_V))
+    assert np.array_equal(ref.activation_times(0.0), sur.activation_times(0.0))
+    u = sur.surrogate_usage()
+    assert u["surrogate"] == 0 and u["exact"] == w.mesh.n_nodes * (w.n_steps // 10)
+    ref.close()
+    sur.close()
+
+
+def test_surrogate_in_captured_graphs_matches_direct_launches():
+    """An untrained network scaled to predict almost no change passes every check; the step loop
+    replayed from captured graphs (window inference inside) must match launching step by step,
+    including a start off a window boundary and a remainder shorter than a graph."""
+    w = _tp06_small(t_end=20.0)
+    m = tc.Mlp(seed=4)
+    norm = np.concatenate([np.zeros(20), np.ones(20), np.zeros(19), 1e-6 * np.ones(19)])
+    m.set_normalization(norm[:20], norm[20:40], norm[40:59], norm[59:78])
+    runs = []
+    for graphs in (True, False):
+        sim = tc.from_workload(w, precision=tc.TC_FP32)
+        sim.set_graphs(graphs)
+        sim.set_surrogate(m, window=10, dv_max=2.0, dvdt_max=1.0)
+        gsteps = 0
+        for n in (7, 95, 64, 300, 34):
+            gsteps += sim.step(n)["graph_steps"]
+        assert (gsteps > 0) == graphs
+        runs.append((sim.read(tc.TC_FIELD_V), sim.read(tc.TC_FIELD_STATE + 10), sim.surrogate_usage()))
+        sim.close()
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2] and runs[0][2]["surrogate"] > 0
+
+
+@pytest.mark.slow
+def test_trained_surrogate_meets_accuracy_bar():
+    """Train on two seeded slabs, then run a slab the network never saw: FP32 + surrogate against
+    the FP64 exact model, activation times within 1 ms and APD90 within 2 %, with most
+    node-windows taken by the network."""
+    train_w = inputs.surrogate_training_slabs(count=2, t_end=500.0)
+    x, y, cnt = surrogate.generate(train_w, capacity=12_000_000)
+    assert cnt > 1_000_000
+    m, hist = surrogate.train(x, y, cnt, epochs=8)
+    assert hist[-1] < 0.05 * hist[0], hist
+    w = inputs.surrogate_test_slab(t_end=400.0)
+    ref = surrogate.run(w, tc.TC_FP64)
+    got = surrogate.run(w, tc.TC_FP32, mlp=m)
+    c = surrogate.compare(ref, got)
+    u = got["usage"]
+    frac = u["surrogate"] / max(1, u["surrogate"] + u["exact"])
+    print("surrogate", c, u, frac, ref["seconds"], got["seconds"])
+    assert c["act_only_one"] == 0 and c["act_nodes"] == w.mesh.n_nodes
+    assert c["act_err_max_ms"] <= 1.0
+    assert c["apd_nodes"] > 0.9 * w.mesh.n_nodes and c["apd_rel_err_max"] <= 0.02
+    assert frac > 0.5
+    assert got["seconds"] < ref["seconds"]
