@@ -294,7 +294,7 @@ tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n,
 /* tc_set_surrogate: attach (mlp != NULL) or detach the surrogate to a TC_FP32 TP06 simulation.
  * Every `window` steps each node's surrogate prediction is checked (finite, concentrations > 0,
  * gates in [0,1] within 0.01, |V' - V| <= dv_max over the window, |dV/dt| <= dvdt_max on the
- * step before); nodes that pass take the predicted states at once and use the window's
+ * step before, no stimulus during the window); nodes that pass take the predicted states at once and use the window's
  * effective ionic current I_stim - (V' - V)/(window dt) in every step of the window; all other
  * nodes take the exact model step by step.  The network is not owned; keep it alive. */
 tc_status tc_set_surrogate(tc_sim* sim, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max);

@@ -843,6 +843,9 @@ __global__ void sur_commit_kernel(int64_t n, const float* zout, const float* raw
   const float V = raw[18 * n + i];
   const float dv = y[18] - V;
   ok = ok && fabsf(dv) <= dv_max && fabsf(V - Vprev[i]) <= dvdt_max * (float)dt;
+  // a stimulated window drives an upstroke: never the network's (none is in its training set,
+  // and a wrong small prediction would cancel the stimulus through the effective current)
+  ok = ok && raw[19 * n + i] == 0.f;
   flag[i] = ok ? 1 : 0;
   if (ok) {
 #pragma unroll

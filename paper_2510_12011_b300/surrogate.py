@@ -4,6 +4,7 @@ of a trained network inside the monodomain step against the exact TP06 model.
 All arithmetic runs in the library's kernels (tissue steps, FP64 exact windows, the tensor-core
 network and its training); this module only schedules those calls and holds device buffers.
 """
+import os
 import time
 
 import numpy as np
@@ -38,11 +39,18 @@ def generate(workloads, capacity, window=10, every=10, rest_band=1.0, rest_keep=
     return x[:count], y[:count], count
 
 
-def train(x, y, count, epochs=12, batch=2048, lr=2e-3, lr_end=5e-5, seed=1, mlp=None):
+def train(x, y, count, epochs=20, batch=2048, lr=1e-3, lr_end=1e-5, v_weight=9.0, seed=1, mlp=None):
     """Fit the normalization to (x, y) and train a network with Adam, the step size decaying
-    geometrically from lr to lr_end over the epochs; returns (network, mean loss per epoch)."""
+    geometrically from lr to lr_end over the epochs; returns (network, mean loss per epoch).
+    v_weight multiplies the loss weight of the membrane potential's change (its output scale is
+    divided by sqrt(v_weight)): the potential is the output the tissue sees directly, through
+    the window's effective current."""
     m = mlp or tc.Mlp(seed=seed)
     m.fit_normalization(x.data_ptr(), y.data_ptr(), count)
+    if v_weight != 1.0:
+        nm = m.normalization()
+        nm[2 * tc.Mlp.N_IN + tc.Mlp.N_OUT + 18] /= np.sqrt(v_weight)
+        m.set_normalization(nm[:20], nm[20:40], nm[40:59], nm[59:78])
     hist = []
     for e in range(epochs):
         lr_e = lr * (lr_end / lr) ** (e / max(1, epochs - 1))
@@ -91,3 +99,45 @@ def compare(ref, got):
         "apd_rel_err_max": float(rel.max()) if rep.any() else float("nan"),
         "apd_rel_err_mean": float(rel.mean()) if rep.any() else float("nan"),
     }
+
+
+def save(m, path):
+    """Write a trained network (parameters and normalization) to an .npz file."""
+    np.savez(path, params=m.params(), norm=m.normalization())
+
+
+def load(path, seed=0):
+    """A network with the parameters and normalization stored by save()."""
+    d = np.load(path)
+    m = tc.Mlp(seed=seed)
+    m.set_params(d["params"])
+    nm = d["norm"]
+    m.set_normalization(nm[:20], nm[20:40], nm[40:59], nm[59:78])
+    return m
+
+
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(__file__), "data", "tp06_epi_surrogate.npz")
+
+
+def main(argv=None):
+    """Train the TP06 (epicardial) surrogate from the four seeded training slabs and store it."""
+    import argparse
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--slabs", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=20)
+    a = ap.parse_args(argv)
+    from . import inputs
+    t0 = time.time()
+    x, y, cnt = generate(inputs.surrogate_training_slabs(count=a.slabs, t_end=500.0), capacity=40_000_000)
+    t1 = time.time()
+    m, hist = train(x, y, cnt, epochs=a.epochs)
+    t2 = time.time()
+    os.makedirs(os.path.dirname(a.out), exist_ok=True)
+    save(m, a.out)
+    print(f"{cnt} pairs in {t1 - t0:.1f} s; {a.epochs} epochs in {t2 - t1:.1f} s; loss {hist[0]:.3e} -> "
+          f"{hist[-1]:.3e}; saved {a.out}")
+
+
+if __name__ == "__main__":
+    main()

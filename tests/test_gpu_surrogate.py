@@ -137,16 +137,8 @@ def test_surrogate_in_captured_graphs_matches_direct_launches():
     assert runs[0][2] == runs[1][2] and runs[0][2]["surrogate"] > 0
 
 
-@pytest.mark.slow
-def test_trained_surrogate_meets_accuracy_bar():
-    """Train on two seeded slabs, then run a slab the network never saw: FP32 + surrogate against
-    the FP64 exact model, activation times within 1 ms and APD90 within 2 %, with most
-    node-windows taken by the network."""
-    train_w = inputs.surrogate_training_slabs(count=2, t_end=500.0)
-    x, y, cnt = surrogate.generate(train_w, capacity=12_000_000)
-    assert cnt > 1_000_000
-    m, hist = surrogate.train(x, y, cnt, epochs=8)
-    assert hist[-1] < 0.05 * hist[0], hist
+def _check_against_exact(m):
+    """FP32 + surrogate against the FP64 exact model on a slab the network never saw."""
     w = inputs.surrogate_test_slab(t_end=400.0)
     ref = surrogate.run(w, tc.TC_FP64)
     got = surrogate.run(w, tc.TC_FP32, mlp=m)
@@ -156,6 +148,25 @@ def test_trained_surrogate_meets_accuracy_bar():
     print("surrogate", c, u, frac, ref["seconds"], got["seconds"])
     assert c["act_only_one"] == 0 and c["act_nodes"] == w.mesh.n_nodes
     assert c["act_err_max_ms"] <= 1.0
-    assert c["apd_nodes"] > 0.9 * w.mesh.n_nodes and c["apd_rel_err_max"] <= 0.02
+    assert c["apd_only_one"] == 0 and c["apd_nodes"] > 0.9 * w.mesh.n_nodes
+    assert c["apd_rel_err_max"] <= 0.02
     assert frac > 0.5
     assert got["seconds"] < ref["seconds"]
+
+
+def test_stored_surrogate_meets_accuracy_bar():
+    """The network shipped with the package (trained by ``python -m
+    paper_2510_12011_b300.surrogate``): activation times within 1 ms and APD90 within 2 % of
+    the FP64 exact model, most node-windows taken by the network, faster than FP64."""
+    _check_against_exact(surrogate.load(surrogate.DEFAULT_WEIGHTS))
+
+
+@pytest.mark.slow
+def test_training_from_scratch_meets_accuracy_bar():
+    """The whole pipeline: pairs from the four seeded training slabs, normalization, training,
+    then the same bar on the unseen slab."""
+    x, y, cnt = surrogate.generate(inputs.surrogate_training_slabs(count=4, t_end=500.0), capacity=40_000_000)
+    assert cnt > 10_000_000
+    m, hist = surrogate.train(x, y, cnt)
+    assert hist[-1] < 0.05 * hist[0], hist
+    _check_against_exact(m)
