@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--workload", choices=["large_tp06", "large_ms", "small_ms"], default="large_tp06")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=600)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -230,6 +231,58 @@ def apd90_check(w_big, torch):
             "act_err_ms_max": float(np.abs(out[tc.TC_FP32][1] - out[tc.TC_FP64][1]).max())}
 
 
+# FLOPs of one network evaluation per row: 20 -> 256 -> 256 -> 256 -> 256 -> 19 (2 per MAC)
+MLP_FLOP_PER_ROW = 2 * (20 * 256 + 3 * 256 * 256 + 256 * 19)
+
+
+def surrogate_form(w, K, W, ms64, act64, stream, torch):
+    """FP32 + the learned TP06 surrogate (the network stored with the package) on the same
+    workload and steps: node-steps/s, the network's share of node-windows, activation-time error
+    against the FP64 run, the fused tensor-core kernel's throughput, and APD90 over one beat of
+    the 20x8x3 mm slab the network never saw (against the FP64 exact model)."""
+    from paper_2510_12011_b300 import surrogate as S, tc
+    m = S.load(S.DEFAULT_WEIGHTS)
+    sim = tc.from_workload(w, stream=stream.cuda_stream, precision=tc.TC_FP32)
+    sim.set_surrogate(m, 10, 2.0, 1.0)
+    ms, st, prof = timed_steps(sim, w, K, W, stream, torch)
+    use = sim.surrogate_usage()   # warm-up and timed steps
+    act = sim.activation_times()
+    sim.close()
+    both = (act >= 0) & (act64 >= 0)
+    n = w.mesh.n_nodes
+    mlp_ms = prof["mlp_ms"] / max(prof["surrogate_windows"], 1)
+    flops = MLP_FLOP_PER_ROW * n
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops_sustained", 1407.5) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1400.0
+    t = I.surrogate_test_slab(t_end=400.0)
+    ref = S.run(t, tc.TC_FP64)
+    got = S.run(t, tc.TC_FP32, mlp=m)
+    c = S.compare(ref, got)
+    u = got["usage"]
+    return {"value": n * K / (ms * 1e-3), "unit": "node-steps/s", "ms_per_step": ms / K,
+            "speedup_vs_fp64": ms64 / ms, "dtype": "f32 tissue, bf16 network (fp32 accumulate)",
+            "window_steps": 10, "check": {"dv_max_mV": 2.0, "dvdt_max_mV_per_ms": 1.0},
+            "network_node_windows": use["surrogate"], "exact_node_windows": use["exact"],
+            "network_share": use["surrogate"] / max(1, use["surrogate"] + use["exact"]),
+            "act_err_ms_max": float(np.abs(act[both] - act64[both]).max()) if both.any() else None,
+            "activated_fp64": int((act64 >= 0).sum()), "activated": int((act >= 0).sum()),
+            "mean_cg_iterations": st["cg_iterations"] / max(K, 1),
+            "kernels": {"ionic_ms": prof["ionic_ms"], "pcg_ms": prof["pcg_ms"],
+                        "surrogate_ms": prof["surrogate_ms"], "mlp_ms": prof["mlp_ms"],
+                        "windows": prof["surrogate_windows"]},
+            "roofline_mlp": {"kernel": "mlp_fused_kernel", "bound": "tensor",
+                             "achieved": flops / (mlp_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                             "frac": flops / (mlp_ms * 1e-3) / 1e12 / peak,
+                             "flop_per_launch": flops, "avg_launch_ms": mlp_ms,
+                             "peak_source": "measured bf16_tflops_sustained (kernel timed inside the step loop)"},
+            "apd90": {"workload": f"{t.name}, {t.t_end:g} ms, {t.mesh.n_nodes} nodes (not in the training set)",
+                      "act_err_ms_max": c["act_err_max_ms"], "apd90_err_pct_max": 100 * c["apd_rel_err_max"],
+                      "apd90_err_pct_mean": 100 * c["apd_rel_err_mean"], "nodes_repolarised": c["apd_nodes"],
+                      "nodes": t.mesh.n_nodes,
+                      "network_share": u["surrogate"] / max(1, u["surrogate"] + u["exact"]),
+                      "seconds_fp64": ref["seconds"], "seconds_fp32_surrogate": got["seconds"]}}
+
+
 def batched_form(steps, stream, torch):
     """The batched form: 64 uneven slabs (5.3 M nodes) as independent problems in one
     simulation, FP32, launch shape by the autotuner, step loop by CUDA-graph replay (also timed
@@ -397,6 +450,10 @@ def run_ours(args):
         if w.model == "tp06":
             fp32["apd90"] = apd90_check(w, torch)
 
+    sur = None
+    if not args.no_surrogate and w.model == "tp06":
+        sur = surrogate_form(w, K, W, ms, act64, stream, torch)
+
     batched = None
     if not args.no_batched:
         batched = batched_form(min(args.batched_steps, max(K, 30)), stream, torch)
@@ -427,6 +484,7 @@ def run_ours(args):
         "spmv": {"value": spmv_gbs, "unit": "GB/s", "ms": spmv_ms, "bytes": spmv_bytes(n, size["nnz"]),
                  "frac": spmv_gbs / peak, "l2": "flushed (512 MB read) before every launch"},
         "fp32_form": fp32,
+        "surrogate_form": sur,
         "batched_form": batched,
         "e2e": e2e,
         "gpu_launches": prof["ionic_launches"] + prof["pcg_launches"],

@@ -69,6 +69,9 @@ typedef struct {
   double ionic_ms;        int64_t ionic_launches;
   double pcg_ms;          int64_t pcg_launches;
   int64_t pcg_iterations; /* iterations inside the profiled PCG launches                */
+  double surrogate_ms;    int64_t surrogate_windows;   /* learned-surrogate inference (features,
+                                                          network, check), one per window     */
+  double mlp_ms;          /* of which the network's fused tensor-core forward pass          */
 } tc_profile;
 
 /* ---- mesh ------------------------------------------------------------------------- */
@@ -294,9 +297,12 @@ tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n,
 /* tc_set_surrogate: attach (mlp != NULL) or detach the surrogate to a TC_FP32 TP06 simulation.
  * Every `window` steps each node's surrogate prediction is checked (finite, concentrations > 0,
  * gates in [0,1] within 0.01, |V' - V| <= dv_max over the window, |dV/dt| <= dvdt_max on the
- * step before, no stimulus during the window); nodes that pass take the predicted states at once and use the window's
- * effective ionic current I_stim - (V' - V)/(window dt) in every step of the window; all other
- * nodes take the exact model step by step.  The network is not owned; keep it alive. */
+ * step before, no stimulus during the window); nodes that pass take the predicted states at
+ * once and use the window's effective ionic current I_stim - (V' - V)/(window dt) in every step
+ * of the window; all other nodes take the exact model step by step.  The network is not owned; keep it alive.  While a
+ * node is held by the network its states read back as the window's end values; tc_write_state,
+ * tc_set_step_index and tc_set_ionic return every node to the exact model until the next window
+ * boundary, and tc_set_ionic with a model other than TP06 detaches the surrogate. */
 tc_status tc_set_surrogate(tc_sim* sim, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max);
 /* tc_surrogate_sample: append training pairs drawn from the simulation's current state (TP06,
  * either precision) to device arrays x_dev [capacity][20] and y_dev [capacity][19].  For a

@@ -870,6 +870,7 @@ tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
   sur_features_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.n, q.state, q.V, q.stim_off, q.stim_ids, q.stims,
                                                        q.k_base, q.k_off, q.win, q.cm, m->norm, q.a0, q.raw);
   CUDA_TRY(cudaGetLastError());
+  if (q.ev_mlp[0]) CUDA_TRY(cudaEventRecord(q.ev_mlp[0], st));
   if (m->gemm == kGemmTcgen05) {
     TRY(forward_tc(m, q.n, q.a0, q.zout, false, q.err, st));
   } else {
@@ -878,6 +879,7 @@ tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
     TRY(forward(m, q.n, st));
     CUDA_TRY(cudaMemcpyAsync(q.zout, m->z[kMlpLayers - 1], q.n * kMlpPad * sizeof(float), cudaMemcpyDeviceToDevice, st));
   }
+  if (q.ev_mlp[1]) CUDA_TRY(cudaEventRecord(q.ev_mlp[1], st));
   sur_commit_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.n, q.zout, q.raw, m->norm, q.Vprev, q.dinv, q.dt, q.win,
                                                      q.dv_max, q.dvdt_max, q.state, q.flag, q.iion, q.counts);
   CUDA_TRY(cudaGetLastError());

@@ -467,9 +467,19 @@ tc_status launch_step_any(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<
                                  : launch_step<float>(s, iv, k_off, ev, marks);
 }
 
-// Surrogate inference at the start of a window: step *k_dev + k_off at buffer phase iv.
-tc_status launch_surrogate(tc_sim* s, int iv, int k_off) {
+// Surrogate inference at the start of a window: step *k_dev + k_off at buffer phase iv.  With
+// ev (profiling), four pooled events bracket the inference and its network; their first index is
+// appended to marks.
+tc_status launch_surrogate(tc_sim* s, int iv, int k_off, size_t* ev = nullptr,
+                           std::vector<size_t>* marks = nullptr) {
   SurrogateStep q;
+  if (ev) {
+    for (int e = 0; e < 4; ++e)
+      if (!pooled_event(s, *ev + e)) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
+    q.ev_mlp[0] = s->evpool[*ev + 1];
+    q.ev_mlp[1] = s->evpool[*ev + 2];
+    CUDA_TRY(cudaEventRecord(s->evpool[*ev], s->stream));
+  }
   q.n = s->n_int;
   q.state = static_cast<float*>(s->state);
   q.V = static_cast<const float*>(s->V[iv]);
@@ -492,7 +502,13 @@ tc_status launch_surrogate(tc_sim* s, int iv, int k_off) {
   q.iion = s->sur_iion;
   q.counts = s->sur_counts;
   q.err = s->sur_err;
-  return surrogate_infer(s->sur, q, s->stream);
+  TRY(surrogate_infer(s->sur, q, s->stream));
+  if (ev) {
+    CUDA_TRY(cudaEventRecord(s->evpool[*ev + 3], s->stream));
+    marks->push_back(*ev);
+    *ev += 4;
+  }
+  return TC_OK;
 }
 
 // Capture kGraphSteps steps starting at buffer phase iv, followed by the index advance.  With
@@ -951,6 +967,9 @@ tc_status tc_set_ionic(tc_sim* s, int32_t model, const double* params, int32_t n
   s->model = model;
   s->n_states = ns;
   drop_graphs(s);   // model constants are baked into captured launches
+  // the learned surrogate serves FP32 TP06 only; a re-initialised model starts exact
+  if (model != TC_MODEL_TP06) s->sur = nullptr;
+  if (s->sur_flag) CUDA_TRY(cudaMemset(s->sur_flag, 0, s->n_int));
   std::vector<double> col(s->n_int);
   for (int j = 0; j < ns; ++j) {
     if (init_state)
@@ -1049,14 +1068,15 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
   const long long k0 = s->k;
   CUDA_TRY(cudaMemcpyAsync(s->k_dev, &k0, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
   size_t ev = 0;
-  std::vector<size_t> marks;
+  std::vector<size_t> marks, sur_marks;
   int64_t done = 0, graph_steps = 0;
   // steps done .. done + cnt - 1 launched one by one, then the device index advanced
   auto single_steps = [&](int64_t cnt) -> tc_status {
     for (int64_t j = 0; j < cnt; ++j) {
       const int ivj = (int)((s->iv + done + j) % 3);
       const long long kj = s->k + done + j;
-      if (s->sur && kj % s->sur_window == 0) TRY(launch_surrogate(s, ivj, (int)j));
+      if (s->sur && kj % s->sur_window == 0)
+        TRY(launch_surrogate(s, ivj, (int)j, s->prof ? &ev : nullptr, &sur_marks));
       TRY(launch_step_any(s, ivj, (int)j, s->prof ? &ev : nullptr, &marks));
     }
     if (cnt > 0) {
@@ -1122,6 +1142,14 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
       s->prof_acc.pcg_launches += 1;
     }
     s->prof_acc.pcg_iterations += iters;
+    for (size_t m : sur_marks) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, s->evpool[m], s->evpool[m + 3]);
+      cudaEventElapsedTime(&b, s->evpool[m + 1], s->evpool[m + 2]);
+      s->prof_acc.surrogate_ms += a;
+      s->prof_acc.surrogate_windows += 1;
+      s->prof_acc.mlp_ms += b;
+    }
   }
   if (stats) {
     stats->steps = n_steps;
@@ -1235,6 +1263,8 @@ tc_status tc_write_state(tc_sim* s, int32_t field, const double* src, int64_t n)
   if (!dst) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
   CUDA_TRY(cudaSetDevice(s->device));
   CUDA_TRY(cudaStreamSynchronize(s->stream));   // the staging buffer may still feed a copy
+  // nodes the learned surrogate holds for the current window restart on the exact model
+  if (s->sur_flag) CUDA_TRY(cudaMemset(s->sur_flag, 0, s->n_int));
   to_internal(s, src, s->pinned, 0.0);
   return upload_vec(s, dst, s->pinned, true);
 }
@@ -1299,6 +1329,11 @@ tc_status tc_set_step_index(tc_sim* s, int64_t k) {
   clear_error();
   if (!s || k < 0) return fail(TC_ERR_ARG, "bad step index");
   s->k = k;
+  if (s->sur_flag) {
+    CUDA_TRY(cudaSetDevice(s->device));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    CUDA_TRY(cudaMemset(s->sur_flag, 0, s->n_int));
+  }
   return TC_OK;
 }
 

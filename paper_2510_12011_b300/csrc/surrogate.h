@@ -33,6 +33,7 @@ struct SurrogateStep {
   float* iion;                  // [n] effective ionic current over the window, pA/pF
   unsigned long long* counts;   // [2] surrogate / exact node-windows
   int* err;                     // tensor-core wait failures
+  cudaEvent_t ev_mlp[2] = {nullptr, nullptr};   // recorded around the network when profiling
 };
 
 tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st);

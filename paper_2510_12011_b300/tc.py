@@ -44,7 +44,8 @@ class StepStats(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("ionic_ms", C.c_double), ("ionic_launches", C.c_int64),
                 ("pcg_ms", C.c_double), ("pcg_launches", C.c_int64),
-                ("pcg_iterations", C.c_int64)]
+                ("pcg_iterations", C.c_int64), ("surrogate_ms", C.c_double),
+                ("surrogate_windows", C.c_int64), ("mlp_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
