@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-surrogate-apd", action="store_true",
+                    help="skip the surrogate's 400 ms APD90 check on the unseen slab")
     ap.add_argument("--batched-steps", type=int, default=600)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -235,7 +237,7 @@ def apd90_check(w_big, torch):
 MLP_FLOP_PER_ROW = 2 * (20 * 256 + 3 * 256 * 256 + 256 * 19)
 
 
-def surrogate_form(w, K, W, ms64, act64, stream, torch):
+def surrogate_form(w, K, W, ms64, act64, stream, torch, apd=True):
     """FP32 + the learned TP06 surrogate (the network stored with the package) on the same
     workload and steps: node-steps/s, the network's share of node-windows, activation-time error
     against the FP64 run, the fused tensor-core kernel's throughput, and APD90 over one beat of
@@ -254,11 +256,19 @@ def surrogate_form(w, K, W, ms64, act64, stream, torch):
     flops = MLP_FLOP_PER_ROW * n
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops_sustained", 1407.5) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1400.0
-    t = I.surrogate_test_slab(t_end=400.0)
-    ref = S.run(t, tc.TC_FP64)
-    got = S.run(t, tc.TC_FP32, mlp=m)
-    c = S.compare(ref, got)
-    u = got["usage"]
+    apd90 = None
+    if apd:
+        t = I.surrogate_test_slab(t_end=400.0)
+        ref = S.run(t, tc.TC_FP64)
+        got = S.run(t, tc.TC_FP32, mlp=m)
+        c = S.compare(ref, got)
+        u = got["usage"]
+        apd90 = {"workload": f"{t.name}, {t.t_end:g} ms, {t.mesh.n_nodes} nodes (not in the training set)",
+                 "act_err_ms_max": c["act_err_max_ms"], "apd90_err_pct_max": 100 * c["apd_rel_err_max"],
+                 "apd90_err_pct_mean": 100 * c["apd_rel_err_mean"], "nodes_repolarised": c["apd_nodes"],
+                 "nodes": t.mesh.n_nodes,
+                 "network_share": u["surrogate"] / max(1, u["surrogate"] + u["exact"]),
+                 "seconds_fp64": ref["seconds"], "seconds_fp32_surrogate": got["seconds"]}
     return {"value": n * K / (ms * 1e-3), "unit": "node-steps/s", "ms_per_step": ms / K,
             "speedup_vs_fp64": ms64 / ms, "dtype": "f32 tissue, bf16 network (fp32 accumulate)",
             "window_steps": 10, "check": {"dv_max_mV": 2.0, "dvdt_max_mV_per_ms": 1.0},
@@ -275,12 +285,7 @@ def surrogate_form(w, K, W, ms64, act64, stream, torch):
                              "frac": flops / (mlp_ms * 1e-3) / 1e12 / peak,
                              "flop_per_launch": flops, "avg_launch_ms": mlp_ms,
                              "peak_source": "measured bf16_tflops_sustained (kernel timed inside the step loop)"},
-            "apd90": {"workload": f"{t.name}, {t.t_end:g} ms, {t.mesh.n_nodes} nodes (not in the training set)",
-                      "act_err_ms_max": c["act_err_max_ms"], "apd90_err_pct_max": 100 * c["apd_rel_err_max"],
-                      "apd90_err_pct_mean": 100 * c["apd_rel_err_mean"], "nodes_repolarised": c["apd_nodes"],
-                      "nodes": t.mesh.n_nodes,
-                      "network_share": u["surrogate"] / max(1, u["surrogate"] + u["exact"]),
-                      "seconds_fp64": ref["seconds"], "seconds_fp32_surrogate": got["seconds"]}}
+            "apd90": apd90}
 
 
 def batched_form(steps, stream, torch):
@@ -452,7 +457,7 @@ def run_ours(args):
 
     sur = None
     if not args.no_surrogate and w.model == "tp06":
-        sur = surrogate_form(w, K, W, ms, act64, stream, torch)
+        sur = surrogate_form(w, K, W, ms, act64, stream, torch, apd=not args.no_surrogate_apd)
 
     batched = None
     if not args.no_batched:

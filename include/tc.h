@@ -287,6 +287,13 @@ tc_status tc_mlp_train(tc_mlp* mlp, const float* x_dev, const float* y_dev, int6
                        int32_t batch, float lr, uint64_t seed, void* cuda_stream, float* loss_history);
 tc_status tc_mlp_diagnostics(const tc_mlp* mlp, tc_mlp_diag* out);
 
+/* tc_gemm_bf16_nt: c [M][N] (FP32) = a [M][K] . b [N][K]^T on the tensor cores (tcgen05), a and b
+ * BF16 device arrays, row-major with K contiguous (K a multiple of 8); the GEMM the network's
+ * training pass is built from (weight and input gradients), exposed for direct checks.
+ * Synchronous on `cuda_stream`; TC_ERR_TIMEOUT if a device wait gave up. */
+tc_status tc_gemm_bf16_nt(const void* a_dev, const void* b_dev, float* c_dev, int32_t M, int32_t N, int32_t K,
+                          void* cuda_stream);
+
 /* tc_tp06_window: the exact model over a window, for data generation and as the judge of the
  * surrogate: from in [19][n] (18 states then V, device FP32) and a constant stimulus istim [n]
  * (pA/pF, or NULL), nsub split steps of the single cell (Eq. 2 with V advanced by forward Euler);

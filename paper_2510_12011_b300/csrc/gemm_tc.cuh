@@ -1,13 +1,17 @@
 // Fused MLP forward on the 5th-generation tensor cores (tcgen05, sm_100-family).
 //
-// One CTA (256 threads) owns 128 rows at a time.  For each layer:
+// One CTA (512 threads) owns 128 rows at a time.  For each layer:
 //   * the layer's weights W^T [N][K] arrive in shared memory as a pre-swizzled image through
-//     bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier);
+//     bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier); the copy of
+//     the next layer's image is issued as soon as this layer's MMAs have finished reading, so
+//     it overlaps the epilogue;
 //   * thread 0 issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) over K in steps of 16,
 //     accumulating the 128 x N tile in tensor memory, and commits to a second mbarrier;
-//   * eight warps read the accumulator back (tcgen05.ld), add the bias, apply SiLU and write
-//     the BF16 result straight into the swizzled shared-memory operand of the next layer
-//     (optionally also Z and the activation to global memory for the backward pass).
+//   * sixteen warps (four per tensor-memory lane quarter, each on a quarter of the columns)
+//     read the accumulator back (tcgen05.ld), add the bias (staged in shared memory once per
+//     CTA), apply SiLU and write the BF16 result straight into the swizzled shared-memory
+//     operand of the next layer (optionally also Z and the activation to global memory for the
+//     backward pass).
 // Activations therefore never leave the chip between layers.
 //
 // Shared-memory operand layout (K-major, 128-byte swizzle): K is cut into panels of 64
@@ -27,11 +31,12 @@
 
 namespace tc {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
+constexpr int kTcBias = 4 * kMlpHidden + kMlpPad;      // all biases, staged in shared memory
 constexpr int kTcRows = 128;
 constexpr uint32_t kTcSmemA = 4 * 128 * 128;            // 128 rows x 256 K, BF16
 constexpr uint32_t kTcSmemW = 4 * 256 * 128;            // 256 rows x 256 K, BF16
-constexpr uint32_t kTcSmemBytes = kTcSmemA + kTcSmemW + 1024;
+constexpr uint32_t kTcSmemBytes = kTcSmemA + kTcSmemW + 1024 + kTcBias * 4;
 constexpr long long kTcWaitLimit = 1ll << 24;
 
 struct MlpFusedArgs {
@@ -122,9 +127,9 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's tensor-memory lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// 32 consecutive FP32 columns of this thread's tensor-memory lane, as raw words; the values
+// are valid only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -135,10 +140,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Byte offset of 16-byte chunk `chunk` (0..7 inside a 64-element K panel) of row r in a
 // swizzled operand with `rows` rows per panel.
@@ -147,7 +151,22 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(int panel, int rows, i
          (uint32_t)((chunk ^ (r & 7)) * 16);
 }
 
-__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// SiLU z sigmoid(z) with sigmoid(z) = (1 + tanh(z/2)) / 2: one special-function operation.
+__device__ __forceinline__ float silu_fast(float z) { return z * fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
+
+// Issue the bulk copies of one layer's weight image into sW (thread 0).
+__device__ __forceinline__ void load_weights(uint8_t* sW, const uint8_t* img, uint32_t bytes, uint64_t* bar) {
+  mbar_expect_tx(bar, bytes);
+  for (uint32_t off = 0; off < bytes; off += 32768u) {
+    const uint32_t nb = bytes - off < 32768u ? bytes - off : 32768u;
+    bulk_copy_g2s(sW + off, img + off, nb, bar);
+  }
+}
 
 template <bool STORE>
 __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFusedArgs a) {
@@ -155,14 +174,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sW = smem + kTcSmemA;
+  float* sBias = reinterpret_cast<float*>(sW + kTcSmemW);
   __shared__ uint64_t bar_w, bar_mma;
   __shared__ uint32_t s_tmem;
-  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (a.M + kTcRows - 1) / kTcRows;
   if (tid == 0) {
     mbar_init(&bar_w, 1);
     mbar_init(&bar_mma, 1);
-    s_fail = 0;
+  }
+  {
+    int off = 0;
+    for (int l = 0; l < kMlpLayers; ++l) {
+      for (int c = tid; c < a.out[l]; c += kTcThreads) sBias[off + c] = a.bias[l][c];
+      off += a.out[l];
+    }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
@@ -174,37 +200,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
+  // Work thread 0 has outstanding on the two barriers (a weight copy, an MMA group) and the
+  // phase each completes; on a failure it waits for them before the CTA frees its memory.
+  bool pend_w = false, pend_m = false;
+  uint32_t pend_w_ph = 0, pend_m_ph = 0;
   uint32_t ph_w = 0, ph_m = 0;
-  const int64_t ntiles = (a.M + kTcRows - 1) / kTcRows;
+  bool bad = false;               // this thread saw a wait give up (sticky)
+  bool any_bad = false;           // some thread of the CTA did (uniform, from __syncthreads_or)
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles) {
+    load_weights(sW, a.img[0], a.img_bytes[0], &bar_w);   // layer 0 of the first tile
+    pend_w = true;
+    pend_w_ph = ph_w;
+  }
   const int q = warp & 3;        // tensor-memory lane quarter of this warp
-  const int half = warp >> 2;    // column half handled by this warp
+  const int cg = warp >> 2;      // column quarter handled by this warp
   const int row = 32 * q + lane;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < ntiles && !any_bad; tile += gridDim.x) {
     const int64_t row0 = tile * kTcRows;
     // inputs: 128 rows x 64 BF16 (one 128-byte panel row each) into panel 0
-    {
-      const int r = tid >> 1, c0 = (tid & 1) * 4;
+    for (int e = tid; e < kTcRows * 8; e += kTcThreads) {
+      const int r = e >> 3, c = e & 7;
       const int64_t gr = row0 + r;
-      for (int c = c0; c < c0 + 4; ++c) {
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (gr < a.M) v = *reinterpret_cast<const uint4*>(a.a0 + gr * kMlpIn0 + c * 8);
-        *reinterpret_cast<uint4*>(sA + sw128_offset(0, kTcRows, r, c)) = v;
-      }
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (gr < a.M) v = *reinterpret_cast<const uint4*>(a.a0 + gr * kMlpIn0 + c * 8);
+      *reinterpret_cast<uint4*>(sA + sw128_offset(0, kTcRows, r, c)) = v;
     }
     fence_proxy_async_smem();
+    int boff = 0;
     for (int l = 0; l < kMlpLayers; ++l) {
       const int K = a.in[l], N = a.out[l];
-      if (tid == 0) {
-        mbar_expect_tx(&bar_w, a.img_bytes[l]);
-        for (uint32_t off = 0; off < a.img_bytes[l]; off += 32768u) {
-          const uint32_t nb = a.img_bytes[l] - off < 32768u ? a.img_bytes[l] - off : 32768u;
-          bulk_copy_g2s(sW + off, a.img[l] + off, nb, &bar_w);
-        }
+      if (mbar_wait(&bar_w, ph_w)) {
+        if (tid == 0) pend_w = false;
+      } else {
+        bad = true;
       }
-      if (!mbar_wait(&bar_w, ph_w)) atomicOr(&s_fail, 1);
       ph_w ^= 1u;
-      __syncthreads();
-      if (s_fail) break;
+      any_bad = __syncthreads_or(bad);
+      if (any_bad) break;
       tc_fence_after();
       if (tid == 0) {
         const uint32_t idesc = umma_idesc_bf16(kTcRows, N);
@@ -216,24 +248,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
           umma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
         }
         umma_commit(&bar_mma);
+        pend_m = true;
+        pend_m_ph = ph_m;
       }
-      if (!mbar_wait(&bar_mma, ph_m)) atomicOr(&s_fail, 1);
+      if (mbar_wait(&bar_mma, ph_m)) {
+        if (tid == 0) pend_m = false;
+      } else {
+        bad = true;
+      }
       ph_m ^= 1u;
       tc_fence_after();
-      __syncthreads();
-      if (s_fail) break;
-      // epilogue: warp (q, half) handles lanes 32q..32q+31 and columns [half*N/2, (half+1)*N/2)
-      const int cols = N / 2 >= 32 ? N / 2 : 32;
-      const int cbeg = half * cols;
+      // the MMAs have read sW: start the next image (next layer, or layer 0 of the next tile)
+      if (tid == 0 && !bad) {
+        const bool more = l + 1 < kMlpLayers || tile + gridDim.x < ntiles;
+        if (more) {
+          const int nl = l + 1 < kMlpLayers ? l + 1 : 0;
+          load_weights(sW, a.img[nl], a.img_bytes[nl], &bar_w);
+          pend_w = true;
+          pend_w_ph = ph_w;
+        }
+      }
+      any_bad = __syncthreads_or(bad);
+      if (any_bad) break;
+      // epilogue: warp (q, cg) handles lanes 32q..32q+31 and a quarter of the columns
+      const int cols = N / 4 >= 32 ? N / 4 : 32;
+      const int cbeg = cg * cols;
       const int64_t grow = row0 + row;
       const bool valid = grow < a.M;
       if (cbeg < N) {
-        for (int c0 = cbeg; c0 < cbeg + cols && c0 < N; c0 += 32) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-          const float* b = a.bias[l] + c0;
+        const int nch = cols / 32;   // 1 or 2 chunks of 32 columns (uniform in the warp)
+        uint32_t raw[2][32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += b[j];
+        for (int ch = 0; ch < 2; ++ch)
+          if (ch < nch) tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cbeg + 32 * ch), raw[ch]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          if (ch >= nch) break;
+          const int c0 = cbeg + 32 * ch;
+          float v[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[ch][j]) + sBias[boff + c0 + j];
           if (l + 1 < kMlpLayers) {
             if (STORE && valid && a.z[l]) {
               float* zp = a.z[l] + grow * N + c0;
@@ -265,14 +320,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
           }
         }
       }
+      boff += N;
       fence_proxy_async_smem();
       tc_fence_before();
       __syncthreads();
     }
-    if (s_fail) break;
+  }
+  // after a failure: let thread 0's outstanding copy and MMA group land (bounded) before the
+  // shared and tensor memory go away
+  if (tid == 0 && any_bad) {
+    atomicOr(a.err, 1);
+    if (pend_m) mbar_wait(&bar_mma, pend_m_ph);
+    if (pend_w) mbar_wait(&bar_w, pend_w_ph);
   }
   __syncthreads();
-  if (s_fail && tid == 0) atomicOr(a.err, 1);
   tc_fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
@@ -298,5 +359,187 @@ static __global__ void weight_image_kernel(const __nv_bfloat16* wt, int N, int K
 }
 
 inline uint32_t weight_image_bytes(int N, int Kin) { return (uint32_t)((Kin + 63) / 64) * N * 128u; }
+
+}  // namespace tc
+
+namespace tc {
+
+// ---- generic NT GEMM on the tensor cores (the training pass) -------------------------------
+//
+// C[M][N] (FP32, row stride ldc) = A[M][K] . B[N][K]^T, A and B BF16 with K contiguous (row
+// strides lda, ldb in elements, multiples of 8), K a multiple of 8.  One CTA (128 threads) per
+// 128 x n_tile output tile (n_tile in {32, 64, 128, 256}); K in panels of 64 staged in shared
+// memory (128-byte swizzle, as above) through a two-stage cp.async pipeline, one elected thread
+// issuing the MMAs of a panel and committing them to that stage's mbarrier, which releases the
+// stage for the panel after next.  Rows, columns and K beyond the matrix are zero-filled.  With
+// blockIdx.z > 0 the CTA takes the z-th slice of K (kchunk, a multiple of 64) and writes its
+// partial product to C + z * split_stride.
+
+constexpr int kGemmThreads = 128;
+constexpr long long kGemmWaitLimit = 1ll << 24;
+
+struct GemmNTArgs {
+  int M, N, K, n_tile, kchunk;
+  const __nv_bfloat16* A;
+  int64_t lda;
+  const __nv_bfloat16* B;
+  int64_t ldb;
+  float* C;
+  int64_t ldc, split_stride;
+  int* err;
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Stage one 64-wide K panel (rows [r0, r0 + rows) of X, K range [k0, k0 + 64)) into a swizzled
+// operand of `rows` rows; entries outside rows_max x k_end are zero.
+__device__ __forceinline__ void stage_panel(uint8_t* dst, const __nv_bfloat16* X, int64_t ld, int r0, int rows,
+                                            int rows_max, int k0, int k_end) {
+  for (int e = threadIdx.x; e < rows * 8; e += kGemmThreads) {
+    const int r = e >> 3, c = e & 7;
+    const int gr = r0 + r, gk = k0 + 8 * c;
+    const bool ok = gr < rows_max && gk < k_end;
+    const __nv_bfloat16* src = ok ? X + (int64_t)gr * ld + gk : X;
+    cp_async16(dst + sw128_offset(0, rows, r, c), src, ok);
+  }
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_nt_kernel(const GemmNTArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nt = a.n_tile;
+  const uint32_t a_bytes = 128u * 128u, b_bytes = (uint32_t)nt * 128u;
+  const uint32_t stage_bytes = a_bytes + b_bytes;   // stage s: A at s * stage_bytes, B after it
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * nt;
+  const int kb = blockIdx.z * a.kchunk, ke = min(a.K, kb + a.kchunk);
+  const int np = (ke - kb + 63) / 64;
+  float* C = a.C + (int64_t)blockIdx.z * a.split_stride;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                 "r"(nt)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = umma_idesc_bf16(128, nt);
+  bool bad = false, any_bad = false;
+  uint32_t committed = 0;   // panels whose MMAs thread 0 has committed
+  uint32_t waited0 = 0, waited1 = 0;   // completed phases waited for, per stage
+  stage_panel(smem, a.A, a.lda, m0, 128, a.M, kb, ke);
+  stage_panel(smem + a_bytes, a.B, a.ldb, n0, nt, a.N, kb, ke);
+  cp_async_commit();
+  for (int p = 0; p < np; ++p) {
+    const int s = p & 1;
+    if (p + 1 < np) {
+      const int s1 = (p + 1) & 1;
+      // the stage of panel p+1 held panel p-1: its MMAs must have finished reading it
+      if (p >= 1) {
+        uint32_t& w = s1 ? waited1 : waited0;
+        if (!mbar_wait_limit(&bar[s1], w & 1u, kGemmWaitLimit)) bad = true;
+        ++w;
+      }
+      if (!bad) {
+        uint8_t* st = smem + s1 * stage_bytes;
+        stage_panel(st, a.A, a.lda, m0, 128, a.M, kb + 64 * (p + 1), ke);
+        stage_panel(st + a_bytes, a.B, a.ldb, n0, nt, a.N, kb + 64 * (p + 1), ke);
+      }
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    fence_proxy_async_smem();
+    any_bad = __syncthreads_or(bad);
+    if (any_bad) break;
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t sa = smem_addr(smem + s * stage_bytes);
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t ad = umma_desc_sw128(sa + 32u * ks);
+        const uint64_t bd = umma_desc_sw128(sa + a_bytes + 32u * ks);
+        umma_bf16(tmem, ad, bd, idesc, (p > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(&bar[s]);
+      committed++;
+    }
+  }
+  cp_async_wait<0>();
+  // every committed MMA group must complete before the accumulator is read or freed
+  if (tid == 0) {
+    for (uint32_t p = 0; p < committed; ++p) {
+      const int s = p & 1;
+      if ((p >> 1) < (s ? waited1 : waited0)) continue;   // already waited for
+      if (!mbar_wait_limit(&bar[s], (p >> 1) & 1u, kGemmWaitLimit)) bad = true;
+    }
+  }
+  any_bad = __syncthreads_or(bad) || any_bad;
+  tc_fence_after();
+  if (!any_bad && np > 0) {
+    const int row = m0 + 32 * warp + lane;
+    for (int c0 = 0; c0 < nt; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32_nowait(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+      tmem_wait_ld();
+      if (row < a.M) {
+        float* cp = C + (int64_t)row * a.ldc + n0 + c0;
+        const int lim = min(32, a.N - (n0 + c0));
+        if (lim == 32 && (((uintptr_t)cp) & 15) == 0) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<float4*>(cp + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                             __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < lim) cp[j] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  } else if (np == 0 && a.N > n0) {
+    // an empty K slice contributes zeros
+    const int row = m0 + 32 * warp + lane;
+    if (row < a.M)
+      for (int j = 0; j < nt && n0 + j < a.N; ++j) C[(int64_t)row * a.ldc + n0 + j] = 0.f;
+  }
+  if (any_bad && tid == 0) atomicOr(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(nt) : "memory");
+}
+
+inline uint32_t gemm_nt_smem_bytes(int n_tile) { return 2u * (128u * 128u + (uint32_t)n_tile * 128u) + 1024u; }
 
 }  // namespace tc

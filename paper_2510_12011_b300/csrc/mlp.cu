@@ -53,6 +53,9 @@ struct tc_mlp {
   float* loss = nullptr;                        // device scalar
   float* splitk = nullptr;                      // split-K partial products (kMaxSplits x 256 x 256)
   float* gw0d = nullptr;                        // gradient of the duplicated layer-0 weights [256][64]
+  // tensor-core backward pass: K-major BF16 copies of dZ^T, A_l^T, dZ and the weights W_l [in][out]
+  __nv_bfloat16 *dzT = nullptr, *actT = nullptr, *dzb = nullptr, *wT = nullptr;
+  int* gemm_err = nullptr;                      // wait failures of the GEMM kernel
 };
 
 namespace {
@@ -158,6 +161,79 @@ tc_status gemm_simt(int M, int N, int K, const TA* A, const TB* B, float* C, cud
     sum_splits_kernel<<<blocks_for(mn), 256, 0, st>>>(mn, splits, ws, C);
   }
   CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
+// out[c][r] = bf16(in[r][c]) for r < rows_out (zero where r >= rows), c < cols; 32 x 32 tiles.
+template <typename TI>
+__global__ void transpose_bf16_kernel(int rows, int rows_out, int cols, const TI* __restrict__ in, int64_t ld_in,
+                                      __nv_bfloat16* __restrict__ out, int64_t ld_out) {
+  __shared__ float t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = r0 + j, c = c0 + threadIdx.x;
+    t[j][threadIdx.x] = (r < rows && c < cols) ? to_f(in[(int64_t)r * ld_in + c]) : 0.f;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = c0 + j, r = r0 + threadIdx.x;
+    if (c < cols && r < rows_out) out[(int64_t)c * ld_out + r] = __float2bfloat16(t[threadIdx.x][j]);
+  }
+}
+
+template <typename TI>
+tc_status transpose_bf16(int rows, int rows_out, int cols, const TI* in, int64_t ld_in, __nv_bfloat16* out,
+                         int64_t ld_out, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows_out + 31) / 32);
+  transpose_bf16_kernel<TI><<<grid, dim3(32, 8), 0, st>>>(rows, rows_out, cols, in, ld_in, out, ld_out);
+  CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
+// FP32 [rows][cols] -> BF16 (same layout)
+__global__ void to_bf16_kernel(int64_t n, const float* in, __nv_bfloat16* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = __float2bfloat16(in[e]);
+}
+
+// C = A . B^T on the tensor cores (gemm_nt_kernel): A [M][K], B [N][K] BF16, C [M][N] FP32 with
+// row strides lda, ldb, ldc.  With ws (kMaxSplits M N floats) and a long K, K is split across
+// CTAs and the partial products summed in a fixed order.
+tc_status gemm_nt(int M, int N, int K, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B,
+                  int64_t ldb, float* C, int64_t ldc, cudaStream_t st, float* ws, int* err) {
+  if (M < 1 || N < 1 || K < 8 || (K & 7) || (lda & 7) || (ldb & 7)) return fail(TC_ERR_ARG, "bad GEMM shape");
+  const int nt = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+  const int tiles = ((N + nt - 1) / nt) * ((M + 127) / 128);
+  int splits = 1;
+  if (ws) splits = std::max(1, std::min({kMaxSplits, K / 128, (148 + tiles - 1) / tiles}));
+  int kchunk = ((K + splits - 1) / splits + 63) / 64 * 64;
+  splits = (K + kchunk - 1) / kchunk;
+  GemmNTArgs a{};
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.n_tile = nt;
+  a.kchunk = kchunk;
+  a.A = A;
+  a.lda = lda;
+  a.B = B;
+  a.ldb = ldb;
+  a.C = splits > 1 ? ws : C;
+  a.ldc = splits > 1 ? N : ldc;
+  a.split_stride = (int64_t)M * N;
+  a.err = err;
+  dim3 grid((N + nt - 1) / nt, (M + 127) / 128, splits);
+  gemm_nt_kernel<<<grid, kGemmThreads, gemm_nt_smem_bytes(nt), st>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  if (splits > 1) {
+    const int64_t mn = (int64_t)M * N;
+    if (ldc == N) {
+      sum_splits_kernel<<<blocks_for(mn), 256, 0, st>>>(mn, splits, ws, C);
+    } else {
+      return fail(TC_ERR_ARG, "split-K output must be dense");
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
   return TC_OK;
 }
 
@@ -345,6 +421,10 @@ tc_status rebuild_images(tc_mlp* m, cudaStream_t st) {
     weight_image_kernel<<<(unsigned)((chunks + 255) / 256), 256, 0, st>>>(w, m->d.out[l], m->d.op_in[l],
                                                                         m->img + m->img_off[l]);
   }
+  // W_l as [in][out] (K-major operand of dA = dZ W) for the hidden and output layers
+  for (int l = 1; l < kMlpLayers; ++l)
+    TRY((transpose_bf16<__nv_bfloat16>(m->d.out[l], m->d.out[l], m->d.in[l], m->wt + m->d.w_off[l], m->d.in[l],
+                                       m->wT + m->d.w_off[l], m->d.out[l], st)));
   CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }
@@ -403,6 +483,13 @@ tc_status ensure_workspace(tc_mlp* m, int64_t rows) {
   CUDA_TRY(cudaMalloc(&m->idx, r * sizeof(int32_t)));
   if (!m->splitk) CUDA_TRY(cudaMalloc(&m->splitk, (size_t)kMaxSplits * kMlpHidden * kMlpHidden * sizeof(float)));
   if (!m->gw0d) CUDA_TRY(cudaMalloc(&m->gw0d, (size_t)kMlpHidden * kMlpIn0 * sizeof(float)));
+  cudaFree(m->dzT);
+  cudaFree(m->actT);
+  cudaFree(m->dzb);
+  m->dzT = m->actT = m->dzb = nullptr;
+  CUDA_TRY(cudaMalloc(&m->dzT, r * kMlpHidden * sizeof(__nv_bfloat16)));
+  CUDA_TRY(cudaMalloc(&m->actT, r * kMlpHidden * sizeof(__nv_bfloat16)));
+  CUDA_TRY(cudaMalloc(&m->dzb, r * kMlpHidden * sizeof(__nv_bfloat16)));
   m->ws_rows = r;
   return TC_OK;
 }
@@ -426,8 +513,43 @@ tc_status forward(tc_mlp* m, int64_t rows, cudaStream_t st) {
   return TC_OK;
 }
 
+// Backward pass on the tensor cores: per layer the weight gradient dW^T = dZ^T A (K = batch
+// rows, split across CTAs) and the input gradient dA = dZ W (K = layer width), both as NT GEMMs on
+// K-major BF16 copies (dZ^T, A^T, dZ, W as [in][out]); FP32 accumulation, FP32 dZ kept for the
+// bias gradient and the SiLU derivative.
+tc_status backward_tc(tc_mlp* m, int64_t rows, cudaStream_t st) {
+  const int R = (int)((rows + 127) / 128 * 128);   // K of the weight gradients, zero-padded rows
+  CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+  loss_grad_kernel<<<blocks_for(rows * kMlpPad), 256, 0, st>>>(rows, m->z[kMlpLayers - 1], m->tgt, m->dz,
+                                                                m->loss);
+  CUDA_TRY(cudaGetLastError());
+  for (int l = kMlpLayers - 1; l >= 0; --l) {
+    const int in = m->d.op_in[l], out = m->d.out[l];
+    TRY((transpose_bf16<float>((int)rows, R, out, m->dz, out, m->dzT, R, st)));
+    TRY((transpose_bf16<__nv_bfloat16>((int)rows, R, in, m->act[l], in, m->actT, R, st)));
+    TRY(gemm_nt(out, in, R, m->dzT, R, m->actT, R, l == 0 ? m->gw0d : m->grads + m->d.w_off[l], in, st,
+                m->splitk, m->gemm_err));
+    if (l == 0)
+      fold_w0_kernel<<<blocks_for(kMlpHidden * kMlpPad), 256, 0, st>>>(m->gw0d, m->grads + m->d.w_off[0]);
+    colsum_kernel<<<out, 256, 0, st>>>(rows, out, m->dz, m->grads + m->d.b_off[l]);
+    CUDA_TRY(cudaGetLastError());
+    if (l == 0) break;
+    to_bf16_kernel<<<blocks_for(rows * out), 256, 0, st>>>(rows * out, m->dz, m->dzb);
+    TRY(gemm_nt((int)rows, m->d.in[l], out, m->dzb, out, m->wT + m->d.w_off[l], out, m->da, m->d.in[l], st,
+                nullptr, m->gemm_err));
+    silu_back_kernel<<<blocks_for(rows * m->d.in[l]), 256, 0, st>>>(rows * m->d.in[l], m->da, m->z[l - 1], m->dz);
+    CUDA_TRY(cudaGetLastError());
+  }
+  mask_padding_kernel<<<blocks_for(256 * kMlpPad), 256, 0, st>>>(m->grads, m->d.w_off[0],
+                                                                 m->d.w_off[kMlpLayers - 1],
+                                                                 m->d.b_off[kMlpLayers - 1]);
+  CUDA_TRY(cudaGetLastError());
+  return TC_OK;
+}
+
 // Backward pass from the loss of z[4] against tgt: fills grads (weights as W^T).
 tc_status backward(tc_mlp* m, int64_t rows, cudaStream_t st) {
+  if (m->gemm == kGemmTcgen05) return backward_tc(m, rows, st);
   CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
   loss_grad_kernel<<<blocks_for(rows * kMlpPad), 256, 0, st>>>(rows, m->z[kMlpLayers - 1], m->tgt, m->dz,
                                                                 m->loss);
@@ -482,6 +604,9 @@ tc_status tc_mlp_create(uint64_t seed, tc_mlp** out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->adam_v, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->wt, n * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->wt0d, kMlpHidden * kMlpIn0 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->wT, n * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&m->gemm_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->gemm_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&m->norm, (2 * kMlpIn + 2 * kMlpOut) * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, 4 * sizeof(float));   // loss, error word, epoch sum
   uint32_t img_total = 0;
@@ -496,6 +621,8 @@ tc_status tc_mlp_create(uint64_t seed, tc_mlp** out) {
   e = cudaFuncSetAttribute(mlp_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_nt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_nt_smem_bytes(256));
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute"));
   cudaMemset(m->adam_m, 0, n * sizeof(float));
   cudaMemset(m->adam_v, 0, n * sizeof(float));
@@ -544,7 +671,8 @@ void tc_mlp_destroy(tc_mlp* m) {
   cudaDeviceSynchronize();
   for (void* p : {(void*)m->params, (void*)m->grads, (void*)m->adam_m, (void*)m->adam_v, (void*)m->wt,
                   (void*)m->norm, (void*)m->dz, (void*)m->da, (void*)m->tgt, (void*)m->idx,
-                  (void*)m->loss, (void*)m->img, (void*)m->splitk, (void*)m->gw0d, (void*)m->wt0d})
+                  (void*)m->loss, (void*)m->img, (void*)m->splitk, (void*)m->gw0d, (void*)m->wt0d,
+                  (void*)m->dzT, (void*)m->actT, (void*)m->dzb, (void*)m->wT, (void*)m->gemm_err})
     cudaFree(p);
   for (int l = 0; l < kMlpLayers; ++l) {
     cudaFree(m->act[l]);
@@ -679,10 +807,15 @@ tc_status tc_mlp_gradients(tc_mlp* m, const float* x, const float* t, int64_t n,
   }
   CUDA_TRY(cudaMemcpy(m->act[0], a0.data(), a0.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(m->tgt, tg.data(), tg.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(m->gemm_err, 0, sizeof(int)));
   TRY(forward(m, n, 0));
   TRY(backward(m, n, 0));
   CUDA_TRY(cudaMemcpy(grads, m->grads, m->d.n_params * sizeof(float), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemcpy(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost));
+  int err[2] = {0, 0};
+  CUDA_TRY(cudaMemcpy(&err[0], reinterpret_cast<int*>(m->loss) + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(&err[1], m->gemm_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (m->gemm == kGemmTcgen05 && (err[0] || err[1])) return fail(TC_ERR_TIMEOUT, "a tensor-core wait hit its limit");
   return TC_OK;
 }
 
@@ -716,6 +849,7 @@ tc_status tc_mlp_train(tc_mlp* m, const float* x_dev, const float* y_dev, int64_
     for (int64_t i = n - 1; i > 0; --i) std::swap(order[i], order[next() % (uint64_t)(i + 1)]);
     cudaError_t e = cudaMemcpyAsync(d_order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_sum, 0, sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->gemm_err, 0, sizeof(int), st);
     if (e != cudaSuccess) {
       status = cuda_fail(e, "cudaMemcpyAsync");
       break;
@@ -737,14 +871,15 @@ tc_status tc_mlp_train(tc_mlp* m, const float* x_dev, const float* y_dev, int64_
     if (status != TC_OK) break;
     float sums[2] = {0.f, 0.f};
     cudaMemcpyAsync(sums, d_sum, sizeof(float), cudaMemcpyDeviceToHost, st);
-    int err = 0;
+    int err = 0, gerr = 0;
     cudaMemcpyAsync(&err, reinterpret_cast<int*>(m->loss) + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&gerr, m->gemm_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (e2 != cudaSuccess) {
       status = cuda_fail(e2, "training epoch");
       break;
     }
-    if (m->gemm == kGemmTcgen05 && err) status = fail(TC_ERR_TIMEOUT, "tensor-core MLP wait hit its limit");
+    if (m->gemm == kGemmTcgen05 && (err || gerr)) status = fail(TC_ERR_TIMEOUT, "tensor-core MLP wait hit its limit");
     const float mean = sums[0] / (float)nb;
     if (loss_history) loss_history[ep] = mean;
     if (!std::isfinite(mean)) status = fail(TC_ERR_NAN, "training loss is not finite");
@@ -769,6 +904,31 @@ tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n,
     tp06_window_kernel<float><<<blocks_for(n), 256, 0, st>>>(n, in_dev, istim_dev, out_dev, cell, dt, nsub);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(st));
+  return TC_OK;
+}
+
+// C [M][N] (FP32) = A [M][K] . B [N][K]^T with BF16 A, B on the device (row-major, K
+// contiguous); the tensor-core GEMM of the training pass, exposed for direct checks.
+tc_status tc_gemm_bf16_nt(const void* a_dev, const void* b_dev, float* c_dev, int32_t M, int32_t N, int32_t K,
+                          void* stream) {
+  clear_error();
+  if (!a_dev || !b_dev || !c_dev || M < 1 || N < 1 || K < 8 || (K & 7)) return fail(TC_ERR_ARG, "bad GEMM arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  static int* d_err = nullptr;
+  static bool attr = false;
+  if (!d_err) CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
+  if (!attr) {
+    CUDA_TRY(cudaFuncSetAttribute(gemm_nt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)gemm_nt_smem_bytes(256)));
+    attr = true;
+  }
+  CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  TRY(gemm_nt(M, N, K, static_cast<const __nv_bfloat16*>(a_dev), K, static_cast<const __nv_bfloat16*>(b_dev), K,
+              c_dev, N, st, nullptr, d_err));
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (err) return fail(TC_ERR_TIMEOUT, "a tensor-core GEMM wait hit its limit");
   return TC_OK;
 }
 

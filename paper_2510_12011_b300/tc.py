@@ -103,6 +103,7 @@ _SIGS = {
     "tc_mlp_train": [_P, _P, _P, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, _P,
                      C.POINTER(C.c_float)],
     "tc_mlp_diagnostics": [_P, _P],
+    "tc_gemm_bf16_nt": [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P],
     "tc_tp06_window": [_P, _P, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_int32, _P, _P],
     "tc_set_surrogate": [_P, _P, C.c_int32, C.c_double, C.c_double],
     "tc_surrogate_usage": [_P, _I64, _I64],
@@ -465,6 +466,12 @@ def tp06_window(in_ptr, istim_ptr, n, dt, nsub, cell, precision=TC_FP64, out_ptr
     """Exact single-cell windows on device arrays ([19][n] in and out, istim [n] or None)."""
     _check(lib().tc_tp06_window(_P(in_ptr), None if istim_ptr is None else _P(istim_ptr), n, dt, nsub, cell,
                                 precision, _P(out_ptr), None if stream is None else _P(int(stream))))
+
+
+def gemm_bf16_nt(a_ptr, b_ptr, c_ptr, M, N, K, stream=None):
+    """c [M][N] = a [M][K] . b [N][K]^T on the tensor cores (device pointers; BF16 in, FP32 out)."""
+    _check(lib().tc_gemm_bf16_nt(_P(a_ptr), _P(b_ptr), _P(c_ptr), M, N, K,
+                                 None if stream is None else _P(int(stream))))
 
 
 def selftest_exp(x):

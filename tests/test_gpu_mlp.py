@@ -98,3 +98,22 @@ def test_short_training_reduces_loss():
     m.set_normalization(np.zeros(20), np.ones(20), np.zeros(19), 0.1 * np.ones(19))
     hist = m.train(xd.data_ptr(), yd.data_ptr(), n, epochs=6, batch=512, lr=2e-3)
     assert np.all(np.isfinite(hist)) and hist[-1] < 0.3 * hist[0], hist
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 2048), (300, 64, 256), (256, 32, 4096), (1000, 256, 32), (7, 40, 200)])
+def test_tensor_core_gemm_matches_fp32_reference(M, N, K):
+    """The training pass's tcgen05 GEMM against a plain FP32 product of the same BF16 operands
+    (several tiles, ragged M, N and K, K below one 64-wide panel, split-free)."""
+    import torch
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    a = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    b = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    ref = (a.double() @ b.double().T).float()
+    ad, bd = a.cuda(), b.cuda()
+    c = torch.full((M, N), float("nan"), device="cuda")
+    tc.gemm_bf16_nt(ad.data_ptr(), bd.data_ptr(), c.data_ptr(), M, N, K)
+    got = c.cpu()
+    assert torch.isfinite(got).all()
+    tol = 1e-5 * K ** 0.5 * (a.float().abs().max() * b.float().abs().max()).item()
+    assert (got - ref).abs().max().item() <= max(tol, 1e-4), (got - ref).abs().max().item()
+
