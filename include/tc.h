@@ -101,6 +101,14 @@ tc_status tc_mesh_matrices(const tc_mesh* mesh, const double* sigma_l, const dou
                            int32_t n_regions, int64_t* row_ptr, int32_t* col, double* m_val,
                            double* k_val);
 
+/* tc_monodomain_conductivity: per region, the monodomain conductivity of each direction from the
+ * intracellular (il, it) and extracellular (el, et) ones of the bidomain description used to set
+ * regions up (Listing 1 of the paper): sigma = sigma_i sigma_e / (sigma_i + sigma_e), the
+ * harmonic combination, for the longitudinal and the transverse direction.  Host arrays of
+ * n_regions entries (S/m); every input must be > 0 (TC_ERR_ARG otherwise).  No GPU needed. */
+tc_status tc_monodomain_conductivity(const double* il, const double* it, const double* el, const double* et,
+                                     int32_t n_regions, double* sigma_l, double* sigma_t);
+
 /* tc_mesh_layout_size: number of connected components of the mesh and the internal row count
  * of the device layout (every component padded to a multiple of 32 rows).  Host only.
  * Each connected component is an independent problem: the PCG runs per component (its own
@@ -304,13 +312,19 @@ tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n,
 /* tc_set_surrogate: attach (mlp != NULL) or detach the surrogate to a TC_FP32 TP06 simulation.
  * Every `window` steps each node's surrogate prediction is checked (finite, concentrations > 0,
  * gates in [0,1] within 0.01, |V' - V| <= dv_max over the window, |dV/dt| <= dvdt_max on the
- * step before, no stimulus during the window); nodes that pass take the predicted states at
+ * step before, no stimulus during the window, and - with dv_neighbour > 0 - no neighbour in the
+ * node's matrix row differing from it by more than dv_neighbour mV, i.e. no activation or
+ * repolarisation front next to it), and - with rest_band > 0 - V farther than rest_band mV from
+ * the model's resting potential (a resting cell stays with the exact model: its slow drift and
+ * tiny gate values are below the network's resolution); nodes that pass take the predicted
+ * states at
  * once and use the window's effective ionic current I_stim - (V' - V)/(window dt) in every step
  * of the window; all other nodes take the exact model step by step.  The network is not owned; keep it alive.  While a
  * node is held by the network its states read back as the window's end values; tc_write_state,
  * tc_set_step_index and tc_set_ionic return every node to the exact model until the next window
  * boundary, and tc_set_ionic with a model other than TP06 detaches the surrogate. */
-tc_status tc_set_surrogate(tc_sim* sim, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max);
+tc_status tc_set_surrogate(tc_sim* sim, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max,
+                           double dv_neighbour, double rest_band);
 /* tc_surrogate_sample: append training pairs drawn from the simulation's current state (TP06,
  * either precision) to device arrays x_dev [capacity][20] and y_dev [capacity][19].  For a
  * sampled node, x = (18 states, V, stimulus current averaged over the next `window` steps in

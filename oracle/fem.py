@@ -90,3 +90,10 @@ def system_matrix(M, K, chi, cm, theta, dt):
     A = (chi * cm) * M + (theta * dt) * K
     A.sort_indices()
     return A
+
+
+def monodomain_conductivity(il, it, el, et):
+    """Monodomain conductivities from intra-/extracellular ones (Listing 1 sets regions up with
+    il, it, el, et): per direction the series combination sigma_i sigma_e / (sigma_i + sigma_e)."""
+    il, it, el, et = (np.asarray(v, dtype=np.float64) for v in (il, it, el, et))
+    return 1.0 / (1.0 / il + 1.0 / el), 1.0 / (1.0 / it + 1.0 / et)

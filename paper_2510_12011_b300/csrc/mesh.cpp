@@ -414,6 +414,20 @@ tc_status tc_mesh_matrices(const tc_mesh* mesh, const double* sigma_l, const dou
   return TC_OK;
 }
 
+tc_status tc_monodomain_conductivity(const double* il, const double* it, const double* el, const double* et,
+                                     int32_t n, double* sl, double* st) {
+  clear_error();
+  if (!il || !it || !el || !et || !sl || !st || n < 1) return fail(TC_ERR_ARG, "bad conductivity arguments");
+  for (int32_t r = 0; r < n; ++r)
+    if (!(il[r] > 0 && it[r] > 0 && el[r] > 0 && et[r] > 0) || !std::isfinite(il[r] + it[r] + el[r] + et[r]))
+      return fail(TC_ERR_ARG, "conductivities must be finite and > 0 (region " + std::to_string(r) + ")");
+  for (int32_t r = 0; r < n; ++r) {
+    sl[r] = il[r] * el[r] / (il[r] + el[r]);
+    st[r] = it[r] * et[r] / (it[r] + et[r]);
+  }
+  return TC_OK;
+}
+
 tc_status tc_mesh_layout_size(const tc_mesh* mesh, int32_t* n_components, int64_t* n_internal) {
   clear_error();
   if (!mesh) return fail(TC_ERR_ARG, "mesh must not be NULL");

@@ -948,13 +948,28 @@ tc_status tc_mlp_diagnostics(const tc_mlp* m, tc_mlp_diag* out) {
 namespace tc {
 
 // Window-start features of every node: (18 states, V, window-mean stimulus) normalized, BF16.
+// With dv_nbr > 0 it also marks in `near` the nodes whose matrix-row neighbours differ from them
+// by more than dv_nbr mV: a node next to an activation or repolarisation front, whose window the
+// front may cross (the network sees one cell, not the diffusion that drives the front).
 __global__ void sur_features_kernel(int64_t n, const float* state, const float* V, const int32_t* stim_off,
                                     const int32_t* stim_ids, const StimDev* stims, const long long* k_base,
                                     int k_off, int win, double cm, const float* norm, __nv_bfloat16* a0,
-                                    float* raw) {
+                                    float* raw, float dv_nbr, const int32_t* slice_ptr, const int32_t* col,
+                                    uint8_t* near) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const long long k0 = *k_base + k_off;
+  if (dv_nbr > 0.f) {
+    const int64_t s = i >> 5;
+    const int beg = slice_ptr[s] + (int)(i & 31);
+    const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
+    const float vi = V[i];
+    float d = 0.f;
+    for (int j = 0; j < w; ++j) d = fmaxf(d, fabsf(V[col[beg + 32 * j]] - vi));
+    near[i] = d > dv_nbr ? 1 : 0;
+  } else {
+    near[i] = 0;
+  }
   float f[kMlpIn];
 #pragma unroll
   for (int j = 0; j < 18; ++j) f[j] = state[j * n + i];
@@ -978,8 +993,8 @@ __global__ void sur_features_kernel(int64_t n, const float* state, const float* 
 // Decode the prediction, check it, and commit: states <- prediction, flag, effective current.
 __global__ void sur_commit_kernel(int64_t n, const float* zout, const float* raw, const float* norm,
                                   const float* Vprev, const float* dinv, double dt, int win, float dv_max,
-                                  float dvdt_max, float* state, uint8_t* flag, float* iion,
-                                  unsigned long long* counts) {
+                                  float dvdt_max, float v_rest, float rest_band, float* state, uint8_t* flag,
+                                  float* iion, unsigned long long* counts) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (dinv[i] == 0.f) {   // padding row
@@ -1006,6 +1021,11 @@ __global__ void sur_commit_kernel(int64_t n, const float* zout, const float* raw
   // a stimulated window drives an upstroke: never the network's (none is in its training set,
   // and a wrong small prediction would cancel the stimulus through the effective current)
   ok = ok && raw[19 * n + i] == 0.f;
+  // next to a front (flag holds the neighbourhood test of the features kernel here)
+  ok = ok && flag[i] == 0;
+  // a resting cell: its tiny gate values and slow drift are below the network's resolution, and
+  // errors there would change the tissue's excitability ahead of the next wave
+  ok = ok && !(rest_band > 0.f && fabsf(V - v_rest) <= rest_band);
   flag[i] = ok ? 1 : 0;
   if (ok) {
 #pragma unroll
@@ -1028,7 +1048,8 @@ tc_status surrogate_prepare(tc_mlp* m, int64_t n) {
 
 tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
   sur_features_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.n, q.state, q.V, q.stim_off, q.stim_ids, q.stims,
-                                                       q.k_base, q.k_off, q.win, q.cm, m->norm, q.a0, q.raw);
+                                                       q.k_base, q.k_off, q.win, q.cm, m->norm, q.a0, q.raw,
+                                                       q.dv_nbr, q.slice_ptr, q.col, q.flag);
   CUDA_TRY(cudaGetLastError());
   if (q.ev_mlp[0]) CUDA_TRY(cudaEventRecord(q.ev_mlp[0], st));
   if (m->gemm == kGemmTcgen05) {
@@ -1041,7 +1062,8 @@ tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
   }
   if (q.ev_mlp[1]) CUDA_TRY(cudaEventRecord(q.ev_mlp[1], st));
   sur_commit_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.n, q.zout, q.raw, m->norm, q.Vprev, q.dinv, q.dt, q.win,
-                                                     q.dv_max, q.dvdt_max, q.state, q.flag, q.iion, q.counts);
+                                                     q.dv_max, q.dvdt_max, q.v_rest, q.rest_band, q.state, q.flag,
+                                                     q.iion, q.counts);
   CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }

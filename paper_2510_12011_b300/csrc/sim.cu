@@ -105,7 +105,7 @@ struct tc_sim {
   // learned ionic surrogate (not owned)
   tc_mlp* sur = nullptr;
   int sur_window = 10;
-  float sur_dv_max = 2.0f, sur_dvdt_max = 1.0f;
+  float sur_dv_max = 2.0f, sur_dvdt_max = 1.0f, sur_dv_nbr = 0.0f, sur_rest_band = 0.0f;
   uint8_t* sur_flag = nullptr;
   float *sur_iion = nullptr, *sur_raw = nullptr, *sur_zout = nullptr;
   __nv_bfloat16* sur_a0 = nullptr;
@@ -495,6 +495,11 @@ tc_status launch_surrogate(tc_sim* s, int iv, int k_off, size_t* ev = nullptr,
   q.dt = s->dt;
   q.dv_max = s->sur_dv_max;
   q.dvdt_max = s->sur_dvdt_max;
+  q.dv_nbr = s->sur_dv_nbr;
+  q.v_rest = (float)s->v_rest;
+  q.rest_band = s->sur_rest_band;
+  q.slice_ptr = s->slice_ptr;
+  q.col = s->col;
   q.a0 = s->sur_a0;
   q.raw = s->sur_raw;
   q.zout = s->sur_zout;
@@ -1171,7 +1176,8 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
   return TC_OK;
 }
 
-tc_status tc_set_surrogate(tc_sim* s, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max) {
+tc_status tc_set_surrogate(tc_sim* s, tc_mlp* mlp, int32_t window, double dv_max, double dvdt_max,
+                           double dv_neighbour, double rest_band) {
   clear_error();
   if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
   if (!mlp) {
@@ -1181,8 +1187,8 @@ tc_status tc_set_surrogate(tc_sim* s, tc_mlp* mlp, int32_t window, double dv_max
   }
   if (s->precision != TC_FP32 || s->model != TC_MODEL_TP06)
     return fail(TC_ERR_ARG, "the learned surrogate serves TC_FP32 simulations of TP06");
-  if (window < 1 || !(dv_max > 0) || !(dvdt_max > 0))
-    return fail(TC_ERR_ARG, "need window >= 1, dv_max > 0, dvdt_max > 0");
+  if (window < 1 || !(dv_max > 0) || !(dvdt_max > 0) || !(dv_neighbour >= 0) || !(rest_band >= 0))
+    return fail(TC_ERR_ARG, "need window >= 1, dv_max > 0, dvdt_max > 0, dv_neighbour >= 0, rest_band >= 0");
   CUDA_TRY(cudaSetDevice(s->device));
   if (!s->sur_flag) {
     const int64_t n = s->n_int;
@@ -1201,6 +1207,8 @@ tc_status tc_set_surrogate(tc_sim* s, tc_mlp* mlp, int32_t window, double dv_max
   s->sur_window = window;
   s->sur_dv_max = (float)dv_max;
   s->sur_dvdt_max = (float)dvdt_max;
+  s->sur_dv_nbr = (float)dv_neighbour;
+  s->sur_rest_band = (float)rest_band;
   drop_graphs(s);
   return TC_OK;
 }

@@ -26,6 +26,10 @@ struct SurrogateStep {
   int win;                      // steps per window
   double cm, dt;
   float dv_max, dvdt_max;       // the check: |V' - V| over the window, |dV/dt| before it
+  float dv_nbr;                 // and max |V_j - V_i| over the node's matrix row (0 = off)
+  float v_rest, rest_band;      // and |V - v_rest| > rest_band (0 = off)
+  const int32_t* slice_ptr;     // SELL-C-32 pattern of the system matrix
+  const int32_t* col;
   __nv_bfloat16* a0;            // [n][64] scratch (split-BF16 inputs)
   float* raw;                   // [20][n] scratch
   float* zout;                  // [n][32] scratch

@@ -333,6 +333,124 @@ def surrogate_test_slab(h: float = 0.25, t_end: float = 400.0) -> Workload:
                     max_iter=100)
 
 
+def prolate_shell_mesh(h: float = 0.35, endo=(35.0, 70.0), wall: float = 10.0, z_cut: float = -30.0) -> Mesh:
+    """Truncated prolate-ellipsoid shell (an idealised left ventricle), apex down.
+
+    The endocardium is the ellipsoid x^2/a0^2 + y^2/a0^2 + z^2/c0^2 = 1 (a0, c0 = endo), the
+    epicardium the one with semi-axes a0 + wall, c0 + wall; the shell is cut by the plane z = z_cut.
+    Lattice cells of spacing h (origin at (-a1, -a1, -c1)) whose centres lie in the shell are kept
+    and split into six tetrahedra like the slabs (a voxel mesh: the surfaces are staircases).
+    Every element's transmural depth s in [0, 1] solves x^2/(a0 + s w)^2 + y^2/(a0 + s w)^2 +
+    z^2/(c0 + s w)^2 = 1 at its cell centre (bisection); the fibre turns from -60 deg at the
+    endocardium to +60 deg at the epicardium, f = cos(a) e_c + sin(a) e_l, with e_c the
+    circumferential direction and e_l = n x e_c (n the normal of the ellipsoid through the centre).
+    Region 0 throughout; `lattice` holds the integer cell coordinates of every node."""
+    a0, c0 = endo
+    a1, c1 = a0 + wall, c0 + wall
+    nx = int(np.ceil(2 * a1 / h))
+    nz = int(np.ceil((z_cut + c1) / h))
+    cells = []
+    for k in range(nz):
+        zc = -c1 + (k + 0.5) * h
+        j, i = np.meshgrid(np.arange(nx), np.arange(nx), indexing="ij")
+        xc = -a1 + (i + 0.5) * h
+        yc = -a1 + (j + 0.5) * h
+        r2 = xc * xc + yc * yc
+        inside = (r2 / a1 ** 2 + zc * zc / c1 ** 2 <= 1.0) & (r2 / a0 ** 2 + zc * zc / c0 ** 2 >= 1.0) & (zc <= z_cut)
+        ii, jj = i[inside], j[inside]
+        cells.append(np.stack([ii, jj, np.full(ii.size, k)], axis=1))
+    cells = np.concatenate(cells).astype(np.int64)
+    stride = np.array([1, nx + 1, (nx + 1) * (nx + 1)], dtype=np.int64)
+    corner_ids = np.empty((cells.shape[0], 6, 4), dtype=np.int64)
+    for t, corners in enumerate(KUHN_CORNERS):
+        for v, d in enumerate(corners):
+            corner_ids[:, t, v] = (cells + np.array(d)) @ stride
+    used, tets = np.unique(corner_ids.reshape(-1), return_inverse=True)
+    tets = tets.reshape(-1, 4).astype(np.int32)
+    lat = np.stack([used % (nx + 1), (used // (nx + 1)) % (nx + 1), used // ((nx + 1) * (nx + 1))], axis=1)
+    xyz = np.stack([-a1 + lat[:, 0] * h, -a1 + lat[:, 1] * h, -c1 + lat[:, 2] * h], axis=1)
+    # transmural depth and fibre per cell (shared by its six tetrahedra)
+    cc = np.stack([-a1 + (cells[:, 0] + 0.5) * h, -a1 + (cells[:, 1] + 0.5) * h, -c1 + (cells[:, 2] + 0.5) * h], axis=1)
+    rr = cc[:, 0] ** 2 + cc[:, 1] ** 2
+    lo, hi = np.zeros(len(cc)), np.ones(len(cc))
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        f = rr / (a0 + wall * mid) ** 2 + cc[:, 2] ** 2 / (c0 + wall * mid) ** 2 - 1.0
+        lo = np.where(f > 0.0, mid, lo)
+        hi = np.where(f > 0.0, hi, mid)
+    depth = 0.5 * (lo + hi)
+    a_s, c_s = a0 + wall * depth, c0 + wall * depth
+    nrm = np.stack([cc[:, 0] / a_s ** 2, cc[:, 1] / a_s ** 2, cc[:, 2] / c_s ** 2], axis=1)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    r = np.sqrt(rr)
+    ec = np.where(r[:, None] > 1e-9, np.stack([-cc[:, 1], cc[:, 0], np.zeros_like(r)], axis=1) / np.maximum(r, 1e-9)[:, None],
+                  np.array([1.0, 0.0, 0.0]))
+    el = np.cross(nrm, ec)
+    el /= np.linalg.norm(el, axis=1, keepdims=True)
+    ang = np.deg2rad(-60.0 + 120.0 * depth)
+    fib_cell = np.cos(ang)[:, None] * ec + np.sin(ang)[:, None] * el
+    fib = np.repeat(fib_cell, 6, axis=0)
+    region = np.zeros(tets.shape[0], dtype=np.int32)
+    m = Mesh(xyz=xyz, tets=tets, fibres=fib, region=region, lattice=lat.astype(np.int32), shape=(nx + 1, nx + 1, nz + 1),
+             h=h)
+    m.depth = np.repeat(depth, 6)
+    return m
+
+
+def endocardial_sites(m: Mesh, count: int, seed: int, endo=(35.0, 70.0), radius: float = 1.5,
+                      z_max: float = -45.0) -> list:
+    """`count` node sets (balls of `radius` mm) around seeded nodes of the endocardial surface
+    (nodes on or inside the endocardium's outer layer, x^2/a0^2 + y^2/a0^2 + z^2/c0^2 <= (1 +
+    h/a0)^2) in the apical region z <= z_max on the septal side x <= 0."""
+    a0, c0 = endo
+    x = m.xyz
+    f = (x[:, 0] ** 2 + x[:, 1] ** 2) / a0 ** 2 + x[:, 2] ** 2 / c0 ** 2
+    cand = np.nonzero((f <= (1.0 + m.h / a0) ** 2) & (x[:, 2] <= z_max) & (x[:, 0] <= 0.0))[0]
+    u = uniform01(seed, np.arange(count, dtype=np.uint64))
+    sites = cand[(u * cand.size).astype(np.int64) % cand.size]
+    out = []
+    for sidx in sites:
+        d = np.linalg.norm(x - x[sidx], axis=1)
+        out.append(np.nonzero(d <= radius + 1e-9)[0].astype(np.int32))
+    return out
+
+
+def ellipsoid_tp06(h: float = 0.35, t_end: float = 300.0, seed: int = 5) -> Workload:
+    """The truncated prolate-ellipsoid shell (endocardium 35/35/70 mm, 10 mm wall, cut at
+    z = -30 mm, 31 % of the height from the apex: about 2.0 M nodes at h = 0.35 mm) with the
+    rule-based fibres, TP06 epicardial cells, the small slab's tissue constants, dt = 0.02 ms,
+    and five seeded apical/septal endocardial stimulus sites (1.5 mm balls, 2 ms at 1.0 uA/mm^2,
+    all at t = 0)."""
+    m = prolate_shell_mesh(h)
+    st = [Stimulus(nodes, 0.0, 2.0, 1.0) for nodes in endocardial_sites(m, 5, seed)]
+    return Workload(f"ellipsoid_h{h:g}_tp06", m, 0.17, 0.019, 140.0, 0.01, 0.5, 0.02, t_end, "tp06",
+                    stimuli=st, atol=1e-5, rtol=1e-5, max_iter=100)
+
+
+def nversion_slab(h: float, t_end: float = 100.0, cell: int = 2) -> Workload:
+    """The N-version benchmark slab (Section 3.1.2, Table 3): 20x7x3 mm, fibres along x, spacing
+    h (0.5, 0.2 or 0.1 mm), dt = 0.005 ms, chi = 140 /mm, Cm = 0.01 uF/mm^2, sigma_l =
+    0.1334177, sigma_t = 0.0173515 S/m, ten Tusscher-Panfilov (cell type `cell`).  The 50 uA/mm^3
+    volumetric stimulus enters as 50/chi uA/mm^2 of membrane current; it is applied for 2 ms to
+    the nodes of the 1.5 mm corner cube at P1 = (0, 0, 0) (the table gives neither the corner
+    region's size nor the duration)."""
+    m = slab_mesh(20.0, 7.0, 3.0, h, fibre="x")
+    st = [Stimulus(corner_nodes(m, 1.5), 0.0, 2.0, 50.0 / 140.0)]
+    w = Workload(f"nversion_h{h:g}", m, 0.1334177, 0.0173515, 140.0, 0.01, 0.5, 0.005, t_end, "tp06",
+                 stimuli=st, atol=0.0, rtol=1e-8, max_iter=1000)
+    w.tp06_cell = cell
+    return w
+
+
+def diagonal_nodes(m: Mesh, count: int = 11) -> np.ndarray:
+    """Nodes nearest to `count` equally spaced points on the diagonal from P1 = (0, 0, 0) to the
+    opposite corner P8 (both corners are nodes)."""
+    hi = m.xyz.max(axis=0)
+    t = np.linspace(0.0, 1.0, count)
+    pts = t[:, None] * hi[None, :]
+    return np.array([int(np.argmin(np.linalg.norm(m.xyz - p, axis=1))) for p in pts], dtype=np.int64)
+
+
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """Seeded uniform vector for operator tests."""
     return lo + (hi - lo) * uniform01(seed, np.arange(n, dtype=np.uint64))

@@ -58,7 +58,8 @@ def train(x, y, count, epochs=20, batch=2048, lr=1e-3, lr_end=1e-5, v_weight=9.0
     return m, np.array(hist)
 
 
-def run(w, precision, mlp=None, window=10, dv_max=2.0, dvdt_max=1.0, graphs=True):
+def run(w, precision, mlp=None, window=10, dv_max=2.0, dvdt_max=1.0, dv_neighbour=0.3, rest_band=0.5,
+        graphs=True):
     """One full run of workload w; returns activation times, APD90, wall time and (with a
     network) the surrogate's usage counts."""
     import torch
@@ -66,7 +67,7 @@ def run(w, precision, mlp=None, window=10, dv_max=2.0, dvdt_max=1.0, graphs=True
     try:
         sim.set_graphs(graphs)
         if mlp is not None:
-            sim.set_surrogate(mlp, window, dv_max, dvdt_max)
+            sim.set_surrogate(mlp, window, dv_max, dvdt_max, dv_neighbour, rest_band)
         sim.step(min(50, w.n_steps))    # warm-up (graph capture, tensor-map set-up)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

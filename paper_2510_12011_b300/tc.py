@@ -68,6 +68,7 @@ _SIGS = {
     "tc_autotune": [_P, C.c_int32, _I32, _I32, _D],
     "tc_set_graphs": [_P, C.c_int32],
     "tc_mesh_layout_size": [_P, _I32, _I64],
+    "tc_monodomain_conductivity": [_D, _D, _D, _D, C.c_int32, _D, _D],
     "tc_set_ionic": [_P, C.c_int32, _D, C.c_int32, _D],
     "tc_add_stimulus": [_P, _I32, C.c_int64, C.c_double, C.c_double, C.c_double],
     "tc_set_solver": [_P, C.c_double, C.c_double, C.c_int32],
@@ -105,7 +106,7 @@ _SIGS = {
     "tc_mlp_diagnostics": [_P, _P],
     "tc_gemm_bf16_nt": [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P],
     "tc_tp06_window": [_P, _P, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_int32, _P, _P],
-    "tc_set_surrogate": [_P, _P, C.c_int32, C.c_double, C.c_double],
+    "tc_set_surrogate": [_P, _P, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double],
     "tc_surrogate_usage": [_P, _I64, _I64],
     "tc_surrogate_sample": [_P, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64, _P, _P,
                             C.c_int64, _I64],
@@ -338,9 +339,10 @@ class Simulation:
     def set_graphs(self, on=True):
         _check(lib().tc_set_graphs(self._h, int(bool(on))))
 
-    def set_surrogate(self, mlp, window=10, dv_max=2.0, dvdt_max=1.0):
+    def set_surrogate(self, mlp, window=10, dv_max=2.0, dvdt_max=1.0, dv_neighbour=0.3, rest_band=0.5):
         """Attach a trained Mlp (or None to detach) as the learned ionic surrogate."""
-        _check(lib().tc_set_surrogate(self._h, None if mlp is None else mlp._h, window, dv_max, dvdt_max))
+        _check(lib().tc_set_surrogate(self._h, None if mlp is None else mlp._h, window, dv_max, dvdt_max,
+                                      dv_neighbour, rest_band))
         self._mlp = mlp
 
     def surrogate_sample(self, x_dev, y_dev, capacity, count, window=10, rest_band=1.0, rest_keep=0.05,
@@ -472,6 +474,14 @@ def gemm_bf16_nt(a_ptr, b_ptr, c_ptr, M, N, K, stream=None):
     """c [M][N] = a [M][K] . b [N][K]^T on the tensor cores (device pointers; BF16 in, FP32 out)."""
     _check(lib().tc_gemm_bf16_nt(_P(a_ptr), _P(b_ptr), _P(c_ptr), M, N, K,
                                  None if stream is None else _P(int(stream))))
+
+
+def monodomain_conductivity(il, it, el, et):
+    """Per-region monodomain (sigma_l, sigma_t) from intra-/extracellular conductivities (S/m)."""
+    il, it, el, et = (_f64(v) for v in (il, it, el, et))
+    sl, st = np.empty_like(il), np.empty_like(il)
+    _check(lib().tc_monodomain_conductivity(_d(il), _d(it), _d(el), _d(et), il.size, _d(sl), _d(st)))
+    return sl, st
 
 
 def selftest_exp(x):

@@ -155,3 +155,25 @@ def test_component_layout_of_a_joined_mesh():
         assert np.all(comp[perm[k:k + sizes[c]]] == c)
         k += sizes[c]
     assert seen == {0, 1, 2}
+
+
+def test_monodomain_conductivity_from_bidomain_pairs():
+    """Listing 1 configures regions with intra-/extracellular conductivities; the monodomain
+    value per direction is their series combination.  Pins: equal intra and extra values halve,
+    an extracellular value much larger than the intracellular one leaves the intracellular one,
+    and the ABI agrees with the oracle; non-positive input is rejected."""
+    import numpy as np
+    import pytest
+    from oracle import fem
+    from paper_2510_12011_b300 import tc
+    sl, st = tc.monodomain_conductivity([0.2, 0.3], [0.02, 0.05], [0.2, 0.3], [0.02, 0.05])
+    assert np.allclose(sl, [0.1, 0.15], rtol=0, atol=1e-15) and np.allclose(st, [0.01, 0.025], rtol=0, atol=1e-15)
+    sl, st = tc.monodomain_conductivity([0.17], [0.019], [1e12], [1e12])
+    assert abs(sl[0] - 0.17) < 1e-12 and abs(st[0] - 0.019) < 1e-12
+    rng = np.random.default_rng(4)
+    v = rng.uniform(0.01, 1.0, (4, 9))
+    got = tc.monodomain_conductivity(*v)
+    ref = fem.monodomain_conductivity(*v)
+    assert np.allclose(got[0], ref[0], rtol=1e-15) and np.allclose(got[1], ref[1], rtol=1e-15)
+    with pytest.raises(tc.TcError):
+        tc.monodomain_conductivity([0.1], [0.0], [0.1], [0.1])

@@ -220,3 +220,18 @@ def test_large_slab_full_size_parity():
     g.step(3)
     assert np.abs(g.read() - o.V).max() <= V_TOL
     assert np.abs(g.read(tc.TC_FIELD_STATE) - o.state[0]).max() <= 1e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_nversion_activation_converges_with_refinement():
+    """N-version slab (Section 3.1.2, Table 3) at the table's spacings 0.5, 0.2 and 0.1 mm, FP64:
+    every node activates, activation time grows along the P1-P8 diagonal, and the change from
+    0.2 to 0.1 mm is smaller than the change from 0.5 to 0.2 mm (self-convergence)."""
+    from paper_2510_12011_b300 import nversion
+    res = nversion.study((0.5, 0.2, 0.1), t_end=100.0)
+    for r in res:
+        assert r["all_activated"]
+        act = np.asarray(r["act_ms"])
+        assert np.all(np.diff(act) > 0)
+    assert res[2]["diff_to_coarser_ms_max"] < res[1]["diff_to_coarser_ms_max"]

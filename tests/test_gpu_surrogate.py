@@ -126,7 +126,7 @@ def test_surrogate_in_captured_graphs_matches_direct_launches():
     for graphs in (True, False):
         sim = tc.from_workload(w, precision=tc.TC_FP32)
         sim.set_graphs(graphs)
-        sim.set_surrogate(m, window=10, dv_max=2.0, dvdt_max=1.0)
+        sim.set_surrogate(m, window=10, dv_max=2.0, dvdt_max=1.0, dv_neighbour=0.0, rest_band=0.0)
         gsteps = 0
         for n in (7, 95, 64, 300, 34):
             gsteps += sim.step(n)["graph_steps"]
