@@ -227,67 +227,17 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 
 // Row products over one SELL slice, lane = row.  Four entries are fetched (indices, values,
 // gathered vector entries) before their FMAs; even and odd entries feed two FMA chains.
-// L2 eviction priorities for read-only streams (createpolicy + ld.global.nc.L2::cache_hint).
-// The system matrix and the column indices are re-read by every CG iteration of a step; marked
-// evict-last they stay in the 126 MB L2 across iterations, while the mass and stiffness values
-// (read once per step) are marked evict-first so that they do not push them out.
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ double ld_hint(const double* q, uint64_t pol) {
-  double v;
-  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(q), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ float ld_hint(const float* q, uint64_t pol) {
-  float v;
-  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(q), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ int ld_hint(const int32_t* q, uint64_t pol) {
-  int v;
-  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(q), "l"(pol));
-  return v;
-}
-
-// One row of a SELL-C-32 product: lane's row, entries j = 0..w-1 at beg + 32 j.  Even entries
-// accumulate in acc0, odd ones in acc1, each in entry order (the result does not depend on the
-// unrolling); eight entries' indices and values are in flight before their x gathers.
 template <typename T>
 __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
-                                     int beg, int w, const T* x, uint64_t pol) {
+                                     int beg, int w, const T* x) {
   T acc0 = T(0), acc1 = T(0);
   int j = 0;
-  for (; j + 8 <= w; j += 8) {
-    const int e = beg + 32 * j;
-    int c[8];
-    T v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] = ld_hint(col + e + 32 * u, pol);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = ld_hint(val + e + 32 * u, pol);
-    T xv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) xv[u] = x[c[u]];
-#pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      acc0 = fmaT(v[u], xv[u], acc0);
-      acc1 = fmaT(v[u + 1], xv[u + 1], acc1);
-    }
-  }
   for (; j + 4 <= w; j += 4) {
     const int e = beg + 32 * j;
-    const int c0 = ld_hint(col + e, pol), c1 = ld_hint(col + e + 32, pol), c2 = ld_hint(col + e + 64, pol),
-              c3 = ld_hint(col + e + 96, pol);
-    const T v0 = ld_hint(val + e, pol), v1 = ld_hint(val + e + 32, pol), v2 = ld_hint(val + e + 64, pol),
-            v3 = ld_hint(val + e + 96, pol);
+    const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32), c2 = __ldg(col + e + 64),
+              c3 = __ldg(col + e + 96);
+    const T v0 = __ldg(val + e), v1 = __ldg(val + e + 32), v2 = __ldg(val + e + 64),
+            v3 = __ldg(val + e + 96);
     const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
     acc0 = fmaT(v0, x0, acc0);
     acc1 = fmaT(v1, x1, acc1);
@@ -296,19 +246,13 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
   }
   for (; j < w; ++j) {
     const int e = beg + 32 * j;
-    const T v = ld_hint(val + e, pol), xv = x[ld_hint(col + e, pol)];
+    const T v = __ldg(val + e), xv = x[__ldg(col + e)];
     if (j & 1)
       acc1 = fmaT(v, xv, acc1);
     else
       acc0 = fmaT(v, xv, acc0);
   }
   return acc0 + acc1;
-}
-
-template <typename T>
-__device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
-                                     int beg, int w, const T* x) {
-  return sell_dot(col, val, beg, w, x, l2_evict_last());
 }
 
 // Two value streams over the same pattern: am = sum M_ij g1_j, ak = sum K_ij g2_j.
@@ -319,13 +263,12 @@ __device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const
                                           T& am, T& ak) {
   am = T(0);
   ak = T(0);
-  const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
   int j = 0;
   for (; j + 2 <= w; j += 2) {
     const int e = beg + 32 * j;
-    const int c0 = ld_hint(col + e, keep), c1 = ld_hint(col + e + 32, keep);
-    const T m0 = ld_hint(vm + e, stream), m1 = ld_hint(vm + e + 32, stream);
-    const T k0 = ld_hint(vk + e, stream), k1 = ld_hint(vk + e + 32, stream);
+    const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32);
+    const T m0 = __ldg(vm + e), m1 = __ldg(vm + e + 32);
+    const T k0 = __ldg(vk + e), k1 = __ldg(vk + e + 32);
     const T a0 = __ldg(g1 + c0), a1 = __ldg(g1 + c1);
     const T b0 = __ldg(g2 + c0), b1 = __ldg(g2 + c1);
     am = fmaT(m0, a0, am);
@@ -335,9 +278,9 @@ __device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const
   }
   for (; j < w; ++j) {
     const int e = beg + 32 * j;
-    const int c = ld_hint(col + e, keep);
-    am = fmaT(ld_hint(vm + e, stream), __ldg(g1 + c), am);
-    ak = fmaT(ld_hint(vk + e, stream), __ldg(g2 + c), ak);
+    const int c = __ldg(col + e);
+    am = fmaT(__ldg(vm + e), __ldg(g1 + c), am);
+    ak = fmaT(__ldg(vk + e), __ldg(g2 + c), ak);
   }
 }
 
