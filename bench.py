@@ -271,7 +271,8 @@ def surrogate_form(w, K, W, ms64, act64, stream, torch, apd=True, apd64=None):
     both = (act >= 0) & (act64 >= 0)
     n = w.mesh.n_nodes
     mlp_ms = prof["mlp_ms"] / max(prof["surrogate_windows"], 1)
-    flops = MLP_FLOP_PER_ROW * n
+    rows_per_launch = prof["surrogate_rows"] / max(prof["surrogate_windows"], 1)
+    flops = MLP_FLOP_PER_ROW * rows_per_launch
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops_sustained", 1407.5) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1400.0
     apd90 = None
@@ -302,7 +303,7 @@ def surrogate_form(w, K, W, ms64, act64, stream, torch, apd=True, apd64=None):
             "roofline_mlp": {"kernel": "mlp_fused_kernel", "bound": "tensor",
                              "achieved": flops / (mlp_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                              "frac": flops / (mlp_ms * 1e-3) / 1e12 / peak,
-                             "flop_per_launch": flops, "avg_launch_ms": mlp_ms,
+                             "flop_per_launch": flops, "rows_per_launch": rows_per_launch, "avg_launch_ms": mlp_ms,
                              "peak_source": "measured bf16_tflops_sustained (kernel timed inside the step loop)"},
             "apd90": apd90, "apd90_this_run": apd_run}
 

@@ -72,6 +72,7 @@ typedef struct {
   double surrogate_ms;    int64_t surrogate_windows;   /* learned-surrogate inference (features,
                                                           network, check), one per window     */
   double mlp_ms;          /* of which the network's fused tensor-core forward pass          */
+  int64_t surrogate_rows; /* node rows the network evaluated (the candidates of each window) */
 } tc_profile;
 
 /* ---- mesh ------------------------------------------------------------------------- */

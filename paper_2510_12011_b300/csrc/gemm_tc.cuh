@@ -40,7 +40,8 @@ constexpr uint32_t kTcSmemBytes = kTcSmemA + kTcSmemW + 1024 + kTcBias * 4;
 constexpr long long kTcWaitLimit = 1ll << 24;
 
 struct MlpFusedArgs {
-  int64_t M;
+  int64_t M;                               // rows (an upper bound when M_dev is set)
+  const int* M_dev;                        // optional device row count (read by every CTA)
   const __nv_bfloat16* a0;                 // [M][64] split-BF16 inputs (normalized; hi | lo)
   const uint8_t* img[kMlpLayers];          // swizzled weight images
   uint32_t img_bytes[kMlpLayers];
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
   __shared__ uint64_t bar_w, bar_mma;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t ntiles = (a.M + kTcRows - 1) / kTcRows;
+  const int64_t M = a.M_dev ? (a.M < (int64_t)*a.M_dev ? a.M : (int64_t)*a.M_dev) : a.M;
+  const int64_t ntiles = (M + kTcRows - 1) / kTcRows;
   if (tid == 0) {
     mbar_init(&bar_w, 1);
     mbar_init(&bar_mma, 1);
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
       const int r = e >> 3, c = e & 7;
       const int64_t gr = row0 + r;
       uint4 v = make_uint4(0, 0, 0, 0);
-      if (gr < a.M) v = *reinterpret_cast<const uint4*>(a.a0 + gr * kMlpIn0 + c * 8);
+      if (gr < M) v = *reinterpret_cast<const uint4*>(a.a0 + gr * kMlpIn0 + c * 8);
       *reinterpret_cast<uint4*>(sA + sw128_offset(0, kTcRows, r, c)) = v;
     }
     fence_proxy_async_smem();
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
       const int cols = N / 4 >= 32 ? N / 4 : 32;
       const int cbeg = cg * cols;
       const int64_t grow = row0 + row;
-      const bool valid = grow < a.M;
+      const bool valid = grow < M;
       if (cbeg < N) {
         const int nch = cols / 32;   // 1 or 2 chunks of 32 columns (uniform in the warp)
         uint32_t raw[2][32];

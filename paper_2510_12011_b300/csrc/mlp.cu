@@ -432,9 +432,10 @@ tc_status rebuild_images(tc_mlp* m, cudaStream_t st) {
 // Tensor-core forward of act0 (M x 32 BF16) through all layers; y (M x 32 FP32) gets the
 // output, and with store_hidden Z_l and the activations go to the training workspace.
 tc_status forward_tc(tc_mlp* m, int64_t M, const __nv_bfloat16* act0, float* y, bool store_hidden,
-                     int* err, cudaStream_t st) {
+                     int* err, cudaStream_t st, const int* M_dev = nullptr) {
   MlpFusedArgs a{};
   a.M = M;
+  a.M_dev = M_dev;
   a.a0 = act0;
   for (int l = 0; l < kMlpLayers; ++l) {
     a.img[l] = m->img + m->img_off[l];
@@ -947,36 +948,61 @@ tc_status tc_mlp_diagnostics(const tc_mlp* m, tc_mlp_diag* out) {
 
 namespace tc {
 
-// Window-start features of every node: (18 states, V, window-mean stimulus) normalized, BF16.
-// With dv_nbr > 0 it also marks in `near` the nodes whose matrix-row neighbours differ from them
-// by more than dv_nbr mV: a node next to an activation or repolarisation front, whose window the
-// front may cross (the network sees one cell, not the diffusion that drives the front).
-__global__ void sur_features_kernel(int64_t n, const float* state, const float* V, const int32_t* stim_off,
-                                    const int32_t* stim_ids, const StimDev* stims, const long long* k_base,
-                                    int k_off, int win, double cm, const float* norm, __nv_bfloat16* a0,
-                                    float* raw, float dv_nbr, const int32_t* slice_ptr, const int32_t* col,
-                                    uint8_t* near) {
+// Window start, every node: the checks that need no prediction decide whether the node is a
+// candidate for the network this window - a real row, no stimulus during the window, |dV/dt| on
+// the step before within dvdt_max, V outside the resting band (a resting cell's tiny gate values
+// and slow drift are below the network's resolution, and errors there would change the tissue's
+// excitability ahead of the next wave), and, with dv_nbr > 0, no matrix-row neighbour differing
+// from it by more than dv_nbr mV (a front next to it could cross the window; the network sees one
+// cell, not the diffusion that drives the front).  Candidates get a compacted input row (18
+// states, V, window-mean stimulus; normalized, split BF16) at a position taken from *count, and
+// idx[pos] = node; everyone else stays with the exact model (flag 0) and is counted as such.
+__global__ void sur_features_kernel(int64_t n, const float* state, const float* V, const float* Vprev,
+                                    const float* dinv, const int32_t* stim_off, const int32_t* stim_ids,
+                                    const StimDev* stims, const long long* k_base, int k_off, int win, double cm,
+                                    double dt, float dvdt_max, float v_rest, float rest_band, float dv_nbr,
+                                    const int32_t* slice_ptr, const int32_t* col, const float* norm,
+                                    __nv_bfloat16* a0, float* raw, int32_t* idx, int* count, uint8_t* flag,
+                                    unsigned long long* counts) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const long long k0 = *k_base + k_off;
-  if (dv_nbr > 0.f) {
+  const bool real = i < n && dinv[i] != 0.f;
+  bool cand = real;
+  float vi = 0.f, is = 0.f;
+  if (cand) {
+    vi = V[i];
+    const long long k0 = *k_base + k_off;
+    double acc = 0.0;
+    for (int s = 0; s < win; ++s) acc += stimulus_at(stim_off, stim_ids, stims, i, k0 + s);
+    is = (float)(acc / win / cm);   // uA/mm^2 -> pA/pF
+    cand = is == 0.f && fabsf(vi - Vprev[i]) <= dvdt_max * (float)dt &&
+           !(rest_band > 0.f && fabsf(vi - v_rest) <= rest_band);
+  }
+  if (cand && dv_nbr > 0.f) {
     const int64_t s = i >> 5;
     const int beg = slice_ptr[s] + (int)(i & 31);
     const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
-    const float vi = V[i];
     float d = 0.f;
     for (int j = 0; j < w; ++j) d = fmaxf(d, fabsf(V[col[beg + 32 * j]] - vi));
-    near[i] = d > dv_nbr ? 1 : 0;
-  } else {
-    near[i] = 0;
+    cand = d <= dv_nbr;
   }
+  if (i < n) flag[i] = 0;
+  const unsigned cm_ = __ballot_sync(0xffffffffu, cand);
+  const unsigned rm = __ballot_sync(0xffffffffu, real && !cand);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0) {
+    if (cm_) base = atomicAdd(count, __popc(cm_));
+    if (rm) atomicAdd(&counts[1], (unsigned long long)__popc(rm));
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (!cand) return;
+  const int pos = base + __popc(cm_ & ((1u << lane) - 1u));
+  idx[pos] = (int32_t)i;
   float f[kMlpIn];
 #pragma unroll
   for (int j = 0; j < 18; ++j) f[j] = state[j * n + i];
-  f[18] = V[i];
-  double is = 0.0;
-  for (int s = 0; s < win; ++s) is += stimulus_at(stim_off, stim_ids, stims, i, k0 + s);
-  f[19] = (float)(is / win / cm);   // uA/mm^2 -> pA/pF
+  f[18] = vi;
+  f[19] = is;
   float xn[kMlpIn];
 #pragma unroll
   for (int j = 0; j < kMlpIn; ++j) {
@@ -987,57 +1013,48 @@ __global__ void sur_features_kernel(int64_t n, const float* state, const float* 
   mlp_split_input(xn, h);
 #pragma unroll
   for (int u = 0; u < kMlpIn0 / 8; ++u)
-    reinterpret_cast<uint4*>(a0 + i * kMlpIn0)[u] = reinterpret_cast<const uint4*>(h)[u];
+    reinterpret_cast<uint4*>(a0 + (int64_t)pos * kMlpIn0)[u] = reinterpret_cast<const uint4*>(h)[u];
 }
 
-// Decode the prediction, check it, and commit: states <- prediction, flag, effective current.
-__global__ void sur_commit_kernel(int64_t n, const float* zout, const float* raw, const float* norm,
-                                  const float* Vprev, const float* dinv, double dt, int win, float dv_max,
-                                  float dvdt_max, float v_rest, float rest_band, float* state, uint8_t* flag,
-                                  float* iion, unsigned long long* counts) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (dinv[i] == 0.f) {   // padding row
-    flag[i] = 0;
-    return;
+// Candidates: decode the prediction (row pos, node idx[pos]), check it (finite, concentrations
+// positive, gates inside [0, 1] up to a small margin, |V' - V| <= dv_max) and commit: states <-
+// prediction, flag, the window's effective current.
+__global__ void sur_commit_kernel(const int* count, int64_t n, const int32_t* idx, const float* zout,
+                                  const float* raw, const float* norm, double dt, int win, float dv_max,
+                                  float* state, uint8_t* flag, float* iion, unsigned long long* counts) {
+  const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool have = pos < *count;
+  bool ok = false;
+  if (have) {
+    const int64_t i = idx[pos];
+    const float* out_mean = norm + 2 * kMlpIn;
+    const float* out_scale = norm + 2 * kMlpIn + kMlpOut;
+    float y[kMlpOut];
+    ok = true;
+#pragma unroll
+    for (int j = 0; j < kMlpOut; ++j) {
+      y[j] = raw[j * n + i] + out_mean[j] + out_scale[j] * zout[pos * kMlpPad + j];
+      ok = ok && isfinite(y[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) ok = ok && y[j] > 0.f;
+#pragma unroll
+    for (int j = 5; j < 18; ++j) ok = ok && y[j] > -0.01f && y[j] < 1.01f;
+    const float dv = y[18] - raw[18 * n + i];
+    ok = ok && fabsf(dv) <= dv_max;
+    flag[i] = ok ? 1 : 0;
+    if (ok) {
+#pragma unroll
+      for (int j = 0; j < 18; ++j) state[j * n + i] = j >= 5 ? fminf(fmaxf(y[j], 0.f), 1.f) : y[j];
+      // single cell: dV/dt = -I_ion + I_stim over the window (no stimulus here)
+      iion[i] = raw[19 * n + i] - dv / (float)(win * dt);
+    }
   }
-  const float* out_mean = norm + 2 * kMlpIn;
-  const float* out_scale = norm + 2 * kMlpIn + kMlpOut;
-  float y[kMlpOut];
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < kMlpOut; ++j) {
-    y[j] = raw[j * n + i] + out_mean[j] + out_scale[j] * zout[i * kMlpPad + j];
-    ok = ok && isfinite(y[j]);
-  }
-  // concentrations positive, gates inside [0, 1] up to a small margin
-#pragma unroll
-  for (int j = 0; j < 5; ++j) ok = ok && y[j] > 0.f;
-#pragma unroll
-  for (int j = 5; j < 18; ++j) ok = ok && y[j] > -0.01f && y[j] < 1.01f;
-  const float V = raw[18 * n + i];
-  const float dv = y[18] - V;
-  ok = ok && fabsf(dv) <= dv_max && fabsf(V - Vprev[i]) <= dvdt_max * (float)dt;
-  // a stimulated window drives an upstroke: never the network's (none is in its training set,
-  // and a wrong small prediction would cancel the stimulus through the effective current)
-  ok = ok && raw[19 * n + i] == 0.f;
-  // next to a front (flag holds the neighbourhood test of the features kernel here)
-  ok = ok && flag[i] == 0;
-  // a resting cell: its tiny gate values and slow drift are below the network's resolution, and
-  // errors there would change the tissue's excitability ahead of the next wave
-  ok = ok && !(rest_band > 0.f && fabsf(V - v_rest) <= rest_band);
-  flag[i] = ok ? 1 : 0;
-  if (ok) {
-#pragma unroll
-    for (int j = 0; j < 18; ++j) state[j * n + i] = j >= 5 ? fminf(fmaxf(y[j], 0.f), 1.f) : y[j];
-    // single cell: dV/dt = -I_ion + I_stim over the window
-    iion[i] = raw[19 * n + i] - dv / (float)(win * dt);
-  }
-  const unsigned act = __activemask();
-  const unsigned okm = __ballot_sync(act, ok);
-  if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+  const unsigned okm = __ballot_sync(0xffffffffu, ok);
+  const unsigned hm = __ballot_sync(0xffffffffu, have);
+  if ((threadIdx.x & 31) == 0 && hm) {
     atomicAdd(&counts[0], (unsigned long long)__popc(okm));
-    atomicAdd(&counts[1], (unsigned long long)(__popc(act) - __popc(okm)));
+    atomicAdd(&counts[1], (unsigned long long)(__popc(hm) - __popc(okm)));
   }
 }
 
@@ -1047,13 +1064,15 @@ tc_status surrogate_prepare(tc_mlp* m, int64_t n) {
 }
 
 tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
-  sur_features_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.n, q.state, q.V, q.stim_off, q.stim_ids, q.stims,
-                                                       q.k_base, q.k_off, q.win, q.cm, m->norm, q.a0, q.raw,
-                                                       q.dv_nbr, q.slice_ptr, q.col, q.flag);
+  CUDA_TRY(cudaMemsetAsync(q.count, 0, sizeof(int), st));
+  sur_features_kernel<<<blocks_for(q.n), 256, 0, st>>>(
+      q.n, q.state, q.V, q.Vprev, q.dinv, q.stim_off, q.stim_ids, q.stims, q.k_base, q.k_off, q.win, q.cm, q.dt,
+      q.dvdt_max, q.v_rest, q.rest_band, q.dv_nbr, q.slice_ptr, q.col, m->norm, q.a0, q.raw, q.idx, q.count,
+      q.flag, q.counts);
   CUDA_TRY(cudaGetLastError());
   if (q.ev_mlp[0]) CUDA_TRY(cudaEventRecord(q.ev_mlp[0], st));
   if (m->gemm == kGemmTcgen05) {
-    TRY(forward_tc(m, q.n, q.a0, q.zout, false, q.err, st));
+    TRY(forward_tc(m, q.n, q.a0, q.zout, false, q.err, st, q.count));
   } else {
     TRY(ensure_workspace(m, q.n));
     CUDA_TRY(cudaMemcpyAsync(m->act[0], q.a0, q.n * kMlpIn0 * sizeof(__nv_bfloat16), cudaMemcpyDeviceToDevice, st));
@@ -1061,9 +1080,8 @@ tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
     CUDA_TRY(cudaMemcpyAsync(q.zout, m->z[kMlpLayers - 1], q.n * kMlpPad * sizeof(float), cudaMemcpyDeviceToDevice, st));
   }
   if (q.ev_mlp[1]) CUDA_TRY(cudaEventRecord(q.ev_mlp[1], st));
-  sur_commit_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.n, q.zout, q.raw, m->norm, q.Vprev, q.dinv, q.dt, q.win,
-                                                     q.dv_max, q.dvdt_max, q.v_rest, q.rest_band, q.state, q.flag,
-                                                     q.iion, q.counts);
+  sur_commit_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.count, q.n, q.idx, q.zout, q.raw, m->norm, q.dt, q.win,
+                                                     q.dv_max, q.state, q.flag, q.iion, q.counts);
   CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }

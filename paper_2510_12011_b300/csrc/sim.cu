@@ -109,6 +109,9 @@ struct tc_sim {
   uint8_t* sur_flag = nullptr;
   float *sur_iion = nullptr, *sur_raw = nullptr, *sur_zout = nullptr;
   __nv_bfloat16* sur_a0 = nullptr;
+  int32_t* sur_idx = nullptr;
+  int* sur_count = nullptr;
+  unsigned long long* sur_rows = nullptr;   // profiling: candidate rows summed over windows
   unsigned long long* sur_counts = nullptr;
   int* sur_err = nullptr;
 };
@@ -467,6 +470,8 @@ tc_status launch_step_any(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<
                                  : launch_step<float>(s, iv, k_off, ev, marks);
 }
 
+__global__ void add_count_kernel(const int* count, unsigned long long* acc) { *acc += (unsigned long long)*count; }
+
 // Surrogate inference at the start of a window: step *k_dev + k_off at buffer phase iv.  With
 // ev (profiling), four pooled events bracket the inference and its network; their first index is
 // appended to marks.
@@ -501,6 +506,8 @@ tc_status launch_surrogate(tc_sim* s, int iv, int k_off, size_t* ev = nullptr,
   q.slice_ptr = s->slice_ptr;
   q.col = s->col;
   q.a0 = s->sur_a0;
+  q.idx = s->sur_idx;
+  q.count = s->sur_count;
   q.raw = s->sur_raw;
   q.zout = s->sur_zout;
   q.flag = s->sur_flag;
@@ -509,6 +516,8 @@ tc_status launch_surrogate(tc_sim* s, int iv, int k_off, size_t* ev = nullptr,
   q.err = s->sur_err;
   TRY(surrogate_infer(s->sur, q, s->stream));
   if (ev) {
+    add_count_kernel<<<1, 1, 0, s->stream>>>(s->sur_count, s->sur_rows);
+    CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(s->evpool[*ev + 3], s->stream));
     marks->push_back(*ev);
     *ev += 4;
@@ -1155,6 +1164,12 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
       s->prof_acc.surrogate_windows += 1;
       s->prof_acc.mlp_ms += b;
     }
+    if (!sur_marks.empty()) {
+      unsigned long long rows = 0;
+      CUDA_TRY(cudaMemcpy(&rows, s->sur_rows, sizeof(rows), cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemset(s->sur_rows, 0, sizeof(rows)));
+      s->prof_acc.surrogate_rows += (int64_t)rows;
+    }
   }
   if (stats) {
     stats->steps = n_steps;
@@ -1197,6 +1212,10 @@ tc_status tc_set_surrogate(tc_sim* s, tc_mlp* mlp, int32_t window, double dv_max
     TRY(dalloc(s, &s->sur_raw, 20 * n));
     TRY(dalloc(s, &s->sur_zout, 32 * n));
     TRY(dalloc(s, &s->sur_a0, (size_t)kMlpIn0 * n));
+    TRY(dalloc(s, &s->sur_idx, n));
+    TRY(dalloc(s, &s->sur_count, 1));
+    TRY(dalloc(s, &s->sur_rows, 1));
+    CUDA_TRY(cudaMemset(s->sur_rows, 0, sizeof(unsigned long long)));
     TRY(dalloc(s, &s->sur_counts, 2));
     TRY(dalloc(s, &s->sur_err, 1));
     CUDA_TRY(cudaMemset(s->sur_flag, 0, n));

@@ -30,7 +30,9 @@ struct SurrogateStep {
   float v_rest, rest_band;      // and |V - v_rest| > rest_band (0 = off)
   const int32_t* slice_ptr;     // SELL-C-32 pattern of the system matrix
   const int32_t* col;
-  __nv_bfloat16* a0;            // [n][64] scratch (split-BF16 inputs)
+  __nv_bfloat16* a0;            // [n][64] scratch: compacted split-BF16 inputs of the candidates
+  int32_t* idx;                 // [n] node of each compacted row
+  int* count;                   // number of candidates (device)
   float* raw;                   // [20][n] scratch
   float* zout;                  // [n][32] scratch
   uint8_t* flag;                // [n] 1 = surrogate node for this window

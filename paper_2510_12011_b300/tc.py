@@ -45,7 +45,7 @@ class Profile(C.Structure):
     _fields_ = [("ionic_ms", C.c_double), ("ionic_launches", C.c_int64),
                 ("pcg_ms", C.c_double), ("pcg_launches", C.c_int64),
                 ("pcg_iterations", C.c_int64), ("surrogate_ms", C.c_double),
-                ("surrogate_windows", C.c_int64), ("mlp_ms", C.c_double)]
+                ("surrogate_windows", C.c_int64), ("mlp_ms", C.c_double), ("surrogate_rows", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
