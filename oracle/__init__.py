@@ -19,6 +19,9 @@ What it computes, and where the paper defines it (TorchCor, arXiv 2510.12011):
                   (Section 2.1, "LAT")
   * mms.py        the manufactured-solution verification (Section 3.1.1, Eqs. 4-8) and a 3D
                   zero-flux variant of it on tetrahedra
+  * mlp.py        the learned surrogate's network (forward, loss, gradients) and the exact
+                  single-cell window it is trained on
+  * partitioned.py Algorithm 1 over row-partitioned host ranks (the multi-GPU design check)
 
 Everything is float64.  Loops are vectorised over elements or nodes with numpy; no blocking,
 fusion or reordering beyond the definitions is done.  Pins: see tests/test_oracle_*.py.
