@@ -36,6 +36,10 @@ constexpr double kEC = 1.5, kMaxSR = 2.5, kMinSR = 1.0;
 constexpr double kBufc = 0.2, kKbufc = 0.001, kBufsr = 10.0, kKbufsr = 0.3, kBufss = 0.4;
 constexpr double kKbufss = 0.00025;
 constexpr double kRestV = -85.23;
+// natural logarithms of the constant concentrations of the Nernst potentials (Ko, Nao,
+// Ko + pKNa Nao, Cao), written out so that no logarithm of a constant is left to run time
+constexpr double kLnKo = 1.6863989535702288, kLnNao = 4.941642422609304;
+constexpr double kLnKsNa = 2.2617630984737906, kLnCao = 0.6931471805599453;
 }  // namespace tp06
 
 inline void tp06_rest_state(int /*cell*/, double* u, double* v0) {
@@ -191,18 +195,22 @@ __device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int ce
                                                          const Tp06VFactors<T>& f) {
   using namespace tp06;
   const T ki = u[0], nai = u[1], cai = u[2], cass = u[4];
-  const T ek = T(kRTF) * mlog(T(kKo) / ki);
-  const T ena = T(kRTF) * mlog(T(kNao) / nai);
-  const T eks = T(kRTF) * mlog(T(kKo + kPKNa * kNao) / (ki + T(kPKNa) * nai));
-  const T eca = T(0.5 * kRTF) * mlog(T(kCao) / cai);
+  // Nernst potentials as differences of logarithms (the constants' logarithms folded at compile
+  // time), which saves the divisions of the quotient forms
+  const T ek = T(kRTF) * (T(kLnKo) - mlog(ki));
+  const T ena = T(kRTF) * (T(kLnNao) - mlog(nai));
+  const T eks = T(kRTF) * (T(kLnKsNa) - mlog(ki + T(kPKNa) * nai));
+  const T eca = T(0.5 * kRTF) * (T(kLnCao) - mlog(cai));
   const T dv = V - ek;
-  const T ak1 = T(0.1) / (T(1) + mexp(T(0.06) * (dv - T(200))));
-  const T bk1 = (T(3) * mexp(T(0.0002) * (dv + T(100))) + mexp(T(0.1) * (dv - T(10)))) /
-                (T(1) + mexp(T(-0.5) * dv));
+  // alpha_K1 / (alpha_K1 + beta_K1) over one common denominator
+  const T ea = mexp(T(0.06) * (dv - T(200)));
+  const T eb = mexp(T(-0.5) * dv);
+  const T nb = T(3) * mexp(T(0.0002) * (dv + T(100))) + mexp(T(0.1) * (dv - T(10)));
+  const T na = T(0.1) * (T(1) + eb);
   Tp06Currents<T> c;
   const T gto = cell == 0 ? T(0.073) : T(0.294);
   const T gks = cell == 1 ? T(0.098) : T(0.392);
-  c.ik1 = T(kGK1) * (ak1 / (ak1 + bk1)) * dv;   // sqrt(Ko/5.4) = 1 at Ko = 5.4 mM
+  c.ik1 = T(kGK1) * (na / (na + nb * (T(1) + ea))) * dv;   // sqrt(Ko/5.4) = 1 at Ko = 5.4 mM
   c.ito = gto * u[17] * u[16] * dv;
   c.ikr = T(kGKr) * u[6] * u[7] * dv;
   c.iks = gks * u[8] * u[8] * (V - eks);
@@ -217,13 +225,8 @@ __device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int ce
   return c;
 }
 
-// Rush-Larsen update of one gate: u_inf + (u - u_inf) exp(-dt/tau).
-template <typename T>
-__device__ __forceinline__ T rl(T u, T inf, T tau, T dt) {
-  return inf + (u - inf) * mexp(-dt / tau);
-}
-
-// The same with the gate's total rate alpha + beta = 1/tau given (no division).
+// Rush-Larsen update of one gate, u_inf + (u - u_inf) exp(-dt/tau), with the gate's rate
+// 1/tau given (no division).
 template <typename T>
 __device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dt) {
   return inf + (u - inf) * mexp(-dt * rate);
@@ -241,19 +244,22 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   T un[kTP06States];
   {
     const T cai = u[2], casr = u[3], cass = u[4], rbar = u[5];
-    const T ecs = T(kEC) / casr;
-    const T kcasr = T(kMaxSR) - T(kMaxSR - kMinSR) / (T(1) + ecs * ecs);
-    const T k1 = T(kK1p) / kcasr, k2 = T(kK2p) * kcasr;
+    // the same expressions with each quotient of quotients over one denominator
+    const T casr2 = casr * casr;
+    const T kcasr = T(kMaxSR) - T(kMaxSR - kMinSR) * casr2 / (casr2 + T(kEC * kEC));
+    const T k2 = T(kK2p) * kcasr;
     const T cass2 = cass * cass;
-    const T o = k1 * cass2 * rbar / (T(kK3) + k1 * cass2);
+    const T o = T(kK1p) * cass2 * rbar / (T(kK3) * kcasr + T(kK1p) * cass2);
     const T irel = T(kVrel) * o * (casr - cass);
     const T ileak = T(kVleak) * (casr - cai);
-    const T iup = T(kVmaxUp) / (T(1) + T(kKup * kKup) / (cai * cai));
+    const T cai2 = cai * cai;
+    const T iup = T(kVmaxUp) * cai2 / (cai2 + T(kKup * kKup));
     const T ixfer = T(kVxfer) * (cass - cai);
     const T bi = cai + T(kKbufc), bsr = casr + T(kKbufsr), bss = cass + T(kKbufss);
-    const T fi = T(1) / (T(1) + T(kBufc * kKbufc) / (bi * bi));
-    const T fsr = T(1) / (T(1) + T(kBufsr * kKbufsr) / (bsr * bsr));
-    const T fss = T(1) / (T(1) + T(kBufss * kKbufss) / (bss * bss));
+    const T bi2 = bi * bi, bsr2 = bsr * bsr, bss2 = bss * bss;
+    const T fi = bi2 / (bi2 + T(kBufc * kKbufc));
+    const T fsr = bsr2 / (bsr2 + T(kBufsr * kKbufsr));
+    const T fss = bss2 / (bss2 + T(kBufss * kKbufss));
     const T cvf = T(kCap / (kVc * kF));
     const T dki = -(c.ik1 + c.ito + c.ikr + c.iks + c.ipk - T(2) * c.inak) * cvf;
     const T dnai = -(c.ina + c.ibna + T(3) * c.inak + T(3) * c.inaca) * cvf;
@@ -270,75 +276,96 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     un[4] = cass + dt * dcass;
     un[5] = rbar + dt * drbar;
   }
-  // gates: Rush-Larsen with inf and tau at V^k (fCass at CaSS^k)
+  // gates: Rush-Larsen with inf and tau at V^k (fCass at CaSS^k).  Each rate 1/tau is formed
+  // directly over one common denominator (one division where tau is a sum of quotients, none
+  // where it is a product of them); divisions by constants are multiplications by reciprocals.
   {
-    const T e1 = mexp((T(-56.86) - V) / T(9.03));
+    const T e1 = mexp((T(-56.86) - V) * T(1.0 / 9.03));
     const T minf = T(1) / ((T(1) + e1) * (T(1) + e1));
-    const T am = T(1) / (T(1) + mexp((T(-60) - V) / T(5)));
-    const T bm = T(0.1) / (T(1) + mexp((V + T(35)) / T(5))) +
-                 T(0.1) / (T(1) + mexp((V - T(50)) / T(200)));
-    un[9] = rl(u[9], minf, am * bm, dt);
-    const T e2 = mexp((V + T(71.55)) / T(7.43));
+    // tau_m = alpha_m beta_m, alpha_m = 1/(1+ea), beta_m = 0.1/(1+eb) + 0.1/(1+ec)
+    const T ea = T(1) + mexp((T(-60) - V) * T(0.2));
+    const T eb = T(1) + mexp((V + T(35)) * T(0.2));
+    const T ec = T(1) + mexp((V - T(50)) * T(1.0 / 200.0));
+    un[9] = rl_rate(u[9], minf, ea * eb * ec / (T(0.1) * (eb + ec)), dt);
+    const T e2 = mexp((V + T(71.55)) * T(1.0 / 7.43));
     const T hinf = T(1) / ((T(1) + e2) * (T(1) + e2));
-    T ah, bh, aj, bj;
+    T rh, rj;   // alpha + beta of h and of j
     if (V < T(-40)) {
-      ah = T(0.057) * mexp(-(V + T(80)) / T(6.8));
-      bh = T(2.7) * mexp(T(0.079) * V) + T(3.1e5) * mexp(T(0.3485) * V);
-      aj = (T(-2.5428e4) * mexp(T(0.2444) * V) - T(6.948e-6) * mexp(T(-0.04391) * V)) *
-           (V + T(37.78)) / (T(1) + mexp(T(0.311) * (V + T(79.23))));
-      bj = T(0.02424) * mexp(T(-0.01052) * V) / (T(1) + mexp(T(-0.1378) * (V + T(40.14))));
+      rh = T(0.057) * mexp((V + T(80)) * T(-1.0 / 6.8)) + T(2.7) * mexp(T(0.079) * V) +
+           T(3.1e5) * mexp(T(0.3485) * V);
+      const T ja = T(1) + mexp(T(0.311) * (V + T(79.23)));
+      const T jb = T(1) + mexp(T(-0.1378) * (V + T(40.14)));
+      rj = ((T(-2.5428e4) * mexp(T(0.2444) * V) - T(6.948e-6) * mexp(T(-0.04391) * V)) * (V + T(37.78)) * jb +
+            T(0.02424) * mexp(T(-0.01052) * V) * ja) /
+           (ja * jb);
     } else {
-      ah = T(0);
-      bh = T(0.77) / (T(0.13) * (T(1) + mexp(-(V + T(10.66)) / T(11.1))));
-      aj = T(0);
-      bj = T(0.6) * mexp(T(0.057) * V) / (T(1) + mexp(T(-0.1) * (V + T(32))));
+      rh = T(0.77 / 0.13) / (T(1) + mexp((V + T(10.66)) * T(-1.0 / 11.1)));
+      rj = T(0.6) * mexp(T(0.057) * V) / (T(1) + mexp(T(-0.1) * (V + T(32))));
     }
-    un[10] = rl_rate(u[10], hinf, ah + bh, dt);
-    un[11] = rl_rate(u[11], hinf, aj + bj, dt);
-    const T xr1inf = T(1) / (T(1) + mexp((T(-26) - V) / T(7)));
-    const T txr1 = T(450) / (T(1) + mexp((T(-45) - V) / T(10))) * T(6) /
-                   (T(1) + mexp((V + T(30)) / T(11.5)));
-    un[6] = rl(u[6], xr1inf, txr1, dt);
-    const T xr2inf = T(1) / (T(1) + mexp((V + T(88)) / T(24)));
-    const T txr2 = T(3) / (T(1) + mexp((T(-60) - V) / T(20))) * T(1.12) /
-                   (T(1) + mexp((V - T(60)) / T(20)));
-    un[7] = rl(u[7], xr2inf, txr2, dt);
-    const T xsinf = T(1) / (T(1) + mexp((T(-5) - V) / T(14)));
-    const T txs = T(1400) / msqrt(T(1) + mexp((T(5) - V) / T(6))) /
-                  (T(1) + mexp((V - T(35)) / T(15))) + T(80);
-    un[8] = rl(u[8], xsinf, txs, dt);
-    const T rinf = T(1) / (T(1) + mexp((T(20) - V) / T(6)));
+    un[10] = rl_rate(u[10], hinf, rh, dt);
+    un[11] = rl_rate(u[11], hinf, rj, dt);
+    // tau_xr1 = 450/(1+e) * 6/(1+e'):  1/tau = (1+e)(1+e')/2700
+    const T xr1inf = T(1) / (T(1) + mexp((T(-26) - V) * T(1.0 / 7.0)));
+    un[6] = rl_rate(u[6], xr1inf,
+                    (T(1) + mexp((T(-45) - V) * T(0.1))) * (T(1) + mexp((V + T(30)) * T(1.0 / 11.5))) *
+                        T(1.0 / 2700.0),
+                    dt);
+    // tau_xr2 = 3/(1+e) * 1.12/(1+e'):  1/tau = (1+e)(1+e')/3.36
+    const T xr2inf = T(1) / (T(1) + mexp((V + T(88)) * T(1.0 / 24.0)));
+    un[7] = rl_rate(u[7], xr2inf,
+                    (T(1) + mexp((T(-60) - V) * T(0.05))) * (T(1) + mexp((V - T(60)) * T(0.05))) *
+                        T(1.0 / 3.36),
+                    dt);
+    // tau_xs = 1400/(sqrt(1+e)(1+e')) + 80
+    const T xsinf = T(1) / (T(1) + mexp((T(-5) - V) * T(1.0 / 14.0)));
+    const T sx = msqrt(T(1) + mexp((T(5) - V) * T(1.0 / 6.0))) * (T(1) + mexp((V - T(35)) * T(1.0 / 15.0)));
+    un[8] = rl_rate(u[8], xsinf, sx / (T(1400) + T(80) * sx), dt);
+    const T rinf = T(1) / (T(1) + mexp((T(20) - V) * T(1.0 / 6.0)));
     const T vr = V + T(40);
-    un[17] = rl(u[17], rinf, T(9.5) * mexp(-vr * vr / T(1800)) + T(0.8), dt);
-    T sinf, ts;
+    un[17] = rl_rate(u[17], rinf, T(1) / (T(9.5) * mexp(vr * vr * T(-1.0 / 1800.0)) + T(0.8)), dt);
+    T sinf, rs;
     if (cell == 0) {
-      sinf = T(1) / (T(1) + mexp((V + T(28)) / T(5)));
+      sinf = T(1) / (T(1) + mexp((V + T(28)) * T(0.2)));
       const T vs = V + T(67);
-      ts = T(1000) * mexp(-vs * vs / T(1000)) + T(8);
+      rs = T(1) / (T(1000) * mexp(vs * vs * T(-1.0 / 1000.0)) + T(8));
     } else {
-      sinf = T(1) / (T(1) + mexp((V + T(20)) / T(5)));
+      sinf = T(1) / (T(1) + mexp((V + T(20)) * T(0.2)));
       const T vs = V + T(45);
-      ts = T(85) * mexp(-vs * vs / T(320)) + T(5) / (T(1) + mexp((V - T(20)) / T(5))) + T(3);
+      // tau_s = 85 e + 5/(1+e') + 3
+      const T es = T(1) + mexp((V - T(20)) * T(0.2));
+      rs = es / ((T(85) * mexp(vs * vs * T(-1.0 / 320.0)) + T(3)) * es + T(5));
     }
-    un[16] = rl(u[16], sinf, ts, dt);
-    const T dinf = T(1) / (T(1) + mexp((T(-8) - V) / T(7.5)));
-    const T td = (T(1.4) / (T(1) + mexp((T(-35) - V) / T(13))) + T(0.25)) * T(1.4) /
-                     (T(1) + mexp((V + T(5)) / T(5))) +
-                 T(1) / (T(1) + mexp((T(50) - V) / T(20)));
-    un[12] = rl(u[12], dinf, td, dt);
-    const T finf = T(1) / (T(1) + mexp((V + T(20)) / T(7)));
+    un[16] = rl_rate(u[16], sinf, rs, dt);
+    // tau_d = (1.4/(1+ea) + 0.25) * 1.4/(1+eb) + 1/(1+ec)
+    const T dinf = T(1) / (T(1) + mexp((T(-8) - V) * T(1.0 / 7.5)));
+    {
+      const T da = T(1) + mexp((T(-35) - V) * T(1.0 / 13.0));
+      const T db = T(1) + mexp((V + T(5)) * T(0.2));
+      const T dc = T(1) + mexp((T(50) - V) * T(0.05));
+      un[12] = rl_rate(u[12], dinf, da * db * dc / ((T(1.4) + T(0.25) * da) * T(1.4) * dc + da * db), dt);
+    }
+    // tau_f = 1102.5 e + 200/(1+ea) + 180/(1+eb) + 20
+    const T finf = T(1) / (T(1) + mexp((V + T(20)) * T(1.0 / 7.0)));
     const T vf27 = V + T(27);
-    const T tf = T(1102.5) * mexp(-vf27 * vf27 / T(225)) + T(200) / (T(1) + mexp((T(13) - V) / T(10))) +
-                 T(180) / (T(1) + mexp((V + T(30)) / T(10))) + T(20);
-    un[13] = rl(u[13], finf, tf, dt);
-    const T f2inf = T(0.67) / (T(1) + mexp((V + T(35)) / T(7))) + T(0.33);
+    {
+      const T fa = T(1) + mexp((T(13) - V) * T(0.1));
+      const T fb = T(1) + mexp((V + T(30)) * T(0.1));
+      const T num = (T(1102.5) * mexp(vf27 * vf27 * T(-1.0 / 225.0)) + T(20)) * fa * fb + T(200) * fb + T(180) * fa;
+      un[13] = rl_rate(u[13], finf, fa * fb / num, dt);
+    }
+    // tau_f2 = 600 e + 31/(1+ea) + 16/(1+eb)
+    const T f2inf = T(0.67) / (T(1) + mexp((V + T(35)) * T(1.0 / 7.0))) + T(0.33);
     const T vf25 = V + T(25);
-    const T tf2 = T(600) * mexp(-vf25 * vf25 / T(170)) + T(31) / (T(1) + mexp((T(25) - V) / T(10))) +
-                  T(16) / (T(1) + mexp((V + T(30)) / T(10)));
-    un[14] = rl(u[14], f2inf, tf2, dt);
-    const T cs = u[4] / T(0.05);
-    const T cs2 = cs * cs;
-    un[15] = rl(u[15], T(0.6) / (T(1) + cs2) + T(0.4), T(80) / (T(1) + cs2) + T(2), dt);
+    {
+      const T ga = T(1) + mexp((T(25) - V) * T(0.1));
+      const T gb = T(1) + mexp((V + T(30)) * T(0.1));
+      const T num = T(600) * mexp(vf25 * vf25 * T(-1.0 / 170.0)) * ga * gb + T(31) * gb + T(16) * ga;
+      un[14] = rl_rate(u[14], f2inf, ga * gb / num, dt);
+    }
+    // fCass: inf = 0.6/(1+cs^2) + 0.4, tau = 80/(1+cs^2) + 2, cs = CaSS/0.05
+    const T cs = u[4] * T(20);
+    const T q = T(1) / (T(1) + cs * cs);
+    un[15] = rl_rate(u[15], T(0.6) * q + T(0.4), T(1) / (T(80) * q + T(2)), dt);
   }
 #pragma unroll
   for (int j = 0; j < kTP06States; ++j) u[j] = un[j];
