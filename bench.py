@@ -35,10 +35,10 @@ from paper_2510_12011_b300 import inputs as I  # noqa: E402
 METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + activation "
           "capture); FP32 precision form alongside")
 # FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
-# profiles/ (thread-level FP64 instructions / nodes); used to turn the live launch time into an
-# achieved FP64 instruction rate.
-TP06_FP64_INSTR_PER_NODE = 2188.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 110.35e6   # dram read + write of the same capture
+# profiles/ (FP64 pipe utilisation x elapsed cycles x 296 thread instructions per clock / nodes);
+# used to turn the live launch time into an achieved FP64 instruction rate.
+TP06_FP64_INSTR_PER_NODE = 1761.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.91e6   # dram read + write of the same capture
 
 
 def parse():
