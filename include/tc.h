@@ -258,6 +258,9 @@ tc_status tc_set_wait_limit(tc_sim* sim, int64_t polls);
  * (table-driven, Tang 1989) and the CUDA library exp at the host inputs x[n]; y_fast[n] and
  * y_ref[n] receive the two results (host arrays).  Diagnostics; allocates 24 n bytes. */
 tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_t n);
+/* tc_selftest_log: the same for the FP64 natural logarithm of the ionic kernels (table-driven,
+ * Tang 1990) against the CUDA library log. */
+tc_status tc_selftest_log(const double* x, double* y_fast, double* y_ref, int64_t n);
 
 /* ---- learned ionic surrogate --------------------------------------------------------
  * A multilayer perceptron (20 -> 4 x 256 SiLU -> 19; BF16 weights and activations, FP32

@@ -40,6 +40,13 @@ constexpr double kRestV = -85.23;
 // Ko + pKNa Nao, Cao), written out so that no logarithm of a constant is left to run time
 constexpr double kLnKo = 1.6863989535702288, kLnNao = 4.941642422609304;
 constexpr double kLnKsNa = 2.2617630984737906, kLnCao = 0.6931471805599453;
+// exp(b) for the offsets b of gate exponents exp(a V + b) that share a slope a with another
+// (then exp(a V + b) = exp(a V) exp(b): one exponential per slope)
+constexpr double kE7 = 1096.6331584284585, kE4 = 54.598150033144236, kEm4 = 0.01831563888873418;
+constexpr double kE5p6 = 270.42640742615254, kE1 = 2.718281828459045, kEm4p5 = 0.011108996538242306;
+constexpr double kE1p3 = 3.6692966676192444, kE2p5 = 12.182493960703473, kEm3p2 = 0.04076220397836621;
+constexpr double kE5o6 = 2.300975890892825, kE20o6 = 28.03162489452614, kE20o7 = 17.41170806332765;
+constexpr double kE5 = 148.4131591025766, kEm3 = 0.049787068367863944;
 }  // namespace tp06
 
 inline void tp06_rest_state(int /*cell*/, double* u, double* v0) {
@@ -106,15 +113,189 @@ static __constant__ double kExp2Lo[64] = {
     -0x1.e9c23179c2893p-54, 0x1.dc7f486a4b6b0p-54, 0x1.9d3e12dd8a18bp-54,
     0x1.74853f3a5931ep-55,
 };
+// Natural logarithm, table method (Tang 1990): for positive normal x = 2^e m, m in [1, 2), take
+// F = 1 + j/128 with j the top seven fraction bits of m and c = fl(1/F); then r = m c - 1 (one
+// FMA, exact before its final rounding, 0 <= r < 2^-7) and ln x = e ln2 - ln c + log1p(r), with
+// -ln c from a hi + lo table (of the rounded reciprocal itself, so the rounding of c costs
+// nothing) and log1p(r) by its Taylor polynomial to r^8 (truncation < 2^-63).  ln2 is split into
+// hi (43 bits, so that e ln2_hi is exact) + lo.  Other x (zero, negative, subnormal, inf, NaN)
+// go to the library log.  The tables (and the 2^(j/64) pairs above) are regenerated by
+// math_tables.py beside this file.
+// kLogInv[j] = fl(1/(1 + j/128)); kLogHi[j] + kLogLo[j] = -ln(kLogInv[j])
+static __constant__ double kLogInv[128] = {
+    0x1.0000000000000p+0, 0x1.fc07f01fc07f0p-1, 0x1.f81f81f81f820p-1,
+    0x1.f44659e4a4271p-1, 0x1.f07c1f07c1f08p-1, 0x1.ecc07b301ecc0p-1,
+    0x1.e9131abf0b767p-1, 0x1.e573ac901e574p-1, 0x1.e1e1e1e1e1e1ep-1,
+    0x1.de5d6e3f8868ap-1, 0x1.dae6076b981dbp-1, 0x1.d77b654b82c34p-1,
+    0x1.d41d41d41d41dp-1, 0x1.d0cb58f6ec074p-1, 0x1.cd85689039b0bp-1,
+    0x1.ca4b3055ee191p-1, 0x1.c71c71c71c71cp-1, 0x1.c3f8f01c3f8f0p-1,
+    0x1.c0e070381c0e0p-1, 0x1.bdd2b899406f7p-1, 0x1.bacf914c1bad0p-1,
+    0x1.b7d6c3dda338bp-1, 0x1.b4e81b4e81b4fp-1, 0x1.b2036406c80d9p-1,
+    0x1.af286bca1af28p-1, 0x1.ac5701ac5701bp-1, 0x1.a98ef606a63bep-1,
+    0x1.a6d01a6d01a6dp-1, 0x1.a41a41a41a41ap-1, 0x1.a16d3f97a4b02p-1,
+    0x1.9ec8e951033d9p-1, 0x1.9c2d14ee4a102p-1, 0x1.999999999999ap-1,
+    0x1.970e4f80cb872p-1, 0x1.948b0fcd6e9e0p-1, 0x1.920fb49d0e229p-1,
+    0x1.8f9c18f9c18fap-1, 0x1.8d3018d3018d3p-1, 0x1.8acb90f6bf3aap-1,
+    0x1.886e5f0abb04ap-1, 0x1.8618618618618p-1, 0x1.83c977ab2beddp-1,
+    0x1.8181818181818p-1, 0x1.7f405fd017f40p-1, 0x1.7d05f417d05f4p-1,
+    0x1.7ad2208e0ecc3p-1, 0x1.78a4c8178a4c8p-1, 0x1.767dce434a9b1p-1,
+    0x1.745d1745d1746p-1, 0x1.724287f46debcp-1, 0x1.702e05c0b8170p-1,
+    0x1.6e1f76b4337c7p-1, 0x1.6c16c16c16c17p-1, 0x1.6a13cd1537290p-1,
+    0x1.6816816816817p-1, 0x1.661ec6a5122f9p-1, 0x1.642c8590b2164p-1,
+    0x1.623fa77016240p-1, 0x1.6058160581606p-1, 0x1.5e75bb8d015e7p-1,
+    0x1.5c9882b931057p-1, 0x1.5ac056b015ac0p-1, 0x1.58ed2308158edp-1,
+    0x1.571ed3c506b3ap-1, 0x1.5555555555555p-1, 0x1.5390948f40febp-1,
+    0x1.51d07eae2f815p-1, 0x1.5015015015015p-1, 0x1.4e5e0a72f0539p-1,
+    0x1.4cab88725af6ep-1, 0x1.4afd6a052bf5bp-1, 0x1.49539e3b2d067p-1,
+    0x1.47ae147ae147bp-1, 0x1.460cbc7f5cf9ap-1, 0x1.446f86562d9fbp-1,
+    0x1.42d6625d51f87p-1, 0x1.4141414141414p-1, 0x1.3fb013fb013fbp-1,
+    0x1.3e22cbce4a902p-1, 0x1.3c995a47babe7p-1, 0x1.3b13b13b13b14p-1,
+    0x1.3991c2c187f63p-1, 0x1.3813813813814p-1, 0x1.3698df3de0748p-1,
+    0x1.3521cfb2b78c1p-1, 0x1.33ae45b57bcb2p-1, 0x1.323e34a2b10bfp-1,
+    0x1.30d190130d190p-1, 0x1.2f684bda12f68p-1, 0x1.2e025c04b8097p-1,
+    0x1.2c9fb4d812ca0p-1, 0x1.2b404ad012b40p-1, 0x1.29e4129e4129ep-1,
+    0x1.288b01288b013p-1, 0x1.27350b8812735p-1, 0x1.25e22708092f1p-1,
+    0x1.2492492492492p-1, 0x1.23456789abcdfp-1, 0x1.21fb78121fb78p-1,
+    0x1.20b470c67c0d9p-1, 0x1.1f7047dc11f70p-1, 0x1.1e2ef3b3fb874p-1,
+    0x1.1cf06ada2811dp-1, 0x1.1bb4a4046ed29p-1, 0x1.1a7b9611a7b96p-1,
+    0x1.19453808ca29cp-1, 0x1.1811811811812p-1, 0x1.16e0689427379p-1,
+    0x1.15b1e5f75270dp-1, 0x1.1485f0e0acd3bp-1, 0x1.135c81135c811p-1,
+    0x1.12358e75d3033p-1, 0x1.1111111111111p-1, 0x1.0fef010fef011p-1,
+    0x1.0ecf56be69c90p-1, 0x1.0db20a88f4696p-1, 0x1.0c9714fbcda3bp-1,
+    0x1.0b7e6ec259dc8p-1, 0x1.0a6810a6810a7p-1, 0x1.0953f39010954p-1,
+    0x1.0842108421084p-1, 0x1.073260a47f7c6p-1, 0x1.0624dd2f1a9fcp-1,
+    0x1.05197f7d73404p-1, 0x1.0410410410410p-1, 0x1.03091b51f5e1ap-1,
+    0x1.0204081020408p-1, 0x1.0101010101010p-1,
+};
+static __constant__ double kLogHi[128] = {
+    0x0.0p+0, 0x1.fe02a6b106799p-8, 0x1.fc0a8b0fc03c4p-7,
+    0x1.7b91b07d5b126p-6, 0x1.f829b0e7832f8p-6, 0x1.39e87b9febd68p-5,
+    0x1.77458f632dcffp-5, 0x1.b42dd711971b9p-5, 0x1.f0a30c01162a8p-5,
+    0x1.16536eea37ae3p-4, 0x1.341d7961bd1d0p-4, 0x1.51b073f06183cp-4,
+    0x1.6f0d28ae56b4ep-4, 0x1.8c345d6319b23p-4, 0x1.a926d3a4ad562p-4,
+    0x1.c5e548f5bc743p-4, 0x1.e27076e2af2eap-4, 0x1.fec9131dbeabcp-4,
+    0x1.0d77e7cd08e5bp-3, 0x1.1b72ad52f67a2p-3, 0x1.29552f81ff521p-3,
+    0x1.371fc201e8f75p-3, 0x1.44d2b6ccb7d1cp-3, 0x1.526e5e3a1b438p-3,
+    0x1.5ff3070a793d6p-3, 0x1.6d60fe719d21bp-3, 0x1.7ab890210d907p-3,
+    0x1.87fa06520c911p-3, 0x1.9525a9cf456b6p-3, 0x1.a23bc1fe2b561p-3,
+    0x1.af3c94e80bff3p-3, 0x1.bc286742d8cd4p-3, 0x1.c8ff7c79a9a20p-3,
+    0x1.d5c216b4fbb94p-3, 0x1.e27076e2af2e8p-3, 0x1.ef0adcbdc5935p-3,
+    0x1.fb9186d5e3e29p-3, 0x1.0402594b4d041p-2, 0x1.0a324e27390e2p-2,
+    0x1.1058bf9ae4ad4p-2, 0x1.1675cababa60fp-2, 0x1.1c898c16999fbp-2,
+    0x1.22941fbcf7966p-2, 0x1.2895a13de86a4p-2, 0x1.2e8e2bae11d31p-2,
+    0x1.347dd9a987d56p-2, 0x1.3a64c556945eap-2, 0x1.404308686a7e4p-2,
+    0x1.4618bc21c5ec2p-2, 0x1.4be5f957778a1p-2, 0x1.51aad872df82ep-2,
+    0x1.5767717455a6cp-2, 0x1.5d1bdbf5809cap-2, 0x1.62c82f2b9c796p-2,
+    0x1.686c81e9b14adp-2, 0x1.6e08eaa2ba1e4p-2, 0x1.739d7f6bbd007p-2,
+    0x1.792a55fdd47a1p-2, 0x1.7eaf83b82afc2p-2, 0x1.842d1da1e8b18p-2,
+    0x1.89a3386c1425bp-2, 0x1.8f11e873662c8p-2, 0x1.947941c2116fbp-2,
+    0x1.99d958117e08ap-2, 0x1.9f323ecbf984dp-2, 0x1.a484090e5bb09p-2,
+    0x1.a9cec9a9a084ap-2, 0x1.af1293247786bp-2, 0x1.b44f77bcc8f64p-2,
+    0x1.b9858969310fdp-2, 0x1.beb4d9da71b7ap-2, 0x1.c3dd7a7cdad4dp-2,
+    0x1.c8ff7c79a9a21p-2, 0x1.ce1af0b85f3ecp-2, 0x1.d32fe7e00ebd5p-2,
+    0x1.d83e7258a2f3ep-2, 0x1.dd46a04c1c4a1p-2, 0x1.e24881a7c6c26p-2,
+    0x1.e744261d68789p-2, 0x1.ec399d2468cc1p-2, 0x1.f128f5faf06ecp-2,
+    0x1.f6123fa7028adp-2, 0x1.faf588f78f31dp-2, 0x1.ffd2e0857f497p-2,
+    0x1.02552a5a5d0ffp-1, 0x1.04bdf9da926d2p-1, 0x1.0723e5c1cdf41p-1,
+    0x1.0986f4f573521p-1, 0x1.0be72e4252a83p-1, 0x1.0e44985d1cc8cp-1,
+    0x1.109f39e2d4c96p-1, 0x1.12f719593efbdp-1, 0x1.154c3d2f4d5eap-1,
+    0x1.179eabbd899a0p-1, 0x1.19ee6b467c96fp-1, 0x1.1c3b81f713c25p-1,
+    0x1.1e85f5e7040d1p-1, 0x1.20cdcd192ab6ep-1, 0x1.23130d7bebf43p-1,
+    0x1.2555bce98f7cap-1, 0x1.2795e1289b11bp-1, 0x1.29d37fec2b08bp-1,
+    0x1.2c0e9ed448e8cp-1, 0x1.2e47436e40268p-1, 0x1.307d7334f10bep-1,
+    0x1.32b1339121d71p-1, 0x1.34e289d9ce1d2p-1, 0x1.37117b54747b6p-1,
+    0x1.393e0d3562a1ap-1, 0x1.3b68449fffc23p-1, 0x1.3d9026a7156fbp-1,
+    0x1.3fb5b84d16f43p-1, 0x1.41d8fe84672afp-1, 0x1.43f9fe2f9ce67p-1,
+    0x1.4618bc21c5ec2p-1, 0x1.48353d1ea88dfp-1, 0x1.4a4f85db03ebbp-1,
+    0x1.4c679afccee39p-1, 0x1.4e7d811b75bb0p-1, 0x1.50913cc01686bp-1,
+    0x1.52a2d265bc5abp-1, 0x1.54b2467999498p-1, 0x1.56bf9d5b3f399p-1,
+    0x1.58cadb5cd7989p-1, 0x1.5ad404c359f2dp-1, 0x1.5cdb1dc6c1765p-1,
+    0x1.5ee02a9241676p-1, 0x1.60e32f44788d9p-1,
+};
+static __constant__ double kLogLo[128] = {
+    0x0.0p+0, -0x1.e44b7e3711e7fp-67, -0x1.83092c5964281p-62,
+    -0x1.6d80ab38e9430p-62, 0x1.33e3f04f1ef25p-60, -0x1.5bfa937f551b7p-59,
+    0x1.8d3ca87b92968p-63, 0x1.0a34531f67db5p-59, 0x1.85f325c5bbacdp-59,
+    0x1.2189705cf74cap-58, -0x1.3599f227becbbp-58, -0x1.5b61c65e5741ap-58,
+    -0x1.20db323097324p-59, -0x1.294d2f5668495p-58, -0x1.d7a16eab1e2adp-59,
+    0x1.2eb0bf7c0b0d9p-59, -0x1.61578001e015ap-60, -0x1.5746b9981b36cp-58,
+    0x1.9a5dc5e9030adp-57, -0x1.fbe7ee5c69946p-57, 0x1.301771c407dc0p-57,
+    0x1.e6cb62af18a02p-62, 0x1.7d3d950f87e23p-59, -0x1.546ff8a470d3ap-57,
+    -0x1.bc60efafc6f6cp-58, 0x1.d551d97132e87p-57, -0x1.1072534a57e7dp-57,
+    -0x1.9f7fdbfa08d9ap-57, -0x1.26fb3e2b1d1dap-57, 0x1.24dc46c1ea664p-57,
+    0x1.a3398064df33ep-57, 0x1.cfce744870f57p-58, -0x1.4f689f8434011p-57,
+    -0x1.a37794d03657dp-58, -0x1.61578001e015ep-59, 0x1.e8637950dc20dp-57,
+    0x1.355519b0de535p-57, -0x1.08ec217a5022dp-57, 0x1.bdcfde8061c03p-56,
+    0x1.3f415699663ecp-63, 0x1.ce63eab883727p-61, 0x1.9f1a39d500e3cp-56,
+    -0x1.dbd7ac258a2bdp-58, 0x1.7ad24c13f040fp-56, -0x1.1e99b72bd7bf2p-57,
+    -0x1.16ea62c048cfbp-56, 0x1.cbcd735d03424p-60, -0x1.f79f6c1059cdbp-57,
+    -0x1.7a42642661c62p-61, -0x1.4b366b609027ap-58, -0x1.d8db0a7cc1543p-56,
+    -0x1.fb2a49af933e8p-57, -0x1.7dc9c7c23801fp-56, -0x1.090a0dd59fe35p-58,
+    0x1.710af840538e3p-56, -0x1.bfb1b39ca3a0fp-56, 0x1.ce24c53fad3f0p-58,
+    0x1.f057691fe9ed7p-56, -0x1.698b43096b576p-59, 0x1.54ec519784677p-56,
+    0x1.2d38c40881e0bp-57, 0x1.f85da755a61a3p-56, 0x1.1266e8a3e8838p-57,
+    -0x1.315b444ee1f38p-56, -0x1.a92e513217f58p-59, 0x1.fff29adc3ad3bp-56,
+    -0x1.ab7b00ad0dabcp-58, 0x1.533844a15dc28p-58, -0x1.a0892a8b38eedp-61,
+    -0x1.f3827583b8877p-57, 0x1.be1874deaef08p-56, 0x1.7d9e0a5bd4d37p-57,
+    0x1.3097607bcbfeep-56, -0x1.6416a1aa97b31p-57, 0x1.4ef6465f5f46ep-57,
+    0x1.c515ba2ec9444p-58, -0x1.19d95b62e2476p-62, 0x1.05ec7a2caa523p-57,
+    0x1.cdf68dbcf2ed3p-56, -0x1.94623581958cfp-59, -0x1.328df13bb38c2p-56,
+    0x1.5456c3cb6cd06p-58, 0x1.cd7d9f2754362p-57, -0x1.4d05f9366f27fp-59,
+    0x1.e9c695d7ee800p-57, 0x1.8fe60804593bfp-56, -0x1.6a1a71dbba44ep-59,
+    -0x1.37012b5805e02p-56, 0x1.b4c4bdd99efffp-56, -0x1.c546885a5a707p-59,
+    0x1.f78fb26c2de46p-55, -0x1.67f6e731c1795p-56, 0x1.98f33a3965e29p-57,
+    -0x1.c73e320bf059fp-58, -0x1.fa3422887e218p-57, -0x1.0b583899021d1p-56,
+    -0x1.084e99683070ep-55, -0x1.aabf0bc229014p-55, -0x1.748725e374d6ep-55,
+    0x1.9810eb6b440f4p-55, 0x1.ade0fcf6e5a1dp-55, 0x1.01735b2e9733fp-55,
+    -0x1.8a158f3917586p-55, 0x1.0950861a4886bp-55, 0x1.fdac850fab36dp-56,
+    0x1.d02ab5b3d916bp-56, 0x1.775c96c42e729p-56, -0x1.808bf6deec882p-55,
+    -0x1.38eef67f2483ap-55, 0x1.c63b7b06164dap-55, 0x1.0084c7a15a4f5p-58,
+    0x1.0a74ea82e55dfp-56, -0x1.ee6d0cf42e7fap-55, 0x1.e1c9ee6d83b86p-55,
+    0x1.e85bd9bd99e3ap-56, -0x1.40a85d133f80bp-55, -0x1.d76102e1644f2p-55,
+    -0x1.e971322ce7900p-57, -0x1.5d3d9ea6e9ea8p-55, 0x1.9e59d2d85ab62p-56,
+    0x1.73be4578ad97bp-56, 0x1.f4550a2d0f60cp-55, 0x1.11c6217363fcbp-57,
+    0x1.624bc9764c22cp-55, 0x1.eca6aa97c08e7p-55, 0x1.47b71e2eb8419p-56,
+    -0x1.bca7da80b6f7ep-55, -0x1.58376a5f4b135p-57,
+};
+
 static __shared__ double s_exp2_hi[64];
 static __shared__ double s_exp2_lo[64];
+static __shared__ double s_log_inv[128];
+static __shared__ double s_log_hi[128];
+static __shared__ double s_log_lo[128];
 
+// Copies the exp and log tables into this block's shared memory (call before any exp_tang or
+// log_tang, with every thread of the block).
 __device__ __forceinline__ void exp2_table_init() {
   if (threadIdx.x < 64) {
     s_exp2_hi[threadIdx.x] = kExp2Hi[threadIdx.x];
     s_exp2_lo[threadIdx.x] = kExp2Lo[threadIdx.x];
   }
+  for (int j = threadIdx.x; j < 128; j += blockDim.x) {
+    s_log_inv[j] = kLogInv[j];
+    s_log_hi[j] = kLogHi[j];
+    s_log_lo[j] = kLogLo[j];
+  }
   __syncthreads();
+}
+
+__device__ __forceinline__ double log_tang(double x) {
+  constexpr double kLn2Hi = 0x1.62e42fefa3800p-1, kLn2Lo = 0x1.ef35793c76730p-45;
+  const int hi = __double2hiint(x);
+  if (hi < 0x00100000 || hi >= 0x7ff00000) return log(x);   // not a positive normal number
+  const int lo = __double2loint(x);
+  const double e = (double)((hi >> 20) - 1023);
+  const int j = (hi >> 13) & 127;
+  const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
+  const double r = fma(m, s_log_inv[j], -1.0);
+  double q = fma(r, -1.0 / 8.0, 1.0 / 7.0);
+  q = fma(r, q, -1.0 / 6.0);
+  q = fma(r, q, 1.0 / 5.0);
+  q = fma(r, q, -1.0 / 4.0);
+  q = fma(r, q, 1.0 / 3.0);
+  q = fma(r, q, -0.5);
+  const double small = fma(r * r, q, r) + fma(e, kLn2Lo, s_log_lo[j]);
+  return fma(e, kLn2Hi, s_log_hi[j]) + small;
 }
 
 __device__ __forceinline__ double exp_tang(double x) {
@@ -138,7 +319,7 @@ __device__ __forceinline__ double exp_tang(double x) {
 
 __device__ __forceinline__ double mexp(double x) { return exp_tang(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
-__device__ __forceinline__ double mlog(double x) { return log(x); }
+__device__ __forceinline__ double mlog(double x) { return log_tang(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
 __device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
@@ -280,11 +461,18 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   // directly over one common denominator (one division where tau is a sum of quotients, none
   // where it is a product of them); divisions by constants are multiplications by reciprocals.
   {
+    // exponentials shared by several gates (slopes 1/5, -1/10, 1/10 at V + 30, -1/6, 1/7, -1/20)
+    const T x02 = mexp(T(0.2) * V);
+    const T xm01 = mexp(T(-0.1) * V);
+    const T x30 = mexp((V + T(30)) * T(0.1));
+    const T xm16 = mexp(V * T(-1.0 / 6.0));
+    const T x17 = mexp(V * T(1.0 / 7.0));
+    const T xm005 = mexp(T(-0.05) * V);
     const T e1 = mexp((T(-56.86) - V) * T(1.0 / 9.03));
     const T minf = T(1) / ((T(1) + e1) * (T(1) + e1));
     // tau_m = alpha_m beta_m, alpha_m = 1/(1+ea), beta_m = 0.1/(1+eb) + 0.1/(1+ec)
     const T ea = T(1) + mexp((T(-60) - V) * T(0.2));
-    const T eb = T(1) + mexp((V + T(35)) * T(0.2));
+    const T eb = T(1) + x02 * T(kE7);
     const T ec = T(1) + mexp((V - T(50)) * T(1.0 / 200.0));
     un[9] = rl_rate(u[9], minf, ea * eb * ec / (T(0.1) * (eb + ec)), dt);
     const T e2 = mexp((V + T(71.55)) * T(1.0 / 7.43));
@@ -300,39 +488,39 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
            (ja * jb);
     } else {
       rh = T(0.77 / 0.13) / (T(1) + mexp((V + T(10.66)) * T(-1.0 / 11.1)));
-      rj = T(0.6) * mexp(T(0.057) * V) / (T(1) + mexp(T(-0.1) * (V + T(32))));
+      rj = T(0.6) * mexp(T(0.057) * V) / (T(1) + xm01 * T(kEm3p2));
     }
     un[10] = rl_rate(u[10], hinf, rh, dt);
     un[11] = rl_rate(u[11], hinf, rj, dt);
     // tau_xr1 = 450/(1+e) * 6/(1+e'):  1/tau = (1+e)(1+e')/2700
     const T xr1inf = T(1) / (T(1) + mexp((T(-26) - V) * T(1.0 / 7.0)));
     un[6] = rl_rate(u[6], xr1inf,
-                    (T(1) + mexp((T(-45) - V) * T(0.1))) * (T(1) + mexp((V + T(30)) * T(1.0 / 11.5))) *
+                    (T(1) + xm01 * T(kEm4p5)) * (T(1) + mexp((V + T(30)) * T(1.0 / 11.5))) *
                         T(1.0 / 2700.0),
                     dt);
     // tau_xr2 = 3/(1+e) * 1.12/(1+e'):  1/tau = (1+e)(1+e')/3.36
     const T xr2inf = T(1) / (T(1) + mexp((V + T(88)) * T(1.0 / 24.0)));
     un[7] = rl_rate(u[7], xr2inf,
-                    (T(1) + mexp((T(-60) - V) * T(0.05))) * (T(1) + mexp((V - T(60)) * T(0.05))) *
+                    (T(1) + xm005 * T(kEm3)) * (T(1) + mexp((V - T(60)) * T(0.05))) *
                         T(1.0 / 3.36),
                     dt);
     // tau_xs = 1400/(sqrt(1+e)(1+e')) + 80
     const T xsinf = T(1) / (T(1) + mexp((T(-5) - V) * T(1.0 / 14.0)));
-    const T sx = msqrt(T(1) + mexp((T(5) - V) * T(1.0 / 6.0))) * (T(1) + mexp((V - T(35)) * T(1.0 / 15.0)));
+    const T sx = msqrt(T(1) + xm16 * T(kE5o6)) * (T(1) + mexp((V - T(35)) * T(1.0 / 15.0)));
     un[8] = rl_rate(u[8], xsinf, sx / (T(1400) + T(80) * sx), dt);
-    const T rinf = T(1) / (T(1) + mexp((T(20) - V) * T(1.0 / 6.0)));
+    const T rinf = T(1) / (T(1) + xm16 * T(kE20o6));
     const T vr = V + T(40);
     un[17] = rl_rate(u[17], rinf, T(1) / (T(9.5) * mexp(vr * vr * T(-1.0 / 1800.0)) + T(0.8)), dt);
     T sinf, rs;
     if (cell == 0) {
-      sinf = T(1) / (T(1) + mexp((V + T(28)) * T(0.2)));
+      sinf = T(1) / (T(1) + x02 * T(kE5p6));
       const T vs = V + T(67);
       rs = T(1) / (T(1000) * mexp(vs * vs * T(-1.0 / 1000.0)) + T(8));
     } else {
-      sinf = T(1) / (T(1) + mexp((V + T(20)) * T(0.2)));
+      sinf = T(1) / (T(1) + x02 * T(kE4));
       const T vs = V + T(45);
       // tau_s = 85 e + 5/(1+e') + 3
-      const T es = T(1) + mexp((V - T(20)) * T(0.2));
+      const T es = T(1) + x02 * T(kEm4);
       rs = es / ((T(85) * mexp(vs * vs * T(-1.0 / 320.0)) + T(3)) * es + T(5));
     }
     un[16] = rl_rate(u[16], sinf, rs, dt);
@@ -340,25 +528,25 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     const T dinf = T(1) / (T(1) + mexp((T(-8) - V) * T(1.0 / 7.5)));
     {
       const T da = T(1) + mexp((T(-35) - V) * T(1.0 / 13.0));
-      const T db = T(1) + mexp((V + T(5)) * T(0.2));
-      const T dc = T(1) + mexp((T(50) - V) * T(0.05));
+      const T db = T(1) + x02 * T(kE1);
+      const T dc = T(1) + xm005 * T(kE2p5);
       un[12] = rl_rate(u[12], dinf, da * db * dc / ((T(1.4) + T(0.25) * da) * T(1.4) * dc + da * db), dt);
     }
     // tau_f = 1102.5 e + 200/(1+ea) + 180/(1+eb) + 20
-    const T finf = T(1) / (T(1) + mexp((V + T(20)) * T(1.0 / 7.0)));
+    const T finf = T(1) / (T(1) + x17 * T(kE20o7));
     const T vf27 = V + T(27);
     {
-      const T fa = T(1) + mexp((T(13) - V) * T(0.1));
-      const T fb = T(1) + mexp((V + T(30)) * T(0.1));
+      const T fa = T(1) + xm01 * T(kE1p3);
+      const T fb = T(1) + x30;
       const T num = (T(1102.5) * mexp(vf27 * vf27 * T(-1.0 / 225.0)) + T(20)) * fa * fb + T(200) * fb + T(180) * fa;
       un[13] = rl_rate(u[13], finf, fa * fb / num, dt);
     }
     // tau_f2 = 600 e + 31/(1+ea) + 16/(1+eb)
-    const T f2inf = T(0.67) / (T(1) + mexp((V + T(35)) * T(1.0 / 7.0))) + T(0.33);
+    const T f2inf = T(0.67) / (T(1) + x17 * T(kE5)) + T(0.33);
     const T vf25 = V + T(25);
     {
-      const T ga = T(1) + mexp((T(25) - V) * T(0.1));
-      const T gb = T(1) + mexp((V + T(30)) * T(0.1));
+      const T ga = T(1) + xm01 * T(kE2p5);
+      const T gb = T(1) + x30;
       const T num = T(600) * mexp(vf25 * vf25 * T(-1.0 / 170.0)) * ga * gb + T(31) * gb + T(16) * ga;
       un[14] = rl_rate(u[14], f2inf, ga * gb / num, dt);
     }
@@ -421,14 +609,15 @@ __global__ void __launch_bounds__(256) tp06_window_kernel(int64_t n, const float
   out[kTP06States * n + i] = float(V);
 }
 
-// Self-test of exp_tang against the library exp on device (diagnostics of the ABI).
+// Self-test of exp_tang (fn 0) or log_tang (fn 1) against the library function on device
+// (diagnostics of the ABI).
 static __global__ void __launch_bounds__(256) exp_selftest_kernel(int64_t n, const double* x, double* y_fast,
-                                                           double* y_ref) {
+                                                           double* y_ref, int fn) {
   exp2_table_init();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  y_fast[i] = exp_tang(x[i]);
-  y_ref[i] = exp(x[i]);
+  y_fast[i] = fn ? log_tang(x[i]) : exp_tang(x[i]);
+  y_ref[i] = fn ? log(x[i]) : exp(x[i]);
 }
 
 }  // namespace tc

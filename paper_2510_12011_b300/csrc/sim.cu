@@ -1515,21 +1515,29 @@ tc_status tc_reset_profile(tc_sim* s) {
   return TC_OK;
 }
 
-tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_t n) {
+static tc_status selftest_math(const double* x, double* y_fast, double* y_ref, int64_t n, int fn) {
   clear_error();
   if (!x || !y_fast || !y_ref || n < 1) return fail(TC_ERR_ARG, "bad self-test arguments");
   double* d = nullptr;
   CUDA_TRY(cudaMalloc(&d, 3 * n * sizeof(double)));
   cudaError_t e = cudaMemcpy(d, x, n * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    exp_selftest_kernel<<<(int)((n + 255) / 256), 256>>>(n, d, d + n, d + 2 * n);
+    exp_selftest_kernel<<<(int)((n + 255) / 256), 256>>>(n, d, d + n, d + 2 * n, fn);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(y_fast, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(y_ref, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(d);
-  if (e != cudaSuccess) return cuda_fail(e, "tc_selftest_exp");
+  if (e != cudaSuccess) return cuda_fail(e, "math self-test");
   return TC_OK;
+}
+
+tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_t n) {
+  return selftest_math(x, y_fast, y_ref, n, 0);
+}
+
+tc_status tc_selftest_log(const double* x, double* y_fast, double* y_ref, int64_t n) {
+  return selftest_math(x, y_fast, y_ref, n, 1);
 }
 
 const char* tc_version(void) { return "tc_b300 0.4 (sm_103a)"; }

@@ -90,6 +90,7 @@ _SIGS = {
     "tc_reset_profile": [_P],
     "tc_set_wait_limit": [_P, C.c_int64],
     "tc_selftest_exp": [_D, _D, _D, C.c_int64],
+    "tc_selftest_log": [_D, _D, _D, C.c_int64],
     "tc_mlp_create": [C.c_uint64, C.POINTER(_P)],
     "tc_mlp_n_params": [_P, _I64],
     "tc_mlp_get_params": [_P, C.POINTER(C.c_float), C.c_int64],
@@ -482,6 +483,15 @@ def monodomain_conductivity(il, it, el, et):
     sl, st = np.empty_like(il), np.empty_like(il)
     _check(lib().tc_monodomain_conductivity(_d(il), _d(it), _d(el), _d(et), il.size, _d(sl), _d(st)))
     return sl, st
+
+
+def selftest_log(x):
+    """(device log used by the ionic kernels, CUDA library log) at x."""
+    x = _f64(x)
+    a = np.empty_like(x)
+    b = np.empty_like(x)
+    _check(lib().tc_selftest_log(_d(x), _d(a), _d(b), x.size))
+    return a, b
 
 
 def selftest_exp(x):

@@ -177,3 +177,24 @@ def test_monodomain_conductivity_from_bidomain_pairs():
     assert np.allclose(got[0], ref[0], rtol=1e-15) and np.allclose(got[1], ref[1], rtol=1e-15)
     with pytest.raises(tc.TcError):
         tc.monodomain_conductivity([0.1], [0.0], [0.1], [0.1])
+
+
+def test_math_tables_match_their_definition():
+    """The exp and log tables of the FP64 ionic kernel are the values math_tables.py derives
+    from their definitions (2^(j/64); fl(1/(1 + j/128)) and -ln of it) with mpmath."""
+    import contextlib
+    import io
+    import re
+    import runpy
+    from pathlib import Path
+    csrc = Path(__file__).resolve().parents[1] / "paper_2510_12011_b300" / "csrc"
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        runpy.run_path(str(csrc / "math_tables.py"), run_name="__main__")
+    gen, src = buf.getvalue(), (csrc / "ionic_tp06.cuh").read_text()
+
+    def vals(text, key):
+        i = text.index("{", text.index(key))
+        return [float.fromhex(v) for v in re.findall(r"-?0x[0-9a-fA-F.]+p[+-]?\d+", text[i:text.index("}", i)])]
+    for name, n in (("kExp2Hi", 64), ("kExp2Lo", 64), ("kLogInv", 128), ("kLogHi", 128), ("kLogLo", 128)):
+        assert vals(src, f"double {name}[{n}] =") == vals(gen, f"{name} ="), name

@@ -142,3 +142,31 @@ def test_device_exp_accuracy():
         err_lib = max(err_lib, float(abs(mpmath.mpf(float(ref[i])) - exact)) / ulp)
     assert err_fast <= 1.0, (err_fast, err_lib)
     assert np.isnan(tc.selftest_exp(np.array([np.nan]))[0][0])
+
+
+def test_device_log_accuracy():
+    # the table-driven FP64 log of the ionic kernels: within 1 ulp of the exact value (mpmath,
+    # 40 digits) on concentrations' ranges and well beyond, within 2 ulp of the CUDA library log;
+    # just below 1 (where e ln2 and the table value cancel) the bound is absolute (2^-53);
+    # zero, negatives, subnormals, inf and NaN follow the library
+    import mpmath
+    rng = np.random.default_rng(1)
+    x = np.concatenate([10.0 ** rng.uniform(-8.0, 4.0, 400000), rng.uniform(1e-5, 2e-3, 50000),
+                        rng.uniform(100.0, 160.0, 50000), 10.0 ** rng.uniform(-300, 300, 20000),
+                        np.nextafter(1.0, 0.0) - np.arange(200) * 1e-5, [1.0, 2.0, 0.5, np.e]])
+    fast, ref = tc.selftest_log(x)
+    tol = 2.0 * np.spacing(np.abs(ref)) + 2.0 ** -53
+    assert np.all(np.abs(fast - ref) <= tol)
+    mpmath.mp.dps = 40
+    idx = rng.choice(x.size, 6000, replace=False)
+    worst = 0.0
+    for i in idx:
+        exact = mpmath.log(mpmath.mpf(float(x[i])))
+        ulp = max(np.spacing(abs(float(exact))), 2.0 ** -53) if exact != 0 else 2.0 ** -53
+        worst = max(worst, float(abs(mpmath.mpf(float(fast[i])) - exact)) / ulp)
+    assert worst <= 1.0, worst
+    special = np.array([0.0, -1.0, np.inf, np.nan, 1e-310])
+    f, r = tc.selftest_log(special)
+    assert np.array_equal(np.isnan(f), np.isnan(r))
+    ok = ~np.isnan(r)
+    assert np.array_equal(f[ok], r[ok])
