@@ -37,8 +37,8 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 # FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
 # profiles/ (FP64 pipe utilisation x elapsed cycles x 296 thread instructions per clock / nodes);
 # used to turn the live launch time into an achieved FP64 instruction rate.
-TP06_FP64_INSTR_PER_NODE = 1761.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.91e6   # dram read + write of the same capture
+TP06_FP64_INSTR_PER_NODE = 1517.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.67e6   # dram read + write of the same capture
 
 
 def parse():
