@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-prior-art", action="store_true",
+                    help="skip the PyTorch version of the paper's own design (context line)")
     ap.add_argument("--no-surrogate-apd", action="store_true",
                     help="skip the surrogate's 400 ms APD90 check on the unseen slab")
     ap.add_argument("--batched-steps", type=int, default=600)
@@ -308,6 +310,98 @@ def surrogate_form(w, K, W, ms64, act64, stream, torch, apd=True, apd64=None):
             "apd90": apd90, "apd90_this_run": apd_run}
 
 
+def prior_art_torch(steps, warmup, stream, torch):
+    """The paper's own GPU design on the same B300, as prior-art context (not a baseline this
+    library is checked against): PyTorch FP64 sparse CSR products and elementwise ops, the
+    Mitchell-Schaeffer update as torch expressions, Algorithm 1 driven from the host with its
+    stopping test read back every iteration.  Workload: the 504,711-node slab with the
+    Mitchell-Schaeffer model (the step is then SpMV/PCG work), timed beside this library's FP64
+    step on the same workload and steps.  Matrices come from the library's host assembly."""
+    import warnings
+    from paper_2510_12011_b300 import tc
+    warnings.filterwarnings("ignore", message="Sparse")
+    w = I.slab_large("ms")
+    n = w.mesh.n_nodes
+    mesh = tc.Mesh.from_inputs(w.mesh)
+    rp, col, mv, kv = mesh.matrices(w.sigma_l, w.sigma_t)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    crow = torch.from_numpy(rp).to(dev)
+    cidx = torch.from_numpy(col.astype(np.int64)).to(dev)
+    Mt = torch.sparse_csr_tensor(crow, cidx, torch.from_numpy(mv).to(dev), size=(n, n))
+    Kt = torch.sparse_csr_tensor(crow, cidx, torch.from_numpy(kv).to(dev), size=(n, n))
+    av = w.chi * w.cm * mv + w.theta * w.dt * kv
+    At = torch.sparse_csr_tensor(crow, cidx, torch.from_numpy(av).to(dev), size=(n, n))
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    diag = torch.from_numpy(av[rows == col]).to(dev)
+    p_ = w.ms
+    span = p_.v_max - p_.v_min
+    stim = torch.zeros(n, dtype=torch.float64, device=dev)
+    st = w.stimuli[0]
+    stim[torch.from_numpy(np.asarray(st.nodes, dtype=np.int64)).to(dev)] = st.intensity
+    k0, nk = int(round(st.start / w.dt)), int(round(st.duration / w.dt))
+
+    def run(nsteps):
+        V = torch.full((n,), p_.v_min, dtype=torch.float64, device=dev)
+        Vp = V.clone()
+        h = torch.ones(n, dtype=torch.float64, device=dev)
+        iters = 0
+        for k in range(nsteps):
+            v = (V - p_.v_min) / span
+            opening = v < p_.v_gate
+            hinf = opening.to(torch.float64)
+            tau = torch.where(opening, torch.full_like(v, p_.tau_open), torch.full_like(v, p_.tau_close))
+            h = hinf + (h - hinf) * torch.exp(-w.dt / tau)
+            iion = -w.cm * span * (h * v * v * (1 - v) / p_.tau_in - v / p_.tau_out)
+            ist = stim if k0 <= k < k0 + nk else torch.zeros_like(stim)
+            b = w.chi * (Mt @ (w.cm * V - w.dt * iion + w.dt * ist)) - (1 - w.theta) * w.dt * (Kt @ V)
+            x = 2 * V - Vp
+            r = b - At @ x
+            z = r / diag
+            pvec = z.clone()
+            rho = torch.dot(r, z)
+            z0 = torch.linalg.vector_norm(z).item()
+            if z0 > w.atol:
+                for it in range(w.max_iter):
+                    q = At @ pvec
+                    alpha = rho / torch.dot(pvec, q)
+                    x = x + alpha * pvec
+                    r = r - alpha * q
+                    z = r / diag
+                    zn = torch.linalg.vector_norm(z).item()
+                    iters += 1
+                    if zn < w.atol or zn / z0 < w.rtol:
+                        break
+                    rho_n = torch.dot(r, z)
+                    pvec = z + (rho_n / rho) * pvec
+                    rho = rho_n
+            Vp, V = V, x
+        return iters
+
+    run(warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_t = run(steps)
+    torch.cuda.synchronize()
+    t_torch = time.perf_counter() - t0
+    sim = tc.from_workload(w, stream=stream.cuda_stream)
+    sim.step(warmup)
+    tc.set_model(sim, w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_ours = sim.step(steps)
+    torch.cuda.synchronize()
+    t_ours = time.perf_counter() - t0
+    sim.close()
+    return {"workload": w.name, "n_nodes": n, "steps": steps, "dtype": "f64",
+            "what": "PyTorch sparse CSR + elementwise ops, Algorithm 1 with a host-read stopping test "
+                    "per iteration (the paper's design), same GPU",
+            "torch": {"value": n * steps / t_torch, "unit": "node-steps/s", "ms_per_step": 1e3 * t_torch / steps,
+                      "mean_cg_iterations": it_t / steps},
+            "this_library": {"value": n * steps / t_ours, "unit": "node-steps/s", "ms_per_step": 1e3 * t_ours / steps,
+                             "mean_cg_iterations": st_ours["cg_iterations"] / steps},
+            "speedup": t_torch / t_ours}
+
+
 def batched_form(steps, stream, torch):
     """The batched form: 64 uneven slabs (5.3 M nodes) as independent problems in one
     simulation, FP32, launch shape by the autotuner, step loop by CUDA-graph replay (also timed
@@ -491,6 +585,10 @@ def run_ours(args):
     if not args.no_surrogate and w.model == "tp06":
         sur = surrogate_form(w, K, W, ms, act64, stream, torch, apd=not args.no_surrogate_apd, apd64=apd64)
 
+    prior = None
+    if not args.no_prior_art and world == 1:
+        prior = prior_art_torch(300, 5, stream, torch)
+
     batched = None
     if not args.no_batched:
         batched = batched_form(min(args.batched_steps, max(K, 30)), stream, torch)
@@ -524,6 +622,7 @@ def run_ours(args):
         "fp32_form": fp32,
         "surrogate_form": sur,
         "batched_form": batched,
+        "prior_art_torch": prior,
         "e2e": e2e,
         "gpu_launches": prof["ionic_launches"] + prof["pcg_launches"],
         "clocks": clk,
