@@ -39,6 +39,10 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 # used to turn the live launch time into an achieved FP64 instruction rate.
 TP06_FP64_INSTR_PER_NODE = 1517.0
 TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.67e6   # dram read + write of the same capture
+# dram read + write of one pcg_step_kernel<1024, double> launch on the large slab (ncu capture in
+# profiles/, 8.47 CG iterations in that launch)
+PCG_FP64_DRAM_BYTES_PER_LAUNCH = 1.305e9
+PCG_FP64_CAPTURE_ITERATIONS = 8.47
 
 
 def parse():
@@ -169,8 +173,16 @@ def cpu_baseline(w, seconds):
             sim.step()
         el = time.perf_counter() - t0
         steps, total = (extra, el) if extra > 0 else (1, first)
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
     return {"value": w.mesh.n_nodes * steps / total, "unit": "node-steps/s", "cores": 1,
-            "kind": "oracle",
+            "host_cores": os.cpu_count(), "cpu_model": model, "kind": "oracle",
             "sample": f"{steps} time steps (steps 2..{steps + 1}) of {w.name}, "
                       f"{w.mesh.n_nodes} nodes, numpy/scipy FP64, 1 thread"}
 
@@ -493,8 +505,13 @@ def run_ours(args):
     iters = prof["pcg_iterations"] / max(prof["pcg_launches"], 1)
     bytes_launch = pcg_launch_bytes(n, size["nnz"], (n + 31) // 32, iters)
     pcg_gbs = bytes_launch / (pcg_launch_ms * 1e-3) / 1e9
+    cap = w.name == "slab40x16x6_h0.2_tp06"
     roof_pcg = {"kernel": "pcg_step_kernel", "bound": "hbm", "achieved": pcg_gbs, "peak": peak,
-                "unit": "GB/s", "frac": pcg_gbs / peak, "traffic": None,
+                "unit": "GB/s", "frac": pcg_gbs / peak,
+                "traffic": PCG_FP64_DRAM_BYTES_PER_LAUNCH if cap else None,
+                "traffic_note": (f"ncu dram bytes of one launch with {PCG_FP64_CAPTURE_ITERATIONS} CG iterations "
+                                 f"(this run averages {iters:.2f}); the 4 MB node vectors partly stay in the "
+                                 "132.6 MB L2, the matrix streams from DRAM") if cap else None,
                 "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": bytes_launch,
                 "avg_launch_ms": pcg_launch_ms}
     if prof["ionic_ms"] > prof["pcg_ms"] and w.model == "tp06" and TP06_FP64_INSTR_PER_NODE:
@@ -549,7 +566,7 @@ def run_ours(args):
         host[tc.TC_FIELD_V_PREV][:] = host[tc.TC_FIELD_V]
         for f in fields:
             if f != tc.TC_FIELD_V_PREV:
-                host[f][:] = sim.read(f)
+                sim.read(f, out=host[f])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()

@@ -102,6 +102,10 @@ struct tc_sim {
   std::vector<Dev> allocs;
   double* pinned = nullptr;   // n_int doubles of page-locked staging for host reads/writes
   void* pinned_t = nullptr;   // n_int elements of the device type, page-locked
+  // device-side reordering of host fields: perm (internal -> caller, -1 on padding rows), inv
+  // (caller -> internal) and an n-double staging vector in caller order
+  int32_t *perm_dev = nullptr, *inv_dev = nullptr;
+  double* stage_dev = nullptr;
   // learned ionic surrogate (not owned)
   tc_mlp* sur = nullptr;
   int sur_window = 10;
@@ -170,6 +174,52 @@ void drop_graphs(tc_sim* s) {
 }
 
 int64_t round_half_even(double x) { return (int64_t)std::nearbyint(x); }
+
+// Caller-order doubles (staged on the device) -> internal rows of a device field of type T; padding
+// rows keep their values.
+template <typename T>
+__global__ void from_caller_kernel(int64_t n_int, const int32_t* perm, const double* stage, T* dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_int && perm[i] >= 0) dst[i] = T(stage[perm[i]]);
+}
+
+// Internal rows of a device field of type T -> caller-order doubles in the staging vector.
+template <typename T>
+__global__ void to_caller_kernel(int64_t n, const int32_t* inv, const T* src, double* stage) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) stage[j] = double(src[inv[j]]);
+}
+
+// Host array in caller order (n doubles) -> device field (element type double when is_double,
+// else the simulation's type): one copy into the staging vector, then a reordering kernel.
+tc_status write_caller_field(tc_sim* s, void* dst, bool is_double, const double* host) {
+  CUDA_TRY(cudaMemcpyAsync(s->stage_dev, host, s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  const unsigned blocks = (unsigned)((s->n_int + 255) / 256);
+  if (is_double || s->precision == TC_FP64)
+    from_caller_kernel<double><<<blocks, 256, 0, s->stream>>>(s->n_int, s->perm_dev, s->stage_dev,
+                                                              static_cast<double*>(dst));
+  else
+    from_caller_kernel<float><<<blocks, 256, 0, s->stream>>>(s->n_int, s->perm_dev, s->stage_dev,
+                                                             static_cast<float*>(dst));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TC_OK;
+}
+
+// Device field -> host array in caller order (n doubles).
+tc_status read_caller_field(const tc_sim* s, const void* src, bool is_double, double* host) {
+  const unsigned blocks = (unsigned)((s->n + 255) / 256);
+  if (is_double || s->precision == TC_FP64)
+    to_caller_kernel<double><<<blocks, 256, 0, s->stream>>>(s->n, s->inv_dev, static_cast<const double*>(src),
+                                                            s->stage_dev);
+  else
+    to_caller_kernel<float><<<blocks, 256, 0, s->stream>>>(s->n, s->inv_dev, static_cast<const float*>(src),
+                                                           s->stage_dev);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(host, s->stage_dev, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return TC_OK;
+}
 
 // Host doubles in internal order (n_int entries) -> device array of the simulation's type.
 // With real_only, only the real rows of every component are written (dummy rows keep theirs).
@@ -876,6 +926,13 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   ce = cudaMallocHost(&s->pinned, n * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMallocHost(&s->pinned_t, n * sizeof(double));
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMallocHost"));
+  st = dalloc(s, &s->perm_dev, n);
+  if (st == TC_OK) st = dalloc(s, &s->inv_dev, s->n);
+  if (st == TC_OK) st = dalloc(s, &s->stage_dev, s->n);
+  if (st != TC_OK) return bail(st);
+  ce = cudaMemcpy(s->perm_dev, s->perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(s->inv_dev, s->inv.data(), s->n * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpy"));
   st = set_partition(s);
   if (st != TC_OK) return bail(st);
   st = upload_stimuli(s);
@@ -1276,9 +1333,7 @@ tc_status tc_read_state(const tc_sim* s, int32_t field, double* dst, int64_t n) 
   const void* src = field_ptr(s, field);
   if (!src) return fail(TC_ERR_ARG, "unknown field " + std::to_string(field));
   CUDA_TRY(cudaSetDevice(s->device));
-  TRY(download_vec(s, src, s->pinned));
-  to_caller(s, s->pinned, dst);
-  return TC_OK;
+  return read_caller_field(s, src, false, dst);
 }
 
 tc_status tc_write_state(tc_sim* s, int32_t field, const double* src, int64_t n) {
@@ -1291,9 +1346,8 @@ tc_status tc_write_state(tc_sim* s, int32_t field, const double* src, int64_t n)
   CUDA_TRY(cudaSetDevice(s->device));
   CUDA_TRY(cudaStreamSynchronize(s->stream));   // the staging buffer may still feed a copy
   // nodes the learned surrogate holds for the current window restart on the exact model
-  if (s->sur_flag) CUDA_TRY(cudaMemset(s->sur_flag, 0, s->n_int));
-  to_internal(s, src, s->pinned, 0.0);
-  return upload_vec(s, dst, s->pinned, true);
+  if (s->sur_flag) CUDA_TRY(cudaMemsetAsync(s->sur_flag, 0, s->n_int, s->stream));
+  return write_caller_field(s, dst, false, src);
 }
 
 tc_status tc_activation_times(const tc_sim* s, double v_threshold, double* dst, int64_t n) {
@@ -1303,11 +1357,7 @@ tc_status tc_activation_times(const tc_sim* s, double v_threshold, double* dst, 
   if (v_threshold != s->thr)
     return fail(TC_ERR_STATE, "activation times were captured for another threshold");
   CUDA_TRY(cudaSetDevice(s->device));
-  CUDA_TRY(cudaMemcpyAsync(s->pinned, s->act, s->n_int * sizeof(double), cudaMemcpyDeviceToHost,
-                           s->stream));
-  CUDA_TRY(cudaStreamSynchronize(s->stream));
-  to_caller(s, s->pinned, dst);
-  return TC_OK;
+  return read_caller_field(s, s->act, true, dst);
 }
 
 static tc_status read_double_field(const tc_sim* s, const double* src, double* dst, int64_t n) {
@@ -1315,11 +1365,7 @@ static tc_status read_double_field(const tc_sim* s, const double* src, double* d
   if (n != s->n) return fail(TC_ERR_ARG, "n must equal the node count");
   if (s->model < 0) return fail(TC_ERR_STATE, "no ionic model set");
   CUDA_TRY(cudaSetDevice(s->device));
-  CUDA_TRY(cudaMemcpyAsync(s->pinned, src, s->n_int * sizeof(double), cudaMemcpyDeviceToHost,
-                           s->stream));
-  CUDA_TRY(cudaStreamSynchronize(s->stream));
-  to_caller(s, s->pinned, dst);
-  return TC_OK;
+  return read_caller_field(s, src, true, dst);
 }
 
 tc_status tc_set_repolarisation_threshold(tc_sim* s, double v) {

@@ -264,8 +264,13 @@ class Simulation:
         _check(lib().tc_step(self._h, n_steps, C.byref(st)))
         return st.as_dict()
 
-    def read(self, field=TC_FIELD_V):
-        out = np.empty(self.n_nodes)
+    def read(self, field=TC_FIELD_V, out=None):
+        """Field in caller node order; with `out` (a C-contiguous float64 array of n entries,
+        ideally page-locked) the values land there directly."""
+        if out is None:
+            out = np.empty(self.n_nodes)
+        elif out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size != self.n_nodes:
+            raise TcError(TC_ERR_ARG, "out must be a C-contiguous float64 array of n_nodes entries")
         _check(lib().tc_read_state(self._h, field, _d(out), self.n_nodes))
         return out
 
