@@ -342,7 +342,7 @@ __device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
   using namespace tp06;
   Tp06VFactors<T> f;
   const T vm = V - T(15);
-  const T x = T(2) * vm / T(kRTF);
+  const T x = vm * T(2.0 / kRTF);
   if (x != T(0)) {
     const T c = T(4) * vm * T(kF / kRTF) / mexpm1(x);
     f.ghk_cass = c * T(0.25) * mexp(x);
@@ -351,15 +351,16 @@ __device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
     f.ghk_cass = T(2 * kF * 0.25);
     f.ghk = T(-2 * kF * kCao);
   }
-  const T vf = V / T(kRTF);
+  const T vf = V * T(1.0 / kRTF);
   f.nak = T(kPNaK * kKo / (kKo + kKmK)) /
           (T(1) + T(0.1245) * mexp(T(-0.1) * vf) + T(0.0353) * mexp(-vf));
   const T eg = mexp(T(kGam) * vf), eg1 = mexp(T(kGam - 1.0) * vf);
   const T den = T((kKmNai * kKmNai * kKmNai + kNao * kNao * kNao) * (kKmCa + kCao)) *
                 (T(1) + T(kKsat) * eg1);
-  f.naca_a = T(kKNaCa) * eg / den;
-  f.naca_b = T(kKNaCa * kAlphaNaCa * kNao * kNao * kNao) * eg1 / den;
-  f.ipk = T(1) / (T(1) + mexp((T(25) - V) / T(5.98)));
+  const T rden = T(1) / den;
+  f.naca_a = T(kKNaCa) * eg * rden;
+  f.naca_b = T(kKNaCa * kAlphaNaCa * kNao * kNao * kNao) * eg1 * rden;
+  f.ipk = T(1) / (T(1) + mexp((T(25) - V) * T(1.0 / 5.98)));
   return f;
 }
 

@@ -222,6 +222,25 @@ def test_large_slab_full_size_parity():
     assert np.abs(g.read(tc.TC_FIELD_STATE) - o.state[0]).max() <= 1e-12
 
 
+@pytest.mark.slow
+def test_large_slab_tp06_full_size_parity():
+    """The headline workload at full size (504,711 nodes, TP06 epicardial, FP64) in the bench's
+    launch configuration, with the solver in parity mode: three steps (the stimulus is on), V and
+    all 18 states against the oracle."""
+    w = I.slab_large("tp06")
+    w.rtol, w.atol, w.max_iter = 1e-10, 0.0, 1000
+    g = _sim(w)
+    o = Monodomain(w)
+    for _ in range(3):
+        o.step()
+    g.step(3)
+    assert np.abs(g.read() - o.V).max() <= V_TOL
+    for j in range(18):
+        ref = o.state[j]
+        got = g.read(tc.TC_FIELD_STATE + j)
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-15), j
+
+
 @pytest.mark.gpu
 @pytest.mark.slow
 def test_nversion_activation_converges_with_refinement():
