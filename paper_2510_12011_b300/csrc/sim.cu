@@ -1501,8 +1501,14 @@ tc_status tc_apply_operator_dev(tc_sim* s, int32_t op, const void* x_dev, void* 
   if (((uintptr_t)x_dev | (uintptr_t)y_dev) & 15) return fail(TC_ERR_ARG, "x/y must be 16-byte aligned");
   CUDA_TRY(cudaSetDevice(s->device));
   const int threads = 256;
+  // the kernel strides over slices: one wave of resident blocks, no partial second wave
+  int occ = 1;
+  if (s->precision == TC_FP64)
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmv_sell_kernel<double>, threads, 0));
+  else
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmv_sell_kernel<float>, threads, 0));
   const int64_t blocks = std::min<int64_t>((s->nslices * 32 + threads - 1) / threads,
-                                           (int64_t)s->num_sms * 8);
+                                           (int64_t)s->num_sms * std::max(occ, 1));
   const int nb = (int)std::max<int64_t>(blocks, 1);
   if (s->precision == TC_FP64)
     spmv_sell_kernel<double><<<nb, threads, 0, s->stream>>>(
@@ -1666,8 +1672,10 @@ extern "C" tc_status tc_apply_operator_static(tc_sim* s, int32_t op, const doubl
   to_internal(s, x, h, 0.0);
   CUDA_TRY(cudaMemcpyAsync(scratch, h, s->n_int * sizeof(double), cudaMemcpyHostToDevice, s->stream));
   const int threads = 256;
+  int occ = 1;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmv_sell_static_kernel, threads, 0));
   const int64_t blocks = std::min<int64_t>((s->nslices * 32 + threads - 1) / threads,
-                                           (int64_t)s->num_sms * 8);
+                                           (int64_t)s->num_sms * std::max(occ, 1));
   spmv_sell_static_kernel<<<(int)std::max<int64_t>(blocks, 1), threads, 0, s->stream>>>(
       s->n_int, s->nslices, s->slice_ptr, s->col, val, scratch);
   CUDA_TRY(cudaGetLastError());
