@@ -225,32 +225,57 @@ __device__ __forceinline__ void grid_sum_warp0(const double* part, int stride, u
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Row products over one SELL slice, lane = row.  Four entries are fetched (indices, values,
-// gathered vector entries) before their FMAs; even and odd entries feed two FMA chains.
+// Row products over one SELL slice, lane = row.  Even entries accumulate in acc0 and odd entries
+// in acc1, each in entry order, so both loop shapes below give the same bits.  FP64: four
+// entries (indices, values, gathered vector entries) in flight before their FMAs - the product is
+// bound by B300's FP64 pipe as much as by memory.  FP32: predicated chunks of eight entries, so
+// that a 15-entry row is two rounds of (indices and values, then gathers) - the FP32 solve keeps
+// its working set in L2 and is bound by load latency.
 template <typename T>
 __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
                                      int beg, int w, const T* x) {
   T acc0 = T(0), acc1 = T(0);
-  int j = 0;
-  for (; j + 4 <= w; j += 4) {
-    const int e = beg + 32 * j;
-    const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32), c2 = __ldg(col + e + 64),
-              c3 = __ldg(col + e + 96);
-    const T v0 = __ldg(val + e), v1 = __ldg(val + e + 32), v2 = __ldg(val + e + 64),
-            v3 = __ldg(val + e + 96);
-    const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
-    acc0 = fmaT(v0, x0, acc0);
-    acc1 = fmaT(v1, x1, acc1);
-    acc0 = fmaT(v2, x2, acc0);
-    acc1 = fmaT(v3, x3, acc1);
-  }
-  for (; j < w; ++j) {
-    const int e = beg + 32 * j;
-    const T v = __ldg(val + e), xv = x[__ldg(col + e)];
-    if (j & 1)
-      acc1 = fmaT(v, xv, acc1);
-    else
-      acc0 = fmaT(v, xv, acc0);
+  if constexpr (sizeof(T) == 4) {
+    for (int j = 0; j < w; j += 8) {
+      const int e = beg + 32 * j;
+      int c[8];
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[u] = j + u < w ? __ldg(col + e + 32 * u) : 0;
+        v[u] = j + u < w ? __ldg(val + e + 32 * u) : T(0);
+      }
+      T xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = j + u < w ? x[c[u]] : T(0);
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        if (j + u < w) acc0 = fmaT(v[u], xv[u], acc0);
+        if (j + u + 1 < w) acc1 = fmaT(v[u + 1], xv[u + 1], acc1);
+      }
+    }
+  } else {
+    int j = 0;
+    for (; j + 4 <= w; j += 4) {
+      const int e = beg + 32 * j;
+      const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32), c2 = __ldg(col + e + 64),
+                c3 = __ldg(col + e + 96);
+      const T v0 = __ldg(val + e), v1 = __ldg(val + e + 32), v2 = __ldg(val + e + 64),
+              v3 = __ldg(val + e + 96);
+      const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+      acc0 = fmaT(v0, x0, acc0);
+      acc1 = fmaT(v1, x1, acc1);
+      acc0 = fmaT(v2, x2, acc0);
+      acc1 = fmaT(v3, x3, acc1);
+    }
+    for (; j < w; ++j) {
+      const int e = beg + 32 * j;
+      const T v = __ldg(val + e), xv = x[__ldg(col + e)];
+      if (j & 1)
+        acc1 = fmaT(v, xv, acc1);
+      else
+        acc0 = fmaT(v, xv, acc0);
+    }
   }
   return acc0 + acc1;
 }
