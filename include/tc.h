@@ -116,6 +116,11 @@ tc_status tc_monodomain_conductivity(const double* il, const double* it, const d
  * alpha, beta and stopping test), which is how many meshes are batched into one simulation. */
 tc_status tc_mesh_layout_size(const tc_mesh* mesh, int32_t* n_components, int64_t* n_internal);
 
+/* tc_mesh_set_sell_sigma: the SELL-C-32 row-sorting window (rows sorted by length inside windows
+ * of sell_sigma rows of the RCM order, never across components) of simulations assembled from this
+ * mesh afterwards; default 1024.  sell_sigma >= 1. */
+tc_status tc_mesh_set_sell_sigma(tc_mesh* mesh, int32_t sell_sigma);
+
 /* tc_mesh_ordering: the internal node order the device path uses (host only).
  * perm[k] = caller index of the k-th real row (n_nodes entries, dummy rows left out);
  * slice_width (if not NULL) receives n_internal/32 SELL slice widths. */

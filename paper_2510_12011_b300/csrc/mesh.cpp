@@ -439,6 +439,14 @@ tc_status tc_mesh_layout_size(const tc_mesh* mesh, int32_t* n_components, int64_
   return TC_OK;
 }
 
+tc_status tc_mesh_set_sell_sigma(tc_mesh* mesh, int32_t sell_sigma) {
+  clear_error();
+  if (!mesh) return fail(TC_ERR_ARG, "mesh must not be NULL");
+  if (sell_sigma < 1) return fail(TC_ERR_ARG, "sell_sigma must be >= 1");
+  mesh->sell_sigma = sell_sigma;
+  return TC_OK;
+}
+
 tc_status tc_mesh_ordering(const tc_mesh* mesh, int32_t sell_sigma, int32_t* perm,
                            int32_t* slice_width) {
   clear_error();

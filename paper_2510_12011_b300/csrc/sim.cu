@@ -835,7 +835,7 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   s->nnz = pat.row_ptr[mesh->n];
   s->pcg_threads = env_int("TC_PCG_THREADS", 1024) == 512 ? 512 : 1024;
   s->blocks_per_sm = std::max(1, env_int("TC_PCG_BLOCKS_PER_SM", s->pcg_threads == 1024 ? 1 : 2));
-  s->sell_sigma = std::max(1, env_int("TC_SELL_SIGMA", 1024));
+  s->sell_sigma = mesh->sell_sigma > 0 ? mesh->sell_sigma : std::max(1, env_int("TC_SELL_SIGMA", 1024));
   s->use_graphs = env_int("TC_GRAPHS", 1) != 0;
   Sell sell;
   std::vector<double> av, hdinv;

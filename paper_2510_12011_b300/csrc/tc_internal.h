@@ -36,6 +36,7 @@ struct tc_mesh {
   std::vector<int64_t> inc_ptr;   // n+1
   std::vector<int32_t> inc;       // 4*ne entries: e*4 + a (node is vertex a of element e)
   tc::Csr pattern;
+  int32_t sell_sigma = 0;         // SELL row-sorting window for simulations assembled from it (0: 1024)
 };
 
 namespace tc {

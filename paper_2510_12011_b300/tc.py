@@ -60,6 +60,7 @@ _SIGS = {
     "tc_mesh_nnz": [_P, _I64],
     "tc_mesh_matrices": [_P, _D, _D, C.c_int32, _I64, _I32, _D, _D],
     "tc_mesh_ordering": [_P, C.c_int32, _I32, _I32],
+    "tc_mesh_set_sell_sigma": [_P, C.c_int32],
     "tc_assemble": [_P, _D, _D, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
                     C.c_int32, _P, C.POINTER(_P)],
     "tc_sim_size": [_P, _I64, _I64, _I64, _I32],
@@ -216,6 +217,10 @@ class Mesh:
         _check(lib().tc_mesh_ordering(self._h, sell_sigma, perm.ctypes.data_as(_I32),
                                       sw.ctypes.data_as(_I32)))
         return perm, sw
+
+    def set_sell_sigma(self, sigma):
+        """SELL row-sorting window for simulations assembled from this mesh afterwards."""
+        _check(lib().tc_mesh_set_sell_sigma(self._h, int(sigma)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -508,9 +513,10 @@ def selftest_exp(x):
     return a, b
 
 
-def from_workload(w, stream=None, precision=TC_FP64):
-    """Build a Simulation from an ``inputs.Workload`` (mesh, tissue, model, stimuli, solver)."""
-    mesh = Mesh.from_inputs(w.mesh)
+def from_workload(w, stream=None, precision=TC_FP64, mesh=None):
+    """Build a Simulation from an ``inputs.Workload`` (mesh, tissue, model, stimuli, solver);
+    `mesh` may pass an already created Mesh of w.mesh (e.g. with a chosen SELL window)."""
+    mesh = Mesh.from_inputs(w.mesh) if mesh is None else mesh
     sim = Simulation(mesh, w.sigma_l, w.sigma_t, w.chi, w.cm, w.theta, w.dt, precision, stream)
     sim.mesh = mesh
     sim.set_activation_threshold(w.v_threshold)

@@ -99,3 +99,25 @@ def test_full_batch_steps_in_fp32():
         a = act[off:off + w.mesh.n_nodes]
         assert np.mean(act[nodes] >= 0.0) > 0.5
         assert 0 < np.count_nonzero(a >= 0.0) < a.size
+
+
+def test_layout_autotuner_over_sell_window_and_launch_shape():
+    """The layout autotuner times each SELL window with its best launch shape and keeps the
+    fastest; simulations laid out with different windows compute the same solution (up to the
+    order of additions)."""
+    from paper_2510_12011_b300 import tune
+    b = I.batched_slabs(count=6, seed=11, h=0.5, t_end=5.0)
+    w = b.workload
+    w.rtol, w.atol, w.max_iter = 1e-10, 0.0, 1000
+    res = tune.autotune_layout(w, precision=tc.TC_FP64, sigmas=(1, 1024), trial_steps=10)
+    assert {t["sell_sigma"] for t in res["trials"]} == {1, 1024}
+    assert res["ms_per_step"] == min(t["ms_per_step"] for t in res["trials"])
+    assert res["trials"][0]["padded_nnz"] >= res["trials"][1]["padded_nnz"]
+    vs = []
+    for sg in (1, 1024):
+        res["mesh"].set_sell_sigma(sg)
+        sim = tc.from_workload(w, precision=tc.TC_FP64, mesh=res["mesh"])
+        sim.step(200)
+        vs.append(sim.read())
+        sim.close()
+    assert np.abs(vs[0] - vs[1]).max() <= 1e-9 * max(1.0, np.abs(vs[1]).max())
