@@ -56,6 +56,7 @@ struct tc_mlp {
   // tensor-core backward pass: K-major BF16 copies of dZ^T, A_l^T, dZ and the weights W_l [in][out]
   __nv_bfloat16 *dzT = nullptr, *actT = nullptr, *dzb = nullptr, *wT = nullptr;
   int* gemm_err = nullptr;                      // wait failures of the GEMM kernel
+  int* counters = nullptr;                      // device: [0] batch index in the epoch, [1] Adam steps
 };
 
 namespace {
@@ -294,11 +295,17 @@ __global__ void silu_back_kernel(int64_t n, const float* da, const float* zprev,
   if (e < n) dz[e] = da[e] * silu_grad(zprev[e]);
 }
 
-// Adam (Kingma & Ba 2015) on the FP32 master parameters, then the BF16 weight copies.
+__global__ void accumulate_kernel(float* sum, const float* v) { *sum += *v; }
+
+// Adam (Kingma & Ba 2015) on the FP32 master parameters, then the BF16 weight copies; the step
+// count t = counters[1] + 1 is read on the device (bias corrections 1 - b^t), so that one captured
+// training step serves every batch.
 __global__ void adam_kernel(int64_t n, float* p, const float* g, float* m, float* v, __nv_bfloat16* wt,
-                            float lr, float b1, float b2, float eps, float c1, float c2) {
+                                 float lr, float b1, float b2, float eps, const int* counters) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const float t = (float)(counters[1] + 1);
+  const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -309,7 +316,11 @@ __global__ void adam_kernel(int64_t n, float* p, const float* g, float* m, float
   wt[i] = __float2bfloat16(pi);
 }
 
-__global__ void accumulate_kernel(float* sum, const float* v) { *sum += *v; }
+// End of a training step: next batch of the epoch, one more Adam step.
+__global__ void train_tick_kernel(int* counters) {
+  counters[0] += 1;
+  counters[1] += 1;
+}
 
 __global__ void cast_kernel(int64_t n, const float* p, __nv_bfloat16* wt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,13 +378,13 @@ __global__ void init_kernel(int64_t n, float* p, uint64_t seed, const int64_t* o
 
 // Rows of the training set -> normalized split-BF16 inputs and FP32 targets of one batch.
 // x: [n][20] raw features; y: [n][19] raw next state; targets are normalized deltas.
-__global__ void gather_batch_kernel(int64_t rows, const int32_t* idx, const float* x, const float* y,
-                                    const float* norm, __nv_bfloat16* a0, float* tgt) {
+__global__ void gather_batch_kernel(int64_t rows, const int32_t* idx, const int* batch_index, const float* x,
+                                    const float* y, const float* norm, __nv_bfloat16* a0, float* tgt) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rows * kMlpPad) return;
   const int64_t r = e / kMlpPad;
   const int c = (int)(e % kMlpPad);
-  const int64_t s = idx ? idx[r] : r;
+  const int64_t s = idx ? idx[(batch_index ? (int64_t)*batch_index * rows : 0) + r] : r;
   const float* in_mean = norm;
   const float* in_scale = norm + kMlpIn;
   const float* out_mean = norm + 2 * kMlpIn;
@@ -498,8 +509,7 @@ tc_status ensure_workspace(tc_mlp* m, int64_t rows) {
 // Forward pass on act[0] (rows x 32): fills z[l], act[l+1]; output in z[4].
 tc_status forward(tc_mlp* m, int64_t rows, cudaStream_t st) {
   if (m->gemm == kGemmTcgen05) {
-    int* err = reinterpret_cast<int*>(m->loss) + 1;   // the word after the loss scalar
-    CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    int* err = reinterpret_cast<int*>(m->loss) + 1;   // the word after the loss scalar (callers reset it)
     TRY(forward_tc(m, rows, m->act[0], m->z[kMlpLayers - 1], true, err, st));
     return TC_OK;
   }
@@ -607,6 +617,7 @@ tc_status tc_mlp_create(uint64_t seed, tc_mlp** out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->wt0d, kMlpHidden * kMlpIn0 * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->wT, n * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->gemm_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&m->counters, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->gemm_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&m->norm, (2 * kMlpIn + 2 * kMlpOut) * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, 4 * sizeof(float));   // loss, error word, epoch sum
@@ -673,7 +684,8 @@ void tc_mlp_destroy(tc_mlp* m) {
   for (void* p : {(void*)m->params, (void*)m->grads, (void*)m->adam_m, (void*)m->adam_v, (void*)m->wt,
                   (void*)m->norm, (void*)m->dz, (void*)m->da, (void*)m->tgt, (void*)m->idx,
                   (void*)m->loss, (void*)m->img, (void*)m->splitk, (void*)m->gw0d, (void*)m->wt0d,
-                  (void*)m->dzT, (void*)m->actT, (void*)m->dzb, (void*)m->wT, (void*)m->gemm_err})
+                  (void*)m->dzT, (void*)m->actT, (void*)m->dzb, (void*)m->wT, (void*)m->gemm_err,
+                  (void*)m->counters})
     cudaFree(p);
   for (int l = 0; l < kMlpLayers; ++l) {
     cudaFree(m->act[l]);
@@ -780,6 +792,7 @@ tc_status tc_mlp_forward(tc_mlp* m, const float* x, int64_t n, float* y) {
   std::vector<__nv_bfloat16> a0(n * kMlpIn0);
   for (int64_t r = 0; r < n; ++r) mlp_split_input(x + r * kMlpIn, a0.data() + r * kMlpIn0);
   CUDA_TRY(cudaMemcpy(m->act[0], a0.data(), a0.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(reinterpret_cast<int*>(m->loss) + 1, 0, sizeof(int)));
   TRY(forward(m, n, 0));
   int err = 0;
   CUDA_TRY(cudaMemcpy(&err, reinterpret_cast<int*>(m->loss) + 1, sizeof(int), cudaMemcpyDeviceToHost));
@@ -809,6 +822,7 @@ tc_status tc_mlp_gradients(tc_mlp* m, const float* x, const float* t, int64_t n,
   CUDA_TRY(cudaMemcpy(m->act[0], a0.data(), a0.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(m->tgt, tg.data(), tg.size() * sizeof(float), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(m->gemm_err, 0, sizeof(int)));
+  CUDA_TRY(cudaMemset(reinterpret_cast<int*>(m->loss) + 1, 0, sizeof(int)));
   TRY(forward(m, n, 0));
   TRY(backward(m, n, 0));
   CUDA_TRY(cudaMemcpy(grads, m->grads, m->d.n_params * sizeof(float), cudaMemcpyDeviceToHost));
@@ -843,48 +857,82 @@ tc_status tc_mlp_train(tc_mlp* m, const float* x_dev, const float* y_dev, int64_
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
   };
-  tc_status status = TC_OK;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   float* d_sum = m->loss + 2;
+  int* d_err = reinterpret_cast<int*>(m->loss) + 1;
+  // One training step: gather the batch (its index in the epoch from counters[0]), forward,
+  // backward, Adam (step count from counters[1]), weight images, advance the counters.  Captured
+  // once per call as a CUDA graph and replayed for every batch; launched directly if capture fails.
+  auto record_step = [&](cudaStream_t cs) -> tc_status {
+    gather_batch_kernel<<<blocks_for((int64_t)batch * kMlpPad), 256, 0, cs>>>(
+        batch, d_order, m->counters, x_dev, y_dev, m->norm, m->act[0], m->tgt);
+    TRY(forward(m, batch, cs));
+    TRY(backward(m, batch, cs));
+    accumulate_kernel<<<1, 1, 0, cs>>>(d_sum, m->loss);
+    adam_kernel<<<blocks_for(m->d.n_params), 256, 0, cs>>>(m->d.n_params, m->params, m->grads, m->adam_m,
+                                                           m->adam_v, m->wt, lr, b1, b2, eps, m->counters);
+    TRY(rebuild_images(m, cs));   // duplicated layer-0 weights and tensor-core images
+    train_tick_kernel<<<1, 1, 0, cs>>>(m->counters);
+    CUDA_TRY(cudaGetLastError());
+    return TC_OK;
+  };
+  cudaGraphExec_t exec = nullptr;
+  {
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    tc_status rs = e == cudaSuccess ? record_step(cs) : TC_ERR_CUDA;
+    if (e == cudaSuccess) {
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (rs == TC_OK && e2 == cudaSuccess && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cs);
+    cudaGetLastError();   // a failed capture leaves no sticky error; launch step by step then
+    clear_error();
+  }
+  int h_counters[2] = {0, (int)m->adam_t};
+  tc_status status = TC_OK;
   for (int ep = 0; ep < epochs && status == TC_OK; ++ep) {
     for (int64_t i = n - 1; i > 0; --i) std::swap(order[i], order[next() % (uint64_t)(i + 1)]);
+    h_counters[0] = 0;
     cudaError_t e = cudaMemcpyAsync(d_order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->counters, h_counters, 2 * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_sum, 0, sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->gemm_err, 0, sizeof(int), st);
     if (e != cudaSuccess) {
-      status = cuda_fail(e, "cudaMemcpyAsync");
+      status = cuda_fail(e, "training epoch set-up");
       break;
     }
     for (int64_t bi = 0; bi < nb && status == TC_OK; ++bi) {
-      gather_batch_kernel<<<blocks_for((int64_t)batch * kMlpPad), 256, 0, st>>>(
-          batch, d_order + bi * batch, x_dev, y_dev, m->norm, m->act[0], m->tgt);
-      if ((status = forward(m, batch, st)) != TC_OK) break;
-      if ((status = backward(m, batch, st)) != TC_OK) break;
-      accumulate_kernel<<<1, 1, 0, st>>>(d_sum, m->loss);
-      m->adam_t += 1;
-      const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
-      adam_kernel<<<blocks_for(m->d.n_params), 256, 0, st>>>(m->d.n_params, m->params, m->grads, m->adam_m,
-                                                             m->adam_v, m->wt, lr, b1, b2, eps, c1, c2);
-      status = rebuild_images(m, st);   // duplicated layer-0 weights and tensor-core images
-      e = cudaGetLastError();
-      if (e != cudaSuccess) status = cuda_fail(e, "training step");
+      if (exec) {
+        e = cudaGraphLaunch(exec, st);
+        if (e != cudaSuccess) status = cuda_fail(e, "training step");
+      } else {
+        status = record_step(st);
+      }
     }
     if (status != TC_OK) break;
     float sums[2] = {0.f, 0.f};
     cudaMemcpyAsync(sums, d_sum, sizeof(float), cudaMemcpyDeviceToHost, st);
     int err = 0, gerr = 0;
-    cudaMemcpyAsync(&err, reinterpret_cast<int*>(m->loss) + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&gerr, m->gemm_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (e2 != cudaSuccess) {
       status = cuda_fail(e2, "training epoch");
       break;
     }
+    h_counters[1] += (int)nb;
+    m->adam_t = h_counters[1];
     if (m->gemm == kGemmTcgen05 && (err || gerr)) status = fail(TC_ERR_TIMEOUT, "tensor-core MLP wait hit its limit");
     const float mean = sums[0] / (float)nb;
     if (loss_history) loss_history[ep] = mean;
     if (!std::isfinite(mean)) status = fail(TC_ERR_NAN, "training loss is not finite");
   }
+  if (exec) cudaGraphExecDestroy(exec);
   cudaFree(d_order);
   cudaStreamSynchronize(st);
   return status;
