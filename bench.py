@@ -35,14 +35,14 @@ from paper_2510_12011_b300 import inputs as I  # noqa: E402
 METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + activation "
           "capture); FP32 precision form alongside")
 # FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
-# profiles/ (FP64 pipe utilisation x elapsed cycles x 296 thread instructions per clock / nodes);
-# used to turn the live launch time into an achieved FP64 instruction rate.
-TP06_FP64_INSTR_PER_NODE = 1517.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.67e6   # dram read + write of the same capture
+# profiles/ (sm__inst_executed_pipe_fp64.sum x 32 lanes / nodes); used to turn the live launch
+# time into an achieved FP64 instruction rate.
+TP06_FP64_INSTR_PER_NODE = 1302.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.31e6   # dram read + write of the same capture
 # dram read + write of one pcg_step_kernel<1024, double> launch on the large slab (ncu capture in
-# profiles/, 8.47 CG iterations in that launch)
-PCG_FP64_DRAM_BYTES_PER_LAUNCH = 1.305e9
-PCG_FP64_CAPTURE_ITERATIONS = 8.47
+# profiles/, a launch of a 23-step run averaging 8.65 CG iterations per launch)
+PCG_FP64_DRAM_BYTES_PER_LAUNCH = 1.301e9
+PCG_FP64_CAPTURE_ITERATIONS = 8.65
 
 
 def parse():
@@ -531,7 +531,7 @@ def run_ours(args):
     roof_pcg = {"kernel": "pcg_step_kernel", "bound": "hbm", "achieved": pcg_gbs, "peak": peak,
                 "unit": "GB/s", "frac": pcg_gbs / peak,
                 "traffic": PCG_FP64_DRAM_BYTES_PER_LAUNCH if cap else None,
-                "traffic_note": (f"ncu dram bytes of one launch with {PCG_FP64_CAPTURE_ITERATIONS} CG iterations "
+                "traffic_note": (f"ncu dram bytes of one launch in a run averaging {PCG_FP64_CAPTURE_ITERATIONS} CG iterations "
                                  f"(this run averages {iters:.2f}); the 4 MB node vectors partly stay in the "
                                  "132.6 MB L2, the matrix streams from DRAM") if cap else None,
                 "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": bytes_launch,

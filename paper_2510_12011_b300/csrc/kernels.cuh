@@ -268,13 +268,15 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
       acc0 = fmaT(v2, x2, acc0);
       acc1 = fmaT(v3, x3, acc1);
     }
+    // the last w mod 4 entries: one FMA each into acc0, then the two sums trade places so that
+    // the next entry goes to the other one (a branch on the entry's parity was if-converted into
+    // both FMAs, a third more FP64 work on a 15-entry row); the final sum is symmetric
     for (; j < w; ++j) {
       const int e = beg + 32 * j;
-      const T v = __ldg(val + e), xv = x[__ldg(col + e)];
-      if (j & 1)
-        acc1 = fmaT(v, xv, acc1);
-      else
-        acc0 = fmaT(v, xv, acc0);
+      acc0 = fmaT(__ldg(val + e), x[__ldg(col + e)], acc0);
+      const T t = acc0;
+      acc0 = acc1;
+      acc1 = t;
     }
   }
   return acc0 + acc1;
