@@ -115,25 +115,30 @@ def spmv_bytes(n, nnz, value_bytes=8):
 
 
 def spmv_cold(sim, n, dtype, stream, torch, tc, reps=30):
-    """Mean time (ms) of y = A x over `reps` launches, each after a 512 MB read that evicts the
-    matrix from L2 (one launch spans about 15 ticks of the event clock: the mean of many cold
-    launches averages the quantisation out)."""
+    """Mean device time (ms) of one y = A x launch that starts with the matrix out of L2: `reps`
+    pairs (a 512 MB read that evicts L2, then the SpMV) back to back between two events, minus
+    `reps` of the read alone timed the same way; the median of three such differences.  One SpMV
+    spans only about a dozen ticks of the event clock (about 2 us each), so single launches are
+    not timed on their own.  Returns (ms, reps)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     x = torch.randn(n, dtype=dtype, device=dev)
     y = torch.empty_like(x)
     flush = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    times = []
-    for rep in range(reps + 3):
-        flush.sum()
+
+    def seq(with_spmv):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        sim.apply_dev(tc.TC_OP_A, x.data_ptr(), y.data_ptr())
+        for _ in range(reps):
+            flush.sum()   # reading 512 MB evicts the matrix without leaving dirty lines
+            if with_spmv:
+                sim.apply_dev(tc.TC_OP_A, x.data_ptr(), y.data_ptr())
         b.record(stream)
         torch.cuda.synchronize()
-        if rep >= 3:
-            times.append(a.elapsed_time(b))
-    return float(np.mean(times)), len(times)
+        return a.elapsed_time(b)
+    seq(True)
+    diffs = sorted((seq(True) - seq(False)) / reps for _ in range(3))
+    return float(diffs[1]), reps
 
 
 class ClockSampler:
@@ -549,25 +554,8 @@ def run_ours(args):
         roofline = roof_pcg
 
     # SpMV HBM GB/s: y = A x alone, L2 flushed before every launch
-    x = torch.randn(n, dtype=torch.float64, device=dev)
-    y = torch.empty_like(x)
-    flush = torch.ones(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    times = []
-    for rep in range(33):
-        flush_sum = flush.sum()   # reading 512 MB evicts the matrix without leaving dirty lines
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.apply_dev(tc.TC_OP_A, x.data_ptr(), y.data_ptr())
-        b.record(stream)
-        torch.cuda.synchronize()
-        if rep >= 3:
-            times.append(a.elapsed_time(b))
-    # one launch lasts ~30 us and the event clock ticks in steps of about 2 us: the mean of 30
-    # cold launches averages the quantisation out (a median would pick one of two tick counts)
-    spmv_ms = float(np.mean(times))
+    spmv_ms, spmv_reps = spmv_cold(sim, n, torch.float64, stream, torch, tc)
     spmv_gbs = spmv_bytes(n, size["nnz"]) / (spmv_ms * 1e-3) / 1e9
-    del flush, x, y
 
     # end to end through the C ABI with host buffers: each step uploads V^k, V^{k-1} and every
     # ionic state from page-locked host memory, steps once and reads V^{k+1} and the states back
@@ -617,7 +605,8 @@ def run_ours(args):
         ms_sp, reps = spmv_cold(sim32, n, torch.float32, stream, torch, tc)
         by = spmv_bytes(n, size["nnz"], 4)
         fp32["spmv"] = {"value": by / (ms_sp * 1e-3) / 1e9, "unit": "GB/s", "ms": ms_sp, "bytes": by,
-                        "frac": by / (ms_sp * 1e-3) / 1e9 / peak, "launches": reps, "statistic": "mean",
+                        "frac": by / (ms_sp * 1e-3) / 1e9 / peak, "launches": reps,
+                        "statistic": "median of 3 (sequence of flush + SpMV minus sequence of flush) / launches",
                         "l2": "flushed (512 MB read) before every launch"}
         sim32.close()
         if w.model == "tp06":
@@ -662,7 +651,7 @@ def run_ours(args):
         "roofline_pcg": roof_pcg,
         "spmv": {"value": spmv_gbs, "unit": "GB/s", "ms": spmv_ms, "bytes": spmv_bytes(n, size["nnz"]),
                  "frac": spmv_gbs / peak, "l2": "flushed (512 MB read) before every launch",
-                 "launches": len(times), "statistic": "mean"},
+                 "launches": spmv_reps, "statistic": "median of 3 (sequence of flush + SpMV minus sequence of flush) / launches"},
         "fp32_form": fp32,
         "surrogate_form": sur,
         "batched_form": batched,

@@ -226,16 +226,26 @@ __device__ __forceinline__ double fmaT(double a, double b, double c) { return fm
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
 // Row products over one SELL slice, lane = row.  Even entries accumulate in acc0 and odd entries
-// in acc1, each in entry order, so both loop shapes below give the same bits.  FP64: four
-// entries (indices, values, gathered vector entries) in flight before their FMAs - the product is
-// bound by B300's FP64 pipe as much as by memory.  FP32: predicated chunks of eight entries, so
-// that a 15-entry row is two rounds of (indices and values, then gathers) - the FP32 solve keeps
-// its working set in L2 and is bound by load latency.
-template <typename T>
+// in acc1, each in entry order, so every shape below gives the same bits.  The product is bound by
+// the latency of its rounds of dependent loads (index, then gathered vector entry); which shape
+// hides that best depends on the launch (measured on the 40x16x6 mm slab):
+//  kSellChunk8   predicated chunks of eight entries: indices and values of a chunk together, then
+//                its gathers, then its FMAs - a 15-entry row is two rounds.  Standalone FP64
+//                SpMV with 18 two-warp blocks per SM: 22.8 us against 28.0 us for kSellUnroll4;
+//                also the FP32 PCG, whose working set stays in L2.
+//  kSellUnroll4  four entries per round, then the last w mod 4 one at a time; fewer live
+//                registers.  The FP64 PCG (1,024-thread blocks, 64 registers at most) runs 5 %
+//                faster with it than with kSellChunk8.
+// Entries past a row's width are neither loaded nor added; the predicates are uniform across the
+// warp (one width per slice).
+constexpr int kSellUnroll4 = 0;
+constexpr int kSellChunk8 = 1;
+
+template <int SHAPE, typename T>
 __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
                                      int beg, int w, const T* x) {
   T acc0 = T(0), acc1 = T(0);
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (SHAPE == kSellChunk8) {
     for (int j = 0; j < w; j += 8) {
       const int e = beg + 32 * j;
       int c[8];
@@ -268,9 +278,9 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
       acc0 = fmaT(v2, x2, acc0);
       acc1 = fmaT(v3, x3, acc1);
     }
-    // the last w mod 4 entries: one FMA each into acc0, then the two sums trade places so that
-    // the next entry goes to the other one (a branch on the entry's parity was if-converted into
-    // both FMAs, a third more FP64 work on a 15-entry row); the final sum is symmetric
+    // the tail: one FMA each into acc0, then the two sums trade places so that the next entry
+    // goes to the other one (a branch on the entry's parity was if-converted into both FMAs, a
+    // fifth more FP64 work on a 15-entry row); the final sum is symmetric
     for (; j < w; ++j) {
       const int e = beg + 32 * j;
       acc0 = fmaT(__ldg(val + e), x[__ldg(col + e)], acc0);
@@ -280,6 +290,15 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
     }
   }
   return acc0 + acc1;
+}
+
+// The shape of the PCG's product per storage type (see above).
+#ifndef TC_PCG_SELL_SHAPE_F64
+#define TC_PCG_SELL_SHAPE_F64 kSellUnroll4
+#endif
+template <typename T>
+constexpr int pcg_sell_shape() {
+  return sizeof(T) == 8 ? TC_PCG_SELL_SHAPE_F64 : kSellChunk8;
 }
 
 // Two value streams over the same pattern: am = sum M_ij g1_j, ak = sum K_ij g2_j.
@@ -428,7 +447,7 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
     for (int s = s0 + warp; s < s1; s += NW) {
       const int beg = a.slice_ptr[s] + lane;
       const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
-      const T acc = sell_dot(a.col, a.vA, beg, w, a.p);
+      const T acc = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, a.p);
       const int64_t row = (int64_t)s * 32 + lane;
       if (row < a.n) {
         a.q[row] = acc;
@@ -569,7 +588,7 @@ __global__ void __launch_bounds__(256) spmv_sell_kernel(int64_t n, int64_t nslic
   for (int64_t s = gw; s < nslices; s += nw) {
     const int beg = slice_ptr[s] + lane;
     const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
-    const T acc = sell_dot(col, val, beg, w, x);
+    const T acc = sell_dot<kSellChunk8>(col, val, beg, w, x);
     const int64_t row = s * 32 + lane;
     if (row < n) y[row] = acc;
   }
