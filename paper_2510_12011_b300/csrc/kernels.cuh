@@ -297,7 +297,7 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
 #define TC_PCG_SELL_SHAPE_F64 kSellUnroll4
 #endif
 template <typename T>
-constexpr int pcg_sell_shape() {
+__host__ __device__ constexpr int pcg_sell_shape() {
   return sizeof(T) == 8 ? TC_PCG_SELL_SHAPE_F64 : kSellChunk8;
 }
 
