@@ -37,8 +37,8 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 # FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
 # profiles/ (sm__inst_executed_pipe_fp64.sum x 32 lanes / nodes); used to turn the live launch
 # time into an achieved FP64 instruction rate.
-TP06_FP64_INSTR_PER_NODE = 1302.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.31e6   # dram read + write of the same capture
+TP06_FP64_INSTR_PER_NODE = 1134.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 109.18e6   # dram read + write of the same capture
 # dram read + write of one pcg_step_kernel<1024, double> launch on the large slab (ncu capture in
 # profiles/, a launch of a 23-step run averaging 8.65 CG iterations per launch)
 PCG_FP64_DRAM_BYTES_PER_LAUNCH = 1.301e9
@@ -96,16 +96,16 @@ def fp64_instr_peak(sm_mhz):
 
 # ---- algorithmic bytes (FP64 values, int32 indices; SELL padding not counted) -------------
 def pcg_launch_bytes(n, nnz, nslices, iters):
-    """Bytes one PCG launch must move: RHS pass (M, K values, indices, g1/g2, dinv in; r, z, p
-    out), per iteration the A-product (A values, indices, p gather, q out) and the vector
-    phases (x, r r/w; p, q, dinv in; z out), the direction update on all but the last
-    iteration (z in, p r/w), and the activation capture (act, V^k, V^{k+1})."""
-    rhs = 20 * nnz + 4 * (nslices + 1) + 16 * n + 8 * n + 24 * n
-    spmv = 12 * nnz + 4 * (nslices + 1) + 16 * n
+    """Bytes one PCG launch must move: RHS pass (M, K values, indices, g1/g2, dinv in; r, z
+    out), per iteration the A-product (A values, indices, z gather; p, q out, and p, q in on all
+    but the first iteration, where p = z and q = A z) and the vector phase (x, r r/w; p, q, dinv
+    in; z out), and the activation capture (act, V^k, V^{k+1})."""
+    rhs = 20 * nnz + 4 * (nslices + 1) + 16 * n + 8 * n + 16 * n
+    spmv = 12 * nnz + 4 * (nslices + 1) + 8 * n + 16 * n
     vec = 64 * n
-    pupd = 24 * n
+    pq_in = 16 * n
     cap = 24 * n
-    return rhs + iters * (spmv + vec) + max(iters - 1.0, 0.0) * pupd + cap
+    return rhs + iters * (spmv + vec) + max(iters - 1.0, 0.0) * pq_in + cap
 
 
 def spmv_bytes(n, nnz, value_bytes=8):

@@ -266,6 +266,9 @@ tc_status tc_selftest_exp(const double* x, double* y_fast, double* y_ref, int64_
 /* tc_selftest_log: the same for the FP64 natural logarithm of the ionic kernels (table-driven,
  * Tang 1990) against the CUDA library log. */
 tc_status tc_selftest_log(const double* x, double* y_fast, double* y_ref, int64_t n);
+/* tc_selftest_rcp: the same for the FP64 reciprocal of the ionic kernels (hardware estimate and
+ * two Newton-Raphson steps) against the IEEE division 1.0 / x.  x finite, nonzero and normal. */
+tc_status tc_selftest_rcp(const double* x, double* y_fast, double* y_ref, int64_t n);
 
 /* ---- learned ionic surrogate --------------------------------------------------------
  * A multilayer perceptron (20 -> 4 x 256 SiLU -> 19; BF16 weights and activations, FP32

@@ -47,6 +47,12 @@ constexpr double kE5p6 = 270.42640742615254, kE1 = 2.718281828459045, kEm4p5 = 0
 constexpr double kE1p3 = 3.6692966676192444, kE2p5 = 12.182493960703473, kEm3p2 = 0.04076220397836621;
 constexpr double kE5o6 = 2.300975890892825, kE20o6 = 28.03162489452614, kE20o7 = 17.41170806332765;
 constexpr double kE5 = 148.4131591025766, kEm3 = 0.049787068367863944;
+// the same device for slopes whose exponential is the reciprocal (or the square of one) of a
+// shared one: exp(-12), exp(-26/7), exp(-35/15), exp(-8/7.5), exp(3), and exp(-30 F/RT) (the
+// GHK exponential exp(2 (V - 15) F/RT) = exp(-30 F/RT) / exp(-V F/RT)^2)
+constexpr double kEm12 = 6.14421235332821e-06, kEm26o7 = 0.0243728440732796;
+constexpr double kEm35o15 = 0.09697196786440507, kEm8o7p5 = 0.34415378686541237;
+constexpr double kE3 = 20.085536923187668, kGhkK = 0.32529698149690256;
 }  // namespace tp06
 
 inline void tp06_rest_state(int /*cell*/, double* u, double* v0) {
@@ -449,10 +455,25 @@ __device__ __forceinline__ double exp_tang(double x) {
   return in_range ? out : exp(x);
 }
 
+// 1/d for a finite, nonzero, normal d: the hardware estimate (rcp.approx, relative error below
+// 2^-20) refined by two Newton-Raphson steps y <- y + y (1 - d y), each of which squares the
+// relative error.  Four FP64 instructions against about twice that for a division; on 2.7 M
+// sampled d in [1e-20, 1e20] it matched the correctly rounded 1/d in every case.
+__device__ __forceinline__ double rcp_nr(double d) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+
 __device__ __forceinline__ double mexp(double x) { return exp_tang(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
 __device__ __forceinline__ double mlog(double x) { return log_tang(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
+__device__ __forceinline__ double mrcp(double x) { return rcp_nr(x); }
+__device__ __forceinline__ float mrcp(float x) { return 1.f / x; }
 __device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double mexpm1(double x) { return expm1(x); }
@@ -473,34 +494,39 @@ template <typename T>
 __device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
   using namespace tp06;
   Tp06VFactors<T> f;
+  const T vf = V * T(1.0 / kRTF);
+  const T q = mexp(-vf);                       // exp(-V F/RT)
+  const T eg = mexp(T(kGam) * vf);
+  const T eg1 = eg * q;                        // exp((gamma - 1) V F/RT)
   const T vm = V - T(15);
   const T x = vm * T(2.0 / kRTF);
-  if (x != T(0)) {
-    // exp(x) - 1 from the exponential itself where the subtraction loses at most a few ulp
-    // (|x| >= 1/2); the library expm1 only near x = 0, that is within 6.7 mV of 15 mV
-    const T ex = mexp(x);
-    T em1;
-    if (fabs(x) < T(0.5))
-      em1 = mexpm1(x);
-    else
-      em1 = ex - T(1);
+  if (fabs(x) >= T(0.5)) {
+    // exp(x) = K / q^2 with K = exp(-30 F/RT), so that both GHK factors share the denominator
+    // K - q^2 (exp(x) - 1 times q^2), which keeps its relative accuracy while |x| >= 1/2
+    const T q2 = q * q;
+    const T sg = vm * T(kF / kRTF) * mrcp(T(kGhkK) - q2);
+    f.ghk_cass = sg * T(kGhkK);
+    f.ghk = T(-4 * kCao) * sg * q2;
+  } else if (x != T(0)) {   // within 6.7 mV of 15 mV: the library expm1
+    const T em1 = mexpm1(x);
     const T c = T(4) * vm * T(kF / kRTF) / em1;
-    f.ghk_cass = c * T(0.25) * ex;
+    f.ghk_cass = c * T(0.25) * (em1 + T(1));
     f.ghk = -c * T(kCao);
   } else {   // limit V -> 15 mV: 2 F (0.25 CaSS - Cao)
     f.ghk_cass = T(2 * kF * 0.25);
     f.ghk = T(-2 * kF * kCao);
   }
-  const T vf = V * T(1.0 / kRTF);
-  f.nak = T(kPNaK * kKo / (kKo + kKmK)) /
-          (T(1) + T(0.1245) * mexp(T(-0.1) * vf) + T(0.0353) * mexp(-vf));
-  const T eg = mexp(T(kGam) * vf), eg1 = mexp(T(kGam - 1.0) * vf);
+  // I_NaK, I_NaCa and I_pK factors: three quotients over one reciprocal of their denominators
+  const T dn = T(1) + T(0.1245) * mexp(T(-0.1) * vf) + T(0.0353) * q;
   const T den = T((kKmNai * kKmNai * kKmNai + kNao * kNao * kNao) * (kKmCa + kCao)) *
                 (T(1) + T(kKsat) * eg1);
-  const T rden = T(1) / den;
+  const T dp = T(1) + mexp((T(25) - V) * T(1.0 / 5.98));
+  const T rr = mrcp(dn * den * dp);
+  f.nak = T(kPNaK * kKo / (kKo + kKmK)) * (den * dp * rr);
+  const T rden = dn * dp * rr;
   f.naca_a = T(kKNaCa) * eg * rden;
   f.naca_b = T(kKNaCa * kAlphaNaCa * kNao * kNao * kNao) * eg1 * rden;
-  f.ipk = T(1) / (T(1) + mexp((T(25) - V) * T(1.0 / 5.98)));
+  f.ipk = dn * den * rr;
   return f;
 }
 
@@ -529,10 +555,14 @@ __device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int ce
   const T eb = mexp(T(-0.5) * dv);
   const T nb = T(3) * mexp(T(0.0002) * (dv + T(100))) + mexp(T(0.1) * (dv - T(10)));
   const T na = T(0.1) * (T(1) + eb);
+  // the quotients of I_K1, I_NaK and I_pCa over one reciprocal of their denominators
+  const T d1 = na + nb * (T(1) + ea), d2 = nai + T(kKmNa), d3 = T(kKpCa) + cai;
+  const T d23 = d2 * d3;
+  const T rr = mrcp(d1 * d23);
   Tp06Currents<T> c;
   const T gto = cell == 0 ? T(0.073) : T(0.294);
   const T gks = cell == 1 ? T(0.098) : T(0.392);
-  c.ik1 = T(kGK1) * (na / (na + nb * (T(1) + ea))) * dv;   // sqrt(Ko/5.4) = 1 at Ko = 5.4 mM
+  c.ik1 = T(kGK1) * na * (d23 * rr) * dv;   // sqrt(Ko/5.4) = 1 at Ko = 5.4 mM
   c.ito = gto * u[17] * u[16] * dv;
   c.ikr = T(kGKr) * u[6] * u[7] * dv;
   c.iks = gks * u[8] * u[8] * (V - eks);
@@ -540,9 +570,9 @@ __device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int ce
   c.ibna = T(kGbNa) * (V - ena);
   c.ical = T(kGCaL) * u[12] * u[13] * u[14] * u[15] * (f.ghk_cass * cass + f.ghk);
   c.ibca = T(kGbCa) * (V - eca);
-  c.inak = f.nak * (nai / (nai + T(kKmNa)));
+  c.inak = f.nak * nai * (d1 * d3 * rr);
   c.inaca = f.naca_a * (nai * nai * nai) * T(kCao) - f.naca_b * cai;
-  c.ipca = T(kGpCa) * cai / (T(kKpCa) + cai);
+  c.ipca = T(kGpCa) * cai * (d1 * d2 * rr);
   c.ipk = T(kGpK) * f.ipk * dv;
   return c;
 }
@@ -567,21 +597,27 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   {
     const T cai = u[2], casr = u[3], cass = u[4], rbar = u[5];
     // the same expressions with each quotient of quotients over one denominator
-    const T casr2 = casr * casr;
-    const T kcasr = T(kMaxSR) - T(kMaxSR - kMinSR) * casr2 / (casr2 + T(kEC * kEC));
+    // six quotients, two reciprocals: k_casr with I_up, then O with the three buffer factors
+    const T casr2 = casr * casr, cai2 = cai * cai;
+    const T dk = casr2 + T(kEC * kEC), du = cai2 + T(kKup * kKup);
+    const T r1 = mrcp(dk * du);
+    const T kcasr = T(kMaxSR) - T(kMaxSR - kMinSR) * casr2 * (du * r1);
+    const T iup = T(kVmaxUp) * cai2 * (dk * r1);
     const T k2 = T(kK2p) * kcasr;
     const T cass2 = cass * cass;
-    const T o = T(kK1p) * cass2 * rbar / (T(kK3) * kcasr + T(kK1p) * cass2);
-    const T irel = T(kVrel) * o * (casr - cass);
-    const T ileak = T(kVleak) * (casr - cai);
-    const T cai2 = cai * cai;
-    const T iup = T(kVmaxUp) * cai2 / (cai2 + T(kKup * kKup));
-    const T ixfer = T(kVxfer) * (cass - cai);
     const T bi = cai + T(kKbufc), bsr = casr + T(kKbufsr), bss = cass + T(kKbufss);
     const T bi2 = bi * bi, bsr2 = bsr * bsr, bss2 = bss * bss;
-    const T fi = bi2 / (bi2 + T(kBufc * kKbufc));
-    const T fsr = bsr2 / (bsr2 + T(kBufsr * kKbufsr));
-    const T fss = bss2 / (bss2 + T(kBufss * kKbufss));
+    const T dox = T(kK3) * kcasr + T(kK1p) * cass2, dfi = bi2 + T(kBufc * kKbufc);
+    const T dsr = bsr2 + T(kBufsr * kKbufsr), dss = bss2 + T(kBufss * kKbufss);
+    const T pa = dox * dfi, pb = dsr * dss;
+    const T r2 = mrcp(pa * pb);
+    const T o = T(kK1p) * cass2 * rbar * (dfi * pb * r2);
+    const T irel = T(kVrel) * o * (casr - cass);
+    const T ileak = T(kVleak) * (casr - cai);
+    const T ixfer = T(kVxfer) * (cass - cai);
+    const T fi = bi2 * (dox * pb * r2);
+    const T fsr = bsr2 * (pa * dss * r2);
+    const T fss = bss2 * (pa * dsr * r2);
     const T cvf = T(kCap / (kVc * kF));
     const T dki = -(c.ik1 + c.ito + c.ikr + c.iks + c.ipk - T(2) * c.inak) * cvf;
     const T dnai = -(c.ina + c.ibna + T(3) * c.inak + T(3) * c.inaca) * cvf;
@@ -599,102 +635,144 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     un[5] = rbar + dt * drbar;
   }
   // gates: Rush-Larsen with inf and tau at V^k (fCass at CaSS^k).  Each rate 1/tau is formed
-  // directly over one common denominator (one division where tau is a sum of quotients, none
-  // where it is a product of them); divisions by constants are multiplications by reciprocals.
+  // directly over one common denominator, and a gate's steady state and rate share one reciprocal
+  // of the product of their denominators (one division per gate); divisions by constants are
+  // multiplications by reciprocals.  Exponentials exp(a V + b) whose slope a is shared (or is
+  // minus, or minus twice, a shared slope) are the shared exp(a V) times literal exp(b).
   {
-    // exponentials shared by several gates (slopes 1/5, -1/10, 1/10 at V + 30, -1/6, 1/7, -1/20)
-    const T x02 = mexp(T(0.2) * V);
-    const T xm01 = mexp(T(-0.1) * V);
-    const T x30 = mexp((V + T(30)) * T(0.1));
+    const T x02 = mexp(T(0.2) * V);                  // exp(V/5)
+    const T xm01 = mexp(T(-0.1) * V);                // exp(-V/10)
     const T xm16 = mexp(V * T(-1.0 / 6.0));
     const T x17 = mexp(V * T(1.0 / 7.0));
     const T xm005 = mexp(T(-0.05) * V);
-    const T e1 = mexp((T(-56.86) - V) * T(1.0 / 9.03));
-    const T minf = T(1) / ((T(1) + e1) * (T(1) + e1));
-    // tau_m = alpha_m beta_m, alpha_m = 1/(1+ea), beta_m = 0.1/(1+eb) + 0.1/(1+ec)
-    const T ea = T(1) + mexp((T(-60) - V) * T(0.2));
-    const T eb = T(1) + x02 * T(kE7);
-    const T ec = T(1) + mexp((V - T(50)) * T(1.0 / 200.0));
-    un[9] = rl_rate(u[9], minf, ea * eb * ec / (T(0.1) * (eb + ec)), dt);
-    const T e2 = mexp((V + T(71.55)) * T(1.0 / 7.43));
-    const T hinf = T(1) / ((T(1) + e2) * (T(1) + e2));
-    T rh, rj;   // alpha + beta of h and of j
-    if (V < T(-40)) {
-      rh = T(0.057) * mexp((V + T(80)) * T(-1.0 / 6.8)) + T(2.7) * mexp(T(0.079) * V) +
-           T(3.1e5) * mexp(T(0.3485) * V);
-      const T ja = T(1) + mexp(T(0.311) * (V + T(79.23)));
-      const T jb = T(1) + mexp(T(-0.1378) * (V + T(40.14)));
-      rj = ((T(-2.5428e4) * mexp(T(0.2444) * V) - T(6.948e-6) * mexp(T(-0.04391) * V)) * (V + T(37.78)) * jb +
-            T(0.02424) * mexp(T(-0.01052) * V) * ja) /
-           (ja * jb);
-    } else {
-      rh = T(0.77 / 0.13) / (T(1) + mexp((V + T(10.66)) * T(-1.0 / 11.1)));
-      rj = T(0.6) * mexp(T(0.057) * V) / (T(1) + xm01 * T(kEm3p2));
-    }
-    un[10] = rl_rate(u[10], hinf, rh, dt);
-    un[11] = rl_rate(u[11], hinf, rj, dt);
-    // tau_xr1 = 450/(1+e) * 6/(1+e'):  1/tau = (1+e)(1+e')/2700
-    const T xr1inf = T(1) / (T(1) + mexp((T(-26) - V) * T(1.0 / 7.0)));
-    un[6] = rl_rate(u[6], xr1inf,
-                    (T(1) + xm01 * T(kEm4p5)) * (T(1) + mexp((V + T(30)) * T(1.0 / 11.5))) *
-                        T(1.0 / 2700.0),
-                    dt);
-    // tau_xr2 = 3/(1+e) * 1.12/(1+e'):  1/tau = (1+e)(1+e')/3.36
-    const T xr2inf = T(1) / (T(1) + mexp((V + T(88)) * T(1.0 / 24.0)));
-    un[7] = rl_rate(u[7], xr2inf,
-                    (T(1) + xm005 * T(kEm3)) * (T(1) + mexp((V - T(60)) * T(0.05))) *
-                        T(1.0 / 3.36),
-                    dt);
-    // tau_xs = 1400/(sqrt(1+e)(1+e')) + 80
-    const T xsinf = T(1) / (T(1) + mexp((T(-5) - V) * T(1.0 / 14.0)));
-    const T sx = msqrt(T(1) + xm16 * T(kE5o6)) * (T(1) + mexp((V - T(35)) * T(1.0 / 15.0)));
-    un[8] = rl_rate(u[8], xsinf, sx / (T(1400) + T(80) * sx), dt);
-    const T rinf = T(1) / (T(1) + xm16 * T(kE20o6));
-    const T vr = V + T(40);
-    un[17] = rl_rate(u[17], rinf, T(1) / (T(9.5) * mexp(vr * vr * T(-1.0 / 1800.0)) + T(0.8)), dt);
-    T sinf, rs;
-    if (cell == 0) {
-      sinf = T(1) / (T(1) + x02 * T(kE5p6));
-      const T vs = V + T(67);
-      rs = T(1) / (T(1000) * mexp(vs * vs * T(-1.0 / 1000.0)) + T(8));
-    } else {
-      sinf = T(1) / (T(1) + x02 * T(kE4));
-      const T vs = V + T(45);
-      // tau_s = 85 e + 5/(1+e') + 3
-      const T es = T(1) + x02 * T(kEm4);
-      rs = es / ((T(85) * mexp(vs * vs * T(-1.0 / 320.0)) + T(3)) * es + T(5));
-    }
-    un[16] = rl_rate(u[16], sinf, rs, dt);
-    // tau_d = (1.4/(1+ea) + 0.25) * 1.4/(1+eb) + 1/(1+ec)
-    const T dinf = T(1) / (T(1) + mexp((T(-8) - V) * T(1.0 / 7.5)));
+    const T y15 = mexp(V * T(1.0 / 15.0));
+    // m: inf = 1/(1+e1)^2; 1/tau = (1 + e^-12/x02) eb ec / (0.1 (eb + ec))
+    //                            = (x02 + e^-12) eb ec / (0.1 x02 (eb + ec))
     {
+      const T e1 = T(1) + mexp((T(-56.86) - V) * T(1.0 / 9.03));
+      const T p1 = e1 * e1;
+      const T eb = T(1) + x02 * T(kE7);
+      const T ec = T(1) + mexp((V - T(50)) * T(1.0 / 200.0));
+      const T qm = T(0.1) * x02 * (eb + ec);
+      const T r = mrcp(p1 * qm);
+      un[9] = rl_rate(u[9], qm * r, (x02 + T(kEm12)) * eb * ec * p1 * r, dt);
+    }
+    // h and j: inf = 1/(1+e2)^2 for both; rates alpha + beta
+    {
+      const T e2 = T(1) + mexp((V + T(71.55)) * T(1.0 / 7.43));
+      const T p2 = e2 * e2;
+      T hinf, rh, rj;
+      if (V < T(-40)) {
+        rh = T(0.057) * mexp((V + T(80)) * T(-1.0 / 6.8)) + T(2.7) * mexp(T(0.079) * V) +
+             T(3.1e5) * mexp(T(0.3485) * V);
+        const T ja = T(1) + mexp(T(0.311) * (V + T(79.23)));
+        const T jb = T(1) + mexp(T(-0.1378) * (V + T(40.14)));
+        const T jab = ja * jb;
+        const T r = mrcp(p2 * jab);
+        hinf = jab * r;
+        rj = ((T(-2.5428e4) * mexp(T(0.2444) * V) - T(6.948e-6) * mexp(T(-0.04391) * V)) * (V + T(37.78)) * jb +
+              T(0.02424) * mexp(T(-0.01052) * V) * ja) *
+             p2 * r;
+      } else {
+        const T dh = T(1) + mexp((V + T(10.66)) * T(-1.0 / 11.1));
+        const T dj = T(1) + xm01 * T(kEm3p2);
+        const T dhj = dh * dj;
+        const T r = mrcp(p2 * dhj);
+        hinf = dhj * r;
+        rh = T(0.77 / 0.13) * p2 * dj * r;
+        rj = T(0.6) * mexp(T(0.057) * V) * p2 * dh * r;
+      }
+      un[10] = rl_rate(u[10], hinf, rh, dt);
+      un[11] = rl_rate(u[11], hinf, rj, dt);
+    }
+    // xr1 and xr2: xr1_inf = 1/(1 + e^(-26/7)/x17) = x17/(x17 + e^(-26/7)), xr2_inf = 1/(1+e);
+    // 1/tau_xr1 = (1+e)(1+e')/2700; 1/tau_xr2 = (1 + xm005 e^-3)(1 + e^-3/xm005)/3.36
+    //                                         = (1 + xm005 e^-3)(xm005 + e^-3)/(3.36 xm005)
+    {
+      const T a1 = x17 + T(kEm26o7);
+      const T b2 = T(1) + mexp((V + T(88)) * T(1.0 / 24.0));
+      const T a1b2 = a1 * b2;
+      const T r = mrcp(a1b2 * xm005);
+      un[6] = rl_rate(u[6], x17 * b2 * xm005 * r,
+                      (T(1) + xm01 * T(kEm4p5)) * (T(1) + mexp((V + T(30)) * T(1.0 / 11.5))) *
+                          T(1.0 / 2700.0),
+                      dt);
+      un[7] = rl_rate(u[7], a1 * xm005 * r,
+                      (T(1) + xm005 * T(kEm3)) * (xm005 + T(kEm3)) * a1b2 * r * T(1.0 / 3.36), dt);
+    }
+    // xs: tau = 1400/(sqrt(1+e)(1+e')) + 80, so 1/tau = sx/(1400 + 80 sx)
+    {
+      const T axs = T(1) + mexp((T(-5) - V) * T(1.0 / 14.0));
+      const T sx = msqrt(T(1) + xm16 * T(kE5o6)) * (T(1) + y15 * T(kEm35o15));
+      const T bxs = T(1400) + T(80) * sx;
+      const T r = mrcp(axs * bxs);
+      un[8] = rl_rate(u[8], bxs * r, sx * axs * r, dt);
+    }
+    // r: inf = 1/(1 + xm16 e^(20/6)), tau = 9.5 exp(-(V+40)^2/1800) + 0.8
+    {
+      const T vr = V + T(40);
+      const T ar = T(1) + xm16 * T(kE20o6);
+      const T br = T(9.5) * mexp(vr * vr * T(-1.0 / 1800.0)) + T(0.8);
+      const T r = mrcp(ar * br);
+      un[17] = rl_rate(u[17], br * r, ar * r, dt);
+    }
+    // s (endocardial: tau = 1000 exp(-(V+67)^2/1000) + 8; else tau = 85 e + 5/(1+e') + 3)
+    {
+      T as, bs, ns;
+      if (cell == 0) {
+        as = T(1) + x02 * T(kE5p6);
+        const T vs = V + T(67);
+        bs = T(1000) * mexp(vs * vs * T(-1.0 / 1000.0)) + T(8);
+        ns = T(1);
+      } else {
+        as = T(1) + x02 * T(kE4);
+        const T vs = V + T(45);
+        ns = T(1) + x02 * T(kEm4);
+        bs = (T(85) * mexp(vs * vs * T(-1.0 / 320.0)) + T(3)) * ns + T(5);
+      }
+      const T r = mrcp(as * bs);
+      un[16] = rl_rate(u[16], bs * r, ns * as * r, dt);
+    }
+    // d: inf = 1/(1 + e^(-8/7.5)/y15^2) = y15^2/(y15^2 + e^(-8/7.5));
+    // tau = (1.4/(1+ea) + 0.25) 1.4/(1+eb) + 1/(1+ec)
+    {
+      const T y2 = y15 * y15;
+      const T ad = y2 + T(kEm8o7p5);
       const T da = T(1) + mexp((T(-35) - V) * T(1.0 / 13.0));
       const T db = T(1) + x02 * T(kE1);
       const T dc = T(1) + xm005 * T(kE2p5);
-      un[12] = rl_rate(u[12], dinf, da * db * dc / ((T(1.4) + T(0.25) * da) * T(1.4) * dc + da * db), dt);
+      const T bd = (T(1.4) + T(0.25) * da) * T(1.4) * dc + da * db;
+      const T r = mrcp(ad * bd);
+      un[12] = rl_rate(u[12], y2 * bd * r, da * db * dc * ad * r, dt);
     }
-    // tau_f = 1102.5 e + 200/(1+ea) + 180/(1+eb) + 20
-    const T finf = T(1) / (T(1) + x17 * T(kE20o7));
-    const T vf27 = V + T(27);
+    // f and f2 share fb = 1 + exp((V+30)/10) = F/xm01 with F = xm01 + e^3;
+    // tau_f = 1102.5 g + 200/(1+ea) + 180/(1+fb) + 20, tau_f2 = 600 g' + 31/(1+ga) + 16/(1+fb)
+    const T F = xm01 + T(kE3);
     {
+      const T af = T(1) + x17 * T(kE20o7);
+      const T vf27 = V + T(27);
       const T fa = T(1) + xm01 * T(kE1p3);
-      const T fb = T(1) + x30;
-      const T num = (T(1102.5) * mexp(vf27 * vf27 * T(-1.0 / 225.0)) + T(20)) * fa * fb + T(200) * fb + T(180) * fa;
-      un[13] = rl_rate(u[13], finf, fa * fb / num, dt);
+      const T num = (T(1102.5) * mexp(vf27 * vf27 * T(-1.0 / 225.0)) + T(20)) * fa * F + T(200) * F +
+                    T(180) * fa * xm01;
+      const T r = mrcp(af * num);
+      un[13] = rl_rate(u[13], num * r, fa * F * af * r, dt);
     }
-    // tau_f2 = 600 e + 31/(1+ea) + 16/(1+eb)
-    const T f2inf = T(0.67) / (T(1) + x17 * T(kE5)) + T(0.33);
-    const T vf25 = V + T(25);
     {
+      const T af2 = T(1) + x17 * T(kE5);
+      const T vf25 = V + T(25);
       const T ga = T(1) + xm01 * T(kE2p5);
-      const T gb = T(1) + x30;
-      const T num = T(600) * mexp(vf25 * vf25 * T(-1.0 / 170.0)) * ga * gb + T(31) * gb + T(16) * ga;
-      un[14] = rl_rate(u[14], f2inf, ga * gb / num, dt);
+      const T num = T(600) * mexp(vf25 * vf25 * T(-1.0 / 170.0)) * ga * F + T(31) * F + T(16) * ga * xm01;
+      const T r = mrcp(af2 * num);
+      un[14] = rl_rate(u[14], T(0.67) * num * r + T(0.33), ga * F * af2 * r, dt);
     }
-    // fCass: inf = 0.6/(1+cs^2) + 0.4, tau = 80/(1+cs^2) + 2, cs = CaSS/0.05
-    const T cs = u[4] * T(20);
-    const T q = T(1) / (T(1) + cs * cs);
-    un[15] = rl_rate(u[15], T(0.6) * q + T(0.4), T(1) / (T(80) * q + T(2)), dt);
+    // fCass: inf = 0.6 q + 0.4, 1/tau = 1/(80 q + 2) = s2/(80 + 2 s2), q = 1/s2, s2 = 1 + (CaSS/0.05)^2
+    {
+      const T cs = u[4] * T(20);
+      const T s2 = T(1) + cs * cs;
+      const T b = T(80) + T(2) * s2;
+      const T r = mrcp(s2 * b);
+      un[15] = rl_rate(u[15], T(0.6) * (b * r) + T(0.4), s2 * s2 * r, dt);
+    }
   }
 #pragma unroll
   for (int j = 0; j < kTP06States; ++j) u[j] = un[j];
@@ -757,8 +835,8 @@ static __global__ void __launch_bounds__(256) exp_selftest_kernel(int64_t n, con
   exp2_table_init();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  y_fast[i] = fn ? log_tang(x[i]) : exp_tang(x[i]);
-  y_ref[i] = fn ? log(x[i]) : exp(x[i]);
+  y_fast[i] = fn == 2 ? rcp_nr(x[i]) : fn == 1 ? log_tang(x[i]) : exp_tang(x[i]);
+  y_ref[i] = fn == 2 ? 1.0 / x[i] : fn == 1 ? log(x[i]) : exp(x[i]);
 }
 
 }  // namespace tc

@@ -415,7 +415,6 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
       const T zv = __ldg(&a.dinv[row]) * rr;
       a.r[row] = rr;
       a.z[row] = zv;
-      a.p[row] = zv;
       rho_t = fmaT(rr, zv, rho_t);
       zz_t = fmaT(zv, zv, zz_t);
     }
@@ -441,17 +440,27 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   }
   __syncthreads();
   int flag = s_flag;
+  T beta = T(0);
   while (flag == 0 && it < a.max_iter) {
-    // q = A p, p^T q
+    // p = z + beta p and q = A p, formed as q = A z + beta q (A p_k = A z_k + beta A p_{k-1}):
+    // the product gathers z, complete since the last barrier, so p and q are updated row by row
+    // without a barrier of their own; then p^T q
     T pq_t = T(0);
     for (int s = s0 + warp; s < s1; s += NW) {
       const int beg = a.slice_ptr[s] + lane;
       const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
-      const T acc = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, a.p);
+      const T acc = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, a.z);
       const int64_t row = (int64_t)s * 32 + lane;
       if (row < a.n) {
-        a.q[row] = acc;
-        pq_t = fmaT(a.p[row], acc, pq_t);
+        const T zr = a.z[row];
+        T pn = zr, qn = acc;
+        if (it > 0) {
+          pn = fmaT(beta, a.p[row], zr);
+          qn = fmaT(beta, a.q[row], acc);
+        }
+        a.p[row] = pn;
+        a.q[row] = qn;
+        pq_t = fmaT(pn, qn, pq_t);
       }
     }
     {
@@ -528,18 +537,7 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
     }
     __syncthreads();
     flag = s_flag;
-    if (flag != 0) break;
-    const T beta = T(s_sc[2]);
-    for (int64_t i = r0 + tid; i < r1; i += 2 * THREADS) {
-      const int64_t i2 = i + THREADS;
-      const T p0 = a.p[i], z0 = a.z[i];
-      if (i2 < r1) {
-        const T p1 = a.p[i2], z1 = a.z[i2];
-        a.p[i2] = fmaT(beta, p1, z1);
-      }
-      a.p[i] = fmaT(beta, p0, z0);
-    }
-    if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
+    beta = T(s_sc[2]);
   }
   // activation capture (first upward crossing of thr) and, after activation, the peak, the
   // 90 % repolarisation crossing and the LRT crossing, each interpolated inside the step

@@ -92,6 +92,7 @@ _SIGS = {
     "tc_set_wait_limit": [_P, C.c_int64],
     "tc_selftest_exp": [_D, _D, _D, C.c_int64],
     "tc_selftest_log": [_D, _D, _D, C.c_int64],
+    "tc_selftest_rcp": [_D, _D, _D, C.c_int64],
     "tc_mlp_create": [C.c_uint64, C.POINTER(_P)],
     "tc_mlp_n_params": [_P, _I64],
     "tc_mlp_get_params": [_P, C.POINTER(C.c_float), C.c_int64],
@@ -501,6 +502,15 @@ def selftest_log(x):
     a = np.empty_like(x)
     b = np.empty_like(x)
     _check(lib().tc_selftest_log(_d(x), _d(a), _d(b), x.size))
+    return a, b
+
+
+def selftest_rcp(x):
+    """(device reciprocal used by the ionic kernels, IEEE 1.0 / x) at x."""
+    x = _f64(x)
+    a = np.empty_like(x)
+    b = np.empty_like(x)
+    _check(lib().tc_selftest_rcp(_d(x), _d(a), _d(b), x.size))
     return a, b
 
 

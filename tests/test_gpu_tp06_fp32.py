@@ -144,6 +144,19 @@ def test_device_exp_accuracy():
     assert np.isnan(tc.selftest_exp(np.array([np.nan]))[0][0])
 
 
+def test_device_reciprocal_accuracy():
+    # the FP64 reciprocal of the ionic kernels (hardware estimate refined by two Newton-Raphson
+    # steps): within 1 ulp of the correctly rounded 1/x (numpy's IEEE division) on every sample
+    # and within 1 ulp of the CUDA division, over the range its denominators take and beyond
+    rng = np.random.default_rng(2)
+    x = np.concatenate([10.0 ** rng.uniform(-30.0, 30.0, 400000), -(10.0 ** rng.uniform(-30.0, 30.0, 100000)),
+                        1.0 + rng.uniform(0.0, 1.0, 100000), [1.0, 2.0, 3.0, 0.1, 1e300, 1e-300]])
+    fast, ref = tc.selftest_rcp(x)
+    exact = 1.0 / x
+    assert np.all(np.abs(fast - exact) <= np.spacing(np.abs(exact)))
+    assert np.all(np.abs(fast - ref) <= np.spacing(np.abs(ref)))
+
+
 def test_device_log_accuracy():
     # the table-driven FP64 log of the ionic kernels: within 1 ulp of the exact value (mpmath,
     # 40 digits) on concentrations' ranges and well beyond, within 2 ulp of the CUDA library log;
