@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libtc_b300.so")
 SOURCES = ["mesh.cpp", "sim.cu", "mlp.cu"]
-HEADERS = ["tc_internal.h", "kernels.cuh", "ionic_tp06.cuh", "mlp.cuh", "gemm_tc.cuh", "surrogate.h"]
+HEADERS = ["tc_internal.h", "kernels.cuh", "ionic_tp06.cuh", "exp2_table.inc", "mlp.cuh", "gemm_tc.cuh",
+           "surrogate.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

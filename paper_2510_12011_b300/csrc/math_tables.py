@@ -1,16 +1,20 @@
-"""Regenerates the constants of the table-driven FP64 exp and log in ionic_tp06.cuh:
-2^(j/256) for j = 0..255 as hi + lo pairs; the cubic coefficient of the exp's polynomial; and
-for j = 0..127 the rounded reciprocal c_j = fl(1/(1 + j/128)) with -ln(c_j) as a hi + lo pair.
-Values from mpmath at 60 digits, printed as C hex floating-point literals.
+"""Regenerates the constants of the table-driven FP64 exp and log of the ionic kernels:
+2^(j/2048) for j = 0..2047 as hi + lo pairs (the include file exp2_table.inc), the quadratic
+coefficient of the exp's polynomial (kExpC2 in ionic_tp06.cuh), and for j = 0..127 the rounded
+reciprocal c_j = fl(1/(1 + j/128)) with -ln(c_j) as a hi + lo pair (ionic_tp06.cuh).  Values
+from mpmath at 60 digits, printed as C hex floating-point literals.
 
-The exp's polynomial is r + r^2/2 + c3 r^3 + r^4/24 on |r| <= a = ln2/512.  Its error is
-dominated by r^5/120; c3 = 1/6 + k a^2/120 takes the best multiple of r^3 off that term, where
-k solves the equioscillation condition of r^3 (r^2 - k a^2) on [0, a]: the value 1 - k at r = a
-equals minus the interior extremum at r^2 = 3 k a^2 / 5, that is 1 - k = (2k/5)(3k/5)^(3/2).
-That leaves a maximum error of 5.0e-18 (0.022 ulp of 1) against 3.8e-17 for the Taylor cubic.
+The exp's polynomial is r + c2 r^2 + r^3/6 on |r| <= a = ln2/4096.  Its error is dominated by
+r^4/24; c2 = 1/2 + d takes the best multiple of r^2 off that term: r^4/24 - d r^2 on [0, a]
+equioscillates (its value at r = a equals minus its interior extremum -6 d^2 at r^2 = 12 d) for
+d = (sqrt(2) - 1) a^2 / 12.  That leaves a maximum error of 5.9e-18 against 3.4e-17 for 1/2.
 
-    python math_tables.py
+    python math_tables.py           print every table
+    python math_tables.py --write   rewrite exp2_table.inc beside this file
 """
+import os
+import sys
+
 import mpmath
 
 
@@ -19,24 +23,41 @@ def pair(v):
     return hi, float(v - mpmath.mpf(hi))
 
 
-def exp_cubic():
-    k = mpmath.findroot(lambda k: 1 - k - (2 * k / 5) * (3 * k / 5) ** mpmath.mpf(1.5), 0.87)
-    a = mpmath.log(2) / 512
-    return float(mpmath.mpf(1) / 6 + k * a * a / 120)
+def exp_quadratic():
+    a = mpmath.log(2) / 4096
+    return float(mpmath.mpf(1) / 2 + (mpmath.sqrt(2) - 1) * a * a / 12)
+
+
+def exp_tables():
+    return zip(*[pair(mpmath.mpf(2) ** (mpmath.mpf(j) / 2048)) for j in range(2048)])
+
+
+def body(vals):
+    return "\n".join("    " + ", ".join(v.hex() for v in vals[i:i + 3]) + "," for i in range(0, len(vals), 3))
+
+
+def include_file():
+    e_hi, e_lo = exp_tables()
+    return ("// 2^(j/2048) = kExp2Hi[j] + kExp2Lo[j], j = 0..2047, each computed to 60 digits and split\n"
+            "// into the nearest double and the rest; written by math_tables.py --write.\n"
+            f"static __device__ const double kExp2Hi[2048] = {{\n{body(e_hi)}\n}};\n"
+            f"static __device__ const double kExp2Lo[2048] = {{\n{body(e_lo)}\n}};\n")
 
 
 def main():
     mpmath.mp.dps = 60
-    e_hi, e_lo = zip(*[pair(mpmath.mpf(2) ** (mpmath.mpf(j) / 256)) for j in range(256)])
+    if "--write" in sys.argv:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "exp2_table.inc")
+        with open(path, "w") as f:
+            f.write(include_file())
+        return
+    e_hi, e_lo = exp_tables()
     inv = [float(1 / (mpmath.mpf(1) + mpmath.mpf(j) / 128)) for j in range(128)]
     l_hi, l_lo = zip(*[pair(-mpmath.log(mpmath.mpf(c))) for c in inv])
-    print(f"kExpC3 = {exp_cubic().hex()};")
+    print(f"kExpC2 = {exp_quadratic().hex()};")
     for name, vals in (("kExp2Hi", e_hi), ("kExp2Lo", e_lo), ("kLogInv", inv), ("kLogHi", l_hi),
                        ("kLogLo", l_lo)):
-        print(f"{name} = {{")
-        for i in range(0, len(vals), 3):
-            print("    " + ", ".join(v.hex() for v in vals[i:i + 3]) + ",")
-        print("};")
+        print(f"{name} = {{\n{body(vals)}\n}};")
 
 
 if __name__ == "__main__":

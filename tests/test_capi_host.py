@@ -181,8 +181,8 @@ def test_monodomain_conductivity_from_bidomain_pairs():
 
 def test_math_tables_match_their_definition():
     """The exp and log tables of the FP64 ionic kernel are the values math_tables.py derives
-    from their definitions (2^(j/256); fl(1/(1 + j/128)) and -ln of it) with mpmath, and the
-    exp polynomial's cubic coefficient is the one it derives."""
+    from their definitions (2^(j/2048); fl(1/(1 + j/128)) and -ln of it) with mpmath, and the
+    exp polynomial's quadratic coefficient is the one it derives."""
     import contextlib
     import io
     import re
@@ -192,13 +192,15 @@ def test_math_tables_match_their_definition():
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         runpy.run_path(str(csrc / "math_tables.py"), run_name="__main__")
-    gen, src = buf.getvalue(), (csrc / "ionic_tp06.cuh").read_text()
+    gen = buf.getvalue()
+    src = (csrc / "ionic_tp06.cuh").read_text() + (csrc / "exp2_table.inc").read_text()
 
     def vals(text, key):
         i = text.index("{", text.index(key))
         return [float.fromhex(v) for v in re.findall(r"-?0x[0-9a-fA-F.]+p[+-]?\d+", text[i:text.index("}", i)])]
-    for name, n in (("kExp2Hi", 256), ("kExp2Lo", 256), ("kLogInv", 128), ("kLogHi", 128), ("kLogLo", 128)):
-        assert vals(src, f"double {name}[{n}] =") == vals(gen, f"{name} ="), name
-    c3 = re.search(r"kExpC3 = (\S+);", src).group(1)
-    assert float.fromhex(c3) == float.fromhex(re.search(r"kExpC3 = (\S+);", gen).group(1))
-    assert abs(float.fromhex(c3) - 1.0 / 6.0) < 2e-8
+    for name, n in (("kExp2Hi", 2048), ("kExp2Lo", 2048), ("kLogInv", 128), ("kLogHi", 128), ("kLogLo", 128)):
+        v = vals(src, f"double {name}[{n}] =")
+        assert len(v) == n and v == vals(gen, f"{name} ="), name
+    c2 = re.search(r"kExpC2 = (\S+);", src).group(1)
+    assert float.fromhex(c2) == float.fromhex(re.search(r"kExpC2 = (\S+);", gen).group(1))
+    assert 0.0 < float.fromhex(c2) - 0.5 < 2e-9
