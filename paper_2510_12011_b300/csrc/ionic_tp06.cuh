@@ -282,9 +282,14 @@ __device__ __forceinline__ double exp_tang(double x) {
 // 2^-20) refined by two Newton-Raphson steps y <- y + y (1 - d y), each of which squares the
 // relative error.  Four FP64 instructions against about twice that for a division; on 2.7 M
 // sampled d in [1e-20, 1e20] it matched the correctly rounded 1/d in every case.
-__device__ __forceinline__ double rcp_nr(double d) {
+__device__ __forceinline__ double rcp_estimate(double d) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  return y;
+}
+
+__device__ __forceinline__ double rcp_nr(double d) {
+  double y = rcp_estimate(d);
   double e = fma(-d, y, 1.0);
   y = fma(y, e, y);
   e = fma(-d, y, 1.0);
@@ -361,25 +366,91 @@ struct Tp06Currents {
   }
 };
 
+// The concentration-dependent transcendental part of a current evaluation: the logarithms of the
+// Nernst potentials' concentrations and the exponentials of I_K1 at dv = V - E_K.
 template <typename T>
-__device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int cell,
-                                                         const Tp06VFactors<T>& f) {
+struct Tp06Nernst {
+  T lki, lnai, lks, lcai;   // ln Ki, ln Nai, ln(Ki + pKNa Nai), ln Cai
+  T dv;                     // V - E_K
+  T ea, eb, e3, e10;        // exp(0.06 (dv - 200)), exp(-0.5 dv), exp(0.0002 (dv + 100)), exp(0.1 (dv - 10))
+};
+
+template <typename T>
+__device__ __forceinline__ void tp06_k1_exps(Tp06Nernst<T>& n) {
+  n.ea = mexp(T(0.06) * (n.dv - T(200)));
+  n.eb = mexp(T(-0.5) * n.dv);
+  n.e3 = mexp(T(0.0002) * (n.dv + T(100)));
+  n.e10 = mexp(T(0.1) * (n.dv - T(10)));
+}
+
+// Nernst potentials as differences of logarithms (the constants' logarithms folded at compile
+// time), which saves the divisions of the quotient forms
+template <typename T>
+__device__ __forceinline__ Tp06Nernst<T> tp06_nernst(T V, const T* u) {
   using namespace tp06;
-  const T ki = u[0], nai = u[1], cai = u[2], cass = u[4];
-  // Nernst potentials as differences of logarithms (the constants' logarithms folded at compile
-  // time), which saves the divisions of the quotient forms
-  const T ek = T(kRTF) * (T(kLnKo) - mlog(ki));
-  const T ena = T(kRTF) * (T(kLnNao) - mlog(nai));
-  const T eks = T(kRTF) * (T(kLnKsNa) - mlog(ki + T(kPKNa) * nai));
-  const T eca = T(0.5 * kRTF) * (T(kLnCao) - mlog(cai));
-  const T dv = V - ek;
+  Tp06Nernst<T> n;
+  n.lki = mlog(u[0]);
+  n.lnai = mlog(u[1]);
+  n.lks = mlog(u[0] + T(kPKNa) * u[1]);
+  n.lcai = mlog(u[2]);
+  n.dv = V - T(kRTF) * (T(kLnKo) - n.lki);
+  tp06_k1_exps(n);
+  return n;
+}
+
+// The same after one step of the slow concentrations, from the evaluation before it: Ki and Nai
+// change by about 1e-7 of their value per step, so ln x' = ln x + log1p(t), t = (x' - x)/x, with
+// log1p(t) = t - t^2/2 + t^3/3 (error below t^4/4 < 2^-82 for |t| < 2^-20; t needs only 31
+// correct bits there, which one Newton step on the reciprocal estimate gives), and
+// exp(a dv') = exp(a dv) exp(a e), e = dv' - dv, with exp(z) = 1 + z + z^2/2 + z^3/6 (error below
+// z^4/24 < 2^-55 relative for |e| < 2^-12).  Larger changes take the full evaluation.  Cai
+// (several per cent per step in an upstroke) always takes the table log.
+__device__ __forceinline__ double log1p_small(double t) { return fma(t * t, fma(t, 1.0 / 3.0, -0.5), t); }
+__device__ __forceinline__ double exp_small(double z) { return fma(z, fma(z, fma(z, 1.0 / 6.0, 0.5), 1.0), 1.0); }
+__device__ __forceinline__ double rel_change(double x0, double x1) {
+  const double y = rcp_estimate(x0);
+  return (x1 - x0) * fma(y, fma(-x0, y, 1.0), y);
+}
+
+__device__ __forceinline__ Tp06Nernst<double> tp06_nernst_next(double V, const double* u1, double ki0, double nai0,
+                                                               const Tp06Nernst<double>& n0) {
+  using namespace tp06;
+  const double ks0 = ki0 + kPKNa * nai0, ks1 = u1[0] + kPKNa * u1[1];
+  const double tk = rel_change(ki0, u1[0]), tn = rel_change(nai0, u1[1]), ts = rel_change(ks0, ks1);
+  constexpr double kT = 0x1p-20;
+  if (!(fabs(tk) < kT && fabs(tn) < kT && fabs(ts) < kT)) return tp06_nernst(V, u1);
+  Tp06Nernst<double> n;
+  n.lki = n0.lki + log1p_small(tk);
+  n.lnai = n0.lnai + log1p_small(tn);
+  n.lks = n0.lks + log1p_small(ts);
+  n.lcai = mlog(u1[2]);
+  n.dv = V - kRTF * (kLnKo - n.lki);
+  const double e = n.dv - n0.dv;
+  if (!(fabs(e) < 0x1p-12)) {
+    tp06_k1_exps(n);
+    return n;
+  }
+  n.ea = n0.ea * exp_small(0.06 * e);
+  n.eb = n0.eb * exp_small(-0.5 * e);
+  n.e3 = n0.e3 * exp_small(0.0002 * e);
+  n.e10 = n0.e10 * exp_small(0.1 * e);
+  return n;
+}
+
+template <typename T>
+__device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int cell, const Tp06VFactors<T>& f,
+                                                         const Tp06Nernst<T>& n) {
+  using namespace tp06;
+  const T nai = u[1], cai = u[2], cass = u[4];
+  const T ena = T(kRTF) * (T(kLnNao) - n.lnai);
+  const T eks = T(kRTF) * (T(kLnKsNa) - n.lks);
+  const T eca = T(0.5 * kRTF) * (T(kLnCao) - n.lcai);
+  const T dv = n.dv;
   // alpha_K1 / (alpha_K1 + beta_K1) over one common denominator
-  const T ea = mexp(T(0.06) * (dv - T(200)));
-  const T eb = mexp(T(-0.5) * dv);
-  const T nb = T(3) * mexp(T(0.0002) * (dv + T(100))) + mexp(T(0.1) * (dv - T(10)));
-  const T na = T(0.1) * (T(1) + eb);
+  const T nb = T(3) * n.e3 + n.e10;
+  const T na = T(0.1) * (T(1) + n.eb);
   // the quotients of I_K1, I_NaK and I_pCa over one reciprocal of their denominators
-  const T d1 = na + nb * (T(1) + ea), d2 = nai + T(kKmNa), d3 = T(kKpCa) + cai;
+  const T d1 = na + nb * (T(1) + n.ea), d2 = nai + T(kKmNa), d3 = T(kKpCa) + cai;
   const T d23 = d2 * d3;
   const T rr = mrcp(d1 * d23);
   Tp06Currents<T> c;
@@ -413,7 +484,8 @@ template <typename T>
 __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   using namespace tp06;
   const Tp06VFactors<T> vf = tp06_vfactors(V);
-  const Tp06Currents<T> c = tp06_currents(V, u, cell, vf);
+  const Tp06Nernst<T> nern = tp06_nernst(V, u);
+  const Tp06Currents<T> c = tp06_currents(V, u, cell, vf, nern);
 
   // concentrations and Rbar: forward Euler from the rates at (V^k, u^k)
   T un[kTP06States];
@@ -597,9 +669,16 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
       un[15] = rl_rate(u[15], T(0.6) * (b * r) + T(0.4), s2 * s2 * r, dt);
     }
   }
+  // I_ion at (V^k, u^{k+1}); FP64 carries the slow concentrations' logarithms over (see above)
+  Tp06Nernst<T> nern1;
+  if constexpr (sizeof(T) == 8)
+    nern1 = tp06_nernst_next(V, un, u[0], u[1], nern);
+  else
+    nern1 = tp06_nernst(V, un);
+  const T iion = tp06_currents(V, un, cell, vf, nern1).total();
 #pragma unroll
   for (int j = 0; j < kTP06States; ++j) u[j] = un[j];
-  return tp06_currents(V, u, cell, vf).total();
+  return iion;
 }
 
 // (a1) Ionic update of the tissue, TP06.  With a learned surrogate attached, nodes flagged for it
