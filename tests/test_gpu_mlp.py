@@ -86,6 +86,31 @@ def test_window_matches_oracle():
     assert np.allclose(got[:18].T, uw, rtol=1e-6, atol=1e-9)
 
 
+def test_window_with_fast_concentration_changes_matches_oracle():
+    """States whose Ki and Nai are small enough that a step changes them by more than 2^-20 of
+    their value take the full log and I_K1 evaluation at u^{k+1} (the FP64 step otherwise carries
+    the logarithms over from the evaluation at u^k); both kinds of node against the oracle."""
+    import torch
+    n = 96
+    V, u = otp06.rest(n)
+    V = np.linspace(-86.0, 20.0, n)
+    small = np.arange(n) % 2 == 1
+    u = u.copy()
+    u[small, 0] = 0.5 + 0.01 * np.arange(small.sum())     # Ki, mM
+    u[small, 1] = 0.05 + 0.001 * np.arange(small.sum())   # Nai, mM
+    inp = np.ascontiguousarray(np.concatenate([u.T, V[None, :]], axis=0), dtype=np.float32)
+    x = torch.tensor(inp, device="cuda")
+    out = torch.empty_like(x)
+    tc.tp06_window(x.data_ptr(), None, n, 0.02, 10, 2, tc.TC_FP64, out.data_ptr())
+    got = out.cpu().numpy().astype(np.float64)
+    uw, Vw = omlp.window(inp[:18].T.astype(np.float64), inp[18].astype(np.float64), np.zeros(n), 0.02, 10, 2)
+    # the small-Ki nodes do move fast: more than 2^-20 relative per step on Ki or Nai
+    rel = np.abs(uw[:, :2] - inp[:2].T) / inp[:2].T / 10
+    assert np.all(rel[small].max(axis=1) > 2.0 ** -20) and np.all(rel[~small, 0] < 2.0 ** -20)
+    assert np.allclose(got[18], Vw, rtol=1e-6, atol=1e-5)
+    assert np.allclose(got[:18].T, uw, rtol=1e-6, atol=1e-9)
+
+
 def test_short_training_reduces_loss():
     import torch
     rng = np.random.default_rng(7)
