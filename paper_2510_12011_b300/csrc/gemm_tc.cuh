@@ -157,8 +157,12 @@ __device__ __forceinline__ float tanh_approx(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// SiLU z sigmoid(z) with sigmoid(z) = (1 + tanh(z/2)) / 2: one special-function operation.
-__device__ __forceinline__ float silu_fast(float z) { return z * fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
+// SiLU z sigmoid(z) with sigmoid(z) = (1 + tanh(z/2)) / 2, as h + h tanh(h) with h = z/2: one
+// special-function operation and two FP32 instructions.
+__device__ __forceinline__ float silu_fast(float z) {
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_approx(h), h);
+}
 
 // Issue the bulk copies of one layer's weight image into sW (thread 0).
 __device__ __forceinline__ void load_weights(uint8_t* sW, const uint8_t* img, uint32_t bytes, uint64_t* bar) {
@@ -289,17 +293,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
           if (ch >= nch) break;
           const int c0 = cbeg + 32 * ch;
           float v[32];
+          const float4* b4 = reinterpret_cast<const float4*>(sBias + boff + c0);   // 16-byte aligned
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[ch][j]) + sBias[boff + c0 + j];
+          for (int j = 0; j < 32; j += 4) {
+            const float4 bb = b4[j >> 2];
+            v[j] = __uint_as_float(raw[ch][j]) + bb.x;
+            v[j + 1] = __uint_as_float(raw[ch][j + 1]) + bb.y;
+            v[j + 2] = __uint_as_float(raw[ch][j + 2]) + bb.z;
+            v[j + 3] = __uint_as_float(raw[ch][j + 3]) + bb.w;
+          }
           if (l + 1 < kMlpLayers) {
             if (STORE && valid && a.z[l]) {
               float* zp = a.z[l] + grow * N + c0;
 #pragma unroll
               for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(zp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             }
-            __align__(16) __nv_bfloat16 h[32];
+            __align__(16) __nv_bfloat162 h[16];   // column pairs, one conversion each
 #pragma unroll
-            for (int j = 0; j < 32; ++j) h[j] = __float2bfloat16(silu_fast(v[j]));
+            for (int j = 0; j < 16; ++j) h[j] = __floats2bfloat162_rn(silu_fast(v[2 * j]), silu_fast(v[2 * j + 1]));
             const int panel = c0 >> 6, chunk0 = (c0 & 63) >> 3;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
