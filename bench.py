@@ -222,8 +222,11 @@ def run_reference(args):
     budget = max(5.0, min(60.0, args.cpu_seconds * 2))
     cb = cpu_baseline(w, budget)
     steps = int(cb["sample"].split()[0])
+    # the oracle takes about a second per step of the full workload on one core: it times the
+    # steps that fit the CPU budget (reported as steps/warmup) rather than the K requested
     out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "node-steps/s",
            "n_gpus": args.gpus, "steps": steps, "warmup": 1,
+           "requested_steps": args.steps, "requested_warmup": args.warmup,
            "ms_per_step": 1e3 * w.mesh.n_nodes / cb["value"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w.name, "n_nodes": w.mesh.n_nodes, "dt_ms": w.dt,
