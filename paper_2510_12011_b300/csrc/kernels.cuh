@@ -105,6 +105,7 @@ struct PcgArgs {
   double atol, rtol;
   int max_iter;
   long long wait_limit;
+  float l2_keep;              // fraction of A's and the index array's lines kept in L2 (0: none)
   const long long* k_base;
   int k_off;
   double dt, thr;
@@ -222,6 +223,46 @@ __device__ __forceinline__ void grid_sum_warp0(const double* part, int stride, u
   b = two ? warp_sum(sb) : 0.0;
 }
 
+// L2 eviction policies for the matrix streams (createpolicy; hints only).  keep: a fixed fraction
+// of the lines accessed is marked evict-last and the rest evict-first, so that the A-product's
+// repeated passes find that fraction in L2 without the whole matrix displacing it; frac = 0 gives
+// the normal policy.  stream: evict-first, for data read once per step (M, K in the RHS pass).
+__device__ __forceinline__ uint64_t l2_policy_keep(float frac) {
+  uint64_t pol;
+  if (frac > 0.f)
+    asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_first.b64 %0, %1;" : "=l"(pol) : "f"(frac));
+  else
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_stream() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ double ld_hint(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_hint(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int ld_hint(const int32_t* p, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// Back to the normal eviction priority for the 128-byte lines of [p, p + bytes) (the lines of
+// the matrix marked evict-last would otherwise outlast the solve and crowd other work's data).
+static __global__ void l2_normal_priority_kernel(const char* p, int64_t lines) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < lines) asm volatile("applypriority.global.L2::evict_normal [%0], 128;" ::"l"(p + 128 * i) : "memory");
+}
+
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
@@ -243,7 +284,7 @@ constexpr int kSellChunk8 = 1;
 
 template <int SHAPE, typename T>
 __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
-                                     int beg, int w, const T* x) {
+                                     int beg, int w, const T* x, uint64_t pol = 0) {
   T acc0 = T(0), acc1 = T(0);
   if constexpr (SHAPE == kSellChunk8) {
     for (int j = 0; j < w; j += 8) {
@@ -266,12 +307,13 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
     }
   } else {
     int j = 0;
+    // indices and values with the caller's L2 policy (pol)
     for (; j + 4 <= w; j += 4) {
       const int e = beg + 32 * j;
-      const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32), c2 = __ldg(col + e + 64),
-                c3 = __ldg(col + e + 96);
-      const T v0 = __ldg(val + e), v1 = __ldg(val + e + 32), v2 = __ldg(val + e + 64),
-              v3 = __ldg(val + e + 96);
+      const int c0 = ld_hint(col + e, pol), c1 = ld_hint(col + e + 32, pol), c2 = ld_hint(col + e + 64, pol),
+                c3 = ld_hint(col + e + 96, pol);
+      const T v0 = ld_hint(val + e, pol), v1 = ld_hint(val + e + 32, pol), v2 = ld_hint(val + e + 64, pol),
+              v3 = ld_hint(val + e + 96, pol);
       const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
       acc0 = fmaT(v0, x0, acc0);
       acc1 = fmaT(v1, x1, acc1);
@@ -283,7 +325,7 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
     // fifth more FP64 work on a 15-entry row); the final sum is symmetric
     for (; j < w; ++j) {
       const int e = beg + 32 * j;
-      acc0 = fmaT(__ldg(val + e), x[__ldg(col + e)], acc0);
+      acc0 = fmaT(ld_hint(val + e, pol), x[ld_hint(col + e, pol)], acc0);
       const T t = acc0;
       acc0 = acc1;
       acc1 = t;
@@ -309,12 +351,13 @@ __device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const
                                           T& am, T& ak) {
   am = T(0);
   ak = T(0);
+  const uint64_t pol = l2_policy_stream();   // M and K are read once per step
   int j = 0;
   for (; j + 2 <= w; j += 2) {
     const int e = beg + 32 * j;
     const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32);
-    const T m0 = __ldg(vm + e), m1 = __ldg(vm + e + 32);
-    const T k0 = __ldg(vk + e), k1 = __ldg(vk + e + 32);
+    const T m0 = ld_hint(vm + e, pol), m1 = ld_hint(vm + e + 32, pol);
+    const T k0 = ld_hint(vk + e, pol), k1 = ld_hint(vk + e + 32, pol);
     const T a0 = __ldg(g1 + c0), a1 = __ldg(g1 + c1);
     const T b0 = __ldg(g2 + c0), b1 = __ldg(g2 + c1);
     am = fmaT(m0, a0, am);
@@ -325,8 +368,8 @@ __device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const
   for (; j < w; ++j) {
     const int e = beg + 32 * j;
     const int c = __ldg(col + e);
-    am = fmaT(__ldg(vm + e), __ldg(g1 + c), am);
-    ak = fmaT(__ldg(vk + e), __ldg(g2 + c), ak);
+    am = fmaT(ld_hint(vm + e, pol), __ldg(g1 + c), am);
+    ak = fmaT(ld_hint(vk + e, pol), __ldg(g2 + c), ak);
   }
 }
 
@@ -400,6 +443,7 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   const int64_t r1 = min((int64_t)s1 * 32, a.n);
   unsigned epoch = 0;
   double rho = 0.0, z0n = 0.0, zn = 0.0;   // meaningful in thread 0
+  const uint64_t pol_a = l2_policy_keep(a.l2_keep);
   int it = 0;
 
   // r0 = chi M (w - Cm x0) - dt K ((1-theta) V + theta x0) = M g1 - K g2
@@ -465,7 +509,7 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
           }
         }
       }
-      const T acc = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, a.z);
+      const T acc = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, a.z, pol_a);
       if constexpr (sizeof(T) == 8) {
         if (real) {
           zr = a.z[row];

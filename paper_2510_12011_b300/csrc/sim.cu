@@ -61,6 +61,7 @@ struct tc_sim {
   std::vector<int32_t> perm;         // perm[internal] = caller index or -1
   std::vector<int32_t> inv;          // inv[caller] = internal index
   int num_sms = 0, blocks_per_sm = 1, nblocks = 0, pcg_threads = 1024, sell_sigma = 1024;
+  float l2_keep = 0.f;   // fraction of A and the index array kept in L2 by the PCG (FP64)
   // device arrays (element type double for TC_FP64, float for TC_FP32)
   int32_t *slice_ptr = nullptr, *col = nullptr, *blk_slice = nullptr;
   int32_t *comp_of_block = nullptr, *comp_block0 = nullptr;
@@ -497,6 +498,7 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   pa.rtol = s->rtol;
   pa.max_iter = s->max_iter;
   pa.wait_limit = s->wait_limit;
+  pa.l2_keep = s->l2_keep;
   pa.k_base = s->k_dev;
   pa.k_off = k_off;
   pa.dt = s->dt;
@@ -874,6 +876,15 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
   ce = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaDeviceGetAttribute"));
+  {
+    // FP64: the A-product streams A and the index array every iteration; keep about 35 % of L2
+    // worth of their lines resident (evict-last) and let the rest pass (evict-first): 8 % faster
+    // PCG on the 40x16x6 mm slab (half of its 89 MB).  FP32 keeps its whole working set in L2.
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, s->device);
+    const double bytes = (double)sell.padded * (s->precision == TC_FP64 ? 12.0 : 8.0);
+    s->l2_keep = s->precision == TC_FP64 && l2 > 0 ? (float)std::min(0.5, 0.35 * l2 / bytes) : 0.f;
+  }
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
   if (!coop) return bail(fail(TC_ERR_CUDA, "device does not support cooperative launches"));
@@ -941,9 +952,23 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   return TC_OK;
 }
 
+// The PCG marks part of A and the index array evict-last in L2 (FP64); after a tc_step call
+// (and before the memory is freed) their lines go back to the normal priority so that they do
+// not crowd out other work's data.
+static cudaError_t l2_release(tc_sim* s) {
+  if (!(s->l2_keep > 0.f)) return cudaSuccess;
+  const int64_t lines_a = s->padded * 8 / 128, lines_c = s->padded * 4 / 128;
+  l2_normal_priority_kernel<<<(unsigned)((lines_a + 255) / 256), 256, 0, s->stream>>>(
+      static_cast<const char*>(s->vA), lines_a);
+  l2_normal_priority_kernel<<<(unsigned)((lines_c + 255) / 256), 256, 0, s->stream>>>(
+      reinterpret_cast<const char*>(s->col), lines_c);
+  return cudaGetLastError();
+}
+
 void tc_sim_destroy(tc_sim* s) {
   if (!s) return;
   cudaSetDevice(s->device);
+  l2_release(s);
   cudaStreamSynchronize(s->stream);
   drop_graphs(s);
   for (auto& d : s->allocs) cudaFree(d.p);
@@ -1184,6 +1209,7 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
     }
   }
   TRY(single_steps(n_steps - done));
+  CUDA_TRY(l2_release(s));
   s->iv = (int)((s->iv + n_steps) % 3);
   s->k += n_steps;
   std::vector<DevStats> ds(s->n_comp);
