@@ -38,10 +38,10 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 # profiles/ (sm__inst_executed_pipe_fp64.sum x 32 lanes / nodes); used to turn the live launch
 # time into an achieved FP64 instruction rate.
 TP06_FP64_INSTR_PER_NODE = 1050.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 110.92e6   # dram read + write of the same capture
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 110.80e6   # dram read + write of the same capture
 # dram read + write of one pcg_step_kernel<1024, double> launch on the large slab (ncu capture in
 # profiles/, a launch of a 23-step run averaging 8.65 CG iterations per launch)
-PCG_FP64_DRAM_BYTES_PER_LAUNCH = 1.298e9
+PCG_FP64_DRAM_BYTES_PER_LAUNCH = 0.641e9
 PCG_FP64_CAPTURE_ITERATIONS = 8.65
 
 
@@ -540,8 +540,8 @@ def run_ours(args):
                 "unit": "GB/s", "frac": pcg_gbs / peak,
                 "traffic": PCG_FP64_DRAM_BYTES_PER_LAUNCH if cap else None,
                 "traffic_note": (f"ncu dram bytes of one launch in a run averaging {PCG_FP64_CAPTURE_ITERATIONS} CG iterations "
-                                 f"(this run averages {iters:.2f}); the 4 MB node vectors partly stay in the "
-                                 "132.6 MB L2, the matrix streams from DRAM") if cap else None,
+                                 f"(this run averages {iters:.2f}); about half of A and its index array stays in the "
+                                 "132.6 MB L2 across iterations (evict-last fraction), the rest and M, K stream from DRAM") if cap else None,
                 "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": bytes_launch,
                 "avg_launch_ms": pcg_launch_ms}
     if prof["ionic_ms"] > prof["pcg_ms"] and w.model == "tp06" and TP06_FP64_INSTR_PER_NODE:
