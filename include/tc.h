@@ -269,6 +269,9 @@ tc_status tc_selftest_log(const double* x, double* y_fast, double* y_ref, int64_
 /* tc_selftest_rcp: the same for the FP64 reciprocal of the ionic kernels (hardware estimate and
  * two Newton-Raphson steps) against the IEEE division 1.0 / x.  x finite, nonzero and normal. */
 tc_status tc_selftest_rcp(const double* x, double* y_fast, double* y_ref, int64_t n);
+/* tc_selftest_exp2: the same for the base-2 FP64 exponential of the ionic kernels (table-driven,
+ * 2^y) against the CUDA library exp2. */
+tc_status tc_selftest_exp2(const double* x, double* y_fast, double* y_ref, int64_t n);
 
 /* ---- learned ionic surrogate --------------------------------------------------------
  * A multilayer perceptron (20 -> 4 x 256 SiLU -> 19; BF16 weights and activations, FP32

@@ -72,6 +72,9 @@ inline void tp06_rest_state(int /*cell*/, double* u, double* v0) {
 // half an ulp; 2^m is added to the exponent field.  Nine FP64 instructions; the range test runs
 // on the integer pipe (|x| >= 512, inf and NaN go to the library exp).
 constexpr double kExpC2 = 0x1.000000087db8cp-1;
+// base 2: 2^r - 1 = r (a1 + r (a2 + r a3)) on |r| <= 2^-12 (the polynomial above in s = r ln 2)
+constexpr double kExp2A1 = 0x1.62e42fefa39efp-1, kExp2A2 = 0x1.ebfbe0087dd4fp-3, kExp2A3 = 0x1.c6b08d704a0c0p-5;
+constexpr double kLog2e = 0x1.71547652b82fep+0;   // 1 / ln 2
 #include "exp2_table.inc"
 // Natural logarithm, table method (Tang 1990): for positive normal x = 2^e m, m in [1, 2), take
 // F = 1 + j/128 with j the top seven fraction bits of m and c = fl(1/F); then r = m c - 1 (one
@@ -278,6 +281,27 @@ __device__ __forceinline__ double exp_tang(double x) {
   return in_range ? out : exp(x);
 }
 
+// 2^y, the same table method in base 2: y = (2048 m + j)/2048 + r with |r| <= 2^-12 exactly (no
+// split constant: 2048 y and n/2048 are exact), 2^y = 2^m * 2^(j/2048) * 2^r.  Eight FP64
+// instructions.  The ionic kernel's exponentials exp(c x) are 2^((c log2 e) x) with the factor
+// folded into the constant c, so the change of base costs nothing at the call sites.  |y| >= 704,
+// inf and NaN go to the library exp2.
+__device__ __forceinline__ double exp2_tang(double y) {
+  constexpr double kShift = 6755399441055744.0;   // 1.5 * 2^52: round to nearest integer
+  const bool in_range = (__double2hiint(y) & 0x7fffffff) < 0x40860000;   // |y| < 704
+  const double t = fma(y, 2048.0, kShift);
+  const double nd = t - kShift;
+  const int n = __double2loint(t);
+  const double r = fma(-nd, 1.0 / 2048.0, y);
+  const double p = r * fma(r, fma(r, kExp2A3, kExp2A2), kExp2A1);
+  const double th = s_exp2_hi[n & 2047], tl = s_exp2_lo[n & 2047];
+  const double out0 = th + fma(th, p, tl);
+  const int m = n >> 11;
+  const double out =
+      __hiloint2double(__double2hiint(out0) + (int)((unsigned)m << 20), __double2loint(out0));
+  return in_range ? out : exp2(y);
+}
+
 // 1/d for a finite, nonzero, normal d: the hardware estimate (rcp.approx, relative error below
 // 2^-20) refined by two Newton-Raphson steps y <- y + y (1 - d y), each of which squares the
 // relative error.  Four FP64 instructions against about twice that for a division; on 2.7 M
@@ -298,6 +322,8 @@ __device__ __forceinline__ double rcp_nr(double d) {
 
 __device__ __forceinline__ double mexp(double x) { return exp_tang(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
+__device__ __forceinline__ double mexp2(double y) { return exp2_tang(y); }
+__device__ __forceinline__ float mexp2(float y) { return exp2f(y); }
 __device__ __forceinline__ double mlog(double x) { return log_tang(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
 __device__ __forceinline__ double mrcp(double x) { return rcp_nr(x); }
@@ -322,9 +348,9 @@ template <typename T>
 __device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
   using namespace tp06;
   Tp06VFactors<T> f;
-  const T vf = V * T(1.0 / kRTF);
-  const T q = mexp(-vf);                       // exp(-V F/RT)
-  const T eg = mexp(T(kGam) * vf);
+  const T vf2 = V * T(kLog2e / kRTF);         // V F/RT log2 e
+  const T q = mexp2(-vf2);                     // exp(-V F/RT)
+  const T eg = mexp2(T(kGam) * vf2);
   const T eg1 = eg * q;                        // exp((gamma - 1) V F/RT)
   const T vm = V - T(15);
   const T x = vm * T(2.0 / kRTF);
@@ -345,10 +371,10 @@ __device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
     f.ghk = T(-2 * kF * kCao);
   }
   // I_NaK, I_NaCa and I_pK factors: three quotients over one reciprocal of their denominators
-  const T dn = T(1) + T(0.1245) * mexp(T(-0.1) * vf) + T(0.0353) * q;
+  const T dn = T(1) + T(0.1245) * mexp2(T(-0.1) * vf2) + T(0.0353) * q;
   const T den = T((kKmNai * kKmNai * kKmNai + kNao * kNao * kNao) * (kKmCa + kCao)) *
                 (T(1) + T(kKsat) * eg1);
-  const T dp = T(1) + mexp((T(25) - V) * T(1.0 / 5.98));
+  const T dp = T(1) + mexp2((T(25) - V) * T(kLog2e / 5.98));
   const T rr = mrcp(dn * den * dp);
   f.nak = T(kPNaK * kKo / (kKo + kKmK)) * (den * dp * rr);
   const T rden = dn * dp * rr;
@@ -377,10 +403,10 @@ struct Tp06Nernst {
 
 template <typename T>
 __device__ __forceinline__ void tp06_k1_exps(Tp06Nernst<T>& n) {
-  n.ea = mexp(T(0.06) * (n.dv - T(200)));
-  n.eb = mexp(T(-0.5) * n.dv);
-  n.e3 = mexp(T(0.0002) * (n.dv + T(100)));
-  n.e10 = mexp(T(0.1) * (n.dv - T(10)));
+  n.ea = mexp2(T(0.06 * kLog2e) * (n.dv - T(200)));
+  n.eb = mexp2(T(-0.5 * kLog2e) * n.dv);
+  n.e3 = mexp2(T(0.0002 * kLog2e) * (n.dv + T(100)));
+  n.e10 = mexp2(T(0.1 * kLog2e) * (n.dv - T(10)));
 }
 
 // Nernst potentials as differences of logarithms (the constants' logarithms folded at compile
@@ -472,10 +498,10 @@ __device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int ce
 }
 
 // Rush-Larsen update of one gate, u_inf + (u - u_inf) exp(-dt/tau), with the gate's rate
-// 1/tau given (no division).
+// 1/tau given (no division) and dtl = dt log2 e (exp(-dt rate) = 2^(-dtl rate)).
 template <typename T>
-__device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dt) {
-  return inf + (u - inf) * mexp(-dt * rate);
+__device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dtl) {
+  return inf + (u - inf) * mexp2(-dtl * rate);
 }
 
 // One operator-split step of a single cell: u (18 states, in/out) advances from (V, u^k) to
@@ -535,81 +561,82 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   // multiplications by reciprocals.  Exponentials exp(a V + b) whose slope a is shared (or is
   // minus, or minus twice, a shared slope) are the shared exp(a V) times literal exp(b).
   {
-    const T x02 = mexp(T(0.2) * V);                  // exp(V/5)
-    const T xm01 = mexp(T(-0.1) * V);                // exp(-V/10)
-    const T xm16 = mexp(V * T(-1.0 / 6.0));
-    const T x17 = mexp(V * T(1.0 / 7.0));
-    const T xm005 = mexp(T(-0.05) * V);
-    const T y15 = mexp(V * T(1.0 / 15.0));
+    const T dtl = dt * T(kLog2e);
+    const T x02 = mexp2(T(0.2 * kLog2e) * V);                  // exp(V/5)
+    const T xm01 = mexp2(T(-0.1 * kLog2e) * V);                // exp(-V/10)
+    const T xm16 = mexp2(V * T(-kLog2e / 6.0));
+    const T x17 = mexp2(V * T(kLog2e / 7.0));
+    const T xm005 = mexp2(T(-0.05 * kLog2e) * V);
+    const T y15 = mexp2(V * T(kLog2e / 15.0));
     // m: inf = 1/(1+e1)^2; 1/tau = (1 + e^-12/x02) eb ec / (0.1 (eb + ec))
     //                            = (x02 + e^-12) eb ec / (0.1 x02 (eb + ec))
     {
-      const T e1 = T(1) + mexp((T(-56.86) - V) * T(1.0 / 9.03));
+      const T e1 = T(1) + mexp2((T(-56.86) - V) * T(kLog2e / 9.03));
       const T p1 = e1 * e1;
       const T eb = T(1) + x02 * T(kE7);
-      const T ec = T(1) + mexp((V - T(50)) * T(1.0 / 200.0));
+      const T ec = T(1) + mexp2((V - T(50)) * T(kLog2e / 200.0));
       const T qm = T(0.1) * x02 * (eb + ec);
       const T r = mrcp(p1 * qm);
-      un[9] = rl_rate(u[9], qm * r, (x02 + T(kEm12)) * eb * ec * p1 * r, dt);
+      un[9] = rl_rate(u[9], qm * r, (x02 + T(kEm12)) * eb * ec * p1 * r, dtl);
     }
     // h and j: inf = 1/(1+e2)^2 for both; rates alpha + beta
     {
-      const T e2 = T(1) + mexp((V + T(71.55)) * T(1.0 / 7.43));
+      const T e2 = T(1) + mexp2((V + T(71.55)) * T(kLog2e / 7.43));
       const T p2 = e2 * e2;
       T hinf, rh, rj;
       if (V < T(-40)) {
-        rh = T(0.057) * mexp((V + T(80)) * T(-1.0 / 6.8)) + T(2.7) * mexp(T(0.079) * V) +
-             T(3.1e5) * mexp(T(0.3485) * V);
-        const T ja = T(1) + mexp(T(0.311) * (V + T(79.23)));
-        const T jb = T(1) + mexp(T(-0.1378) * (V + T(40.14)));
+        rh = T(0.057) * mexp2((V + T(80)) * T(-kLog2e / 6.8)) + T(2.7) * mexp2(T(0.079 * kLog2e) * V) +
+             T(3.1e5) * mexp2(T(0.3485 * kLog2e) * V);
+        const T ja = T(1) + mexp2(T(0.311 * kLog2e) * (V + T(79.23)));
+        const T jb = T(1) + mexp2(T(-0.1378 * kLog2e) * (V + T(40.14)));
         const T jab = ja * jb;
         const T r = mrcp(p2 * jab);
         hinf = jab * r;
-        rj = ((T(-2.5428e4) * mexp(T(0.2444) * V) - T(6.948e-6) * mexp(T(-0.04391) * V)) * (V + T(37.78)) * jb +
-              T(0.02424) * mexp(T(-0.01052) * V) * ja) *
+        rj = ((T(-2.5428e4) * mexp2(T(0.2444 * kLog2e) * V) - T(6.948e-6) * mexp2(T(-0.04391 * kLog2e) * V)) * (V + T(37.78)) * jb +
+              T(0.02424) * mexp2(T(-0.01052 * kLog2e) * V) * ja) *
              p2 * r;
       } else {
-        const T dh = T(1) + mexp((V + T(10.66)) * T(-1.0 / 11.1));
+        const T dh = T(1) + mexp2((V + T(10.66)) * T(-kLog2e / 11.1));
         const T dj = T(1) + xm01 * T(kEm3p2);
         const T dhj = dh * dj;
         const T r = mrcp(p2 * dhj);
         hinf = dhj * r;
         rh = T(0.77 / 0.13) * p2 * dj * r;
-        rj = T(0.6) * mexp(T(0.057) * V) * p2 * dh * r;
+        rj = T(0.6) * mexp2(T(0.057 * kLog2e) * V) * p2 * dh * r;
       }
-      un[10] = rl_rate(u[10], hinf, rh, dt);
-      un[11] = rl_rate(u[11], hinf, rj, dt);
+      un[10] = rl_rate(u[10], hinf, rh, dtl);
+      un[11] = rl_rate(u[11], hinf, rj, dtl);
     }
     // xr1 and xr2: xr1_inf = 1/(1 + e^(-26/7)/x17) = x17/(x17 + e^(-26/7)), xr2_inf = 1/(1+e);
     // 1/tau_xr1 = (1+e)(1+e')/2700; 1/tau_xr2 = (1 + xm005 e^-3)(1 + e^-3/xm005)/3.36
     //                                         = (1 + xm005 e^-3)(xm005 + e^-3)/(3.36 xm005)
     {
       const T a1 = x17 + T(kEm26o7);
-      const T b2 = T(1) + mexp((V + T(88)) * T(1.0 / 24.0));
+      const T b2 = T(1) + mexp2((V + T(88)) * T(kLog2e / 24.0));
       const T a1b2 = a1 * b2;
       const T r = mrcp(a1b2 * xm005);
       un[6] = rl_rate(u[6], x17 * b2 * xm005 * r,
-                      (T(1) + xm01 * T(kEm4p5)) * (T(1) + mexp((V + T(30)) * T(1.0 / 11.5))) *
+                      (T(1) + xm01 * T(kEm4p5)) * (T(1) + mexp2((V + T(30)) * T(kLog2e / 11.5))) *
                           T(1.0 / 2700.0),
-                      dt);
+                      dtl);
       un[7] = rl_rate(u[7], a1 * xm005 * r,
-                      (T(1) + xm005 * T(kEm3)) * (xm005 + T(kEm3)) * a1b2 * r * T(1.0 / 3.36), dt);
+                      (T(1) + xm005 * T(kEm3)) * (xm005 + T(kEm3)) * a1b2 * r * T(1.0 / 3.36), dtl);
     }
     // xs: tau = 1400/(sqrt(1+e)(1+e')) + 80, so 1/tau = sx/(1400 + 80 sx)
     {
-      const T axs = T(1) + mexp((T(-5) - V) * T(1.0 / 14.0));
+      const T axs = T(1) + mexp2((T(-5) - V) * T(kLog2e / 14.0));
       const T sx = msqrt(T(1) + xm16 * T(kE5o6)) * (T(1) + y15 * T(kEm35o15));
       const T bxs = T(1400) + T(80) * sx;
       const T r = mrcp(axs * bxs);
-      un[8] = rl_rate(u[8], bxs * r, sx * axs * r, dt);
+      un[8] = rl_rate(u[8], bxs * r, sx * axs * r, dtl);
     }
     // r: inf = 1/(1 + xm16 e^(20/6)), tau = 9.5 exp(-(V+40)^2/1800) + 0.8
     {
       const T vr = V + T(40);
       const T ar = T(1) + xm16 * T(kE20o6);
-      const T br = T(9.5) * mexp(vr * vr * T(-1.0 / 1800.0)) + T(0.8);
+      const T br = T(9.5) * mexp2(vr * vr * T(-kLog2e / 1800.0)) + T(0.8);
       const T r = mrcp(ar * br);
-      un[17] = rl_rate(u[17], br * r, ar * r, dt);
+      un[17] = rl_rate(u[17], br * r, ar * r, dtl);
     }
     // s (endocardial: tau = 1000 exp(-(V+67)^2/1000) + 8; else tau = 85 e + 5/(1+e') + 3)
     {
@@ -617,28 +644,28 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
       if (cell == 0) {
         as = T(1) + x02 * T(kE5p6);
         const T vs = V + T(67);
-        bs = T(1000) * mexp(vs * vs * T(-1.0 / 1000.0)) + T(8);
+        bs = T(1000) * mexp2(vs * vs * T(-kLog2e / 1000.0)) + T(8);
         ns = T(1);
       } else {
         as = T(1) + x02 * T(kE4);
         const T vs = V + T(45);
         ns = T(1) + x02 * T(kEm4);
-        bs = (T(85) * mexp(vs * vs * T(-1.0 / 320.0)) + T(3)) * ns + T(5);
+        bs = (T(85) * mexp2(vs * vs * T(-kLog2e / 320.0)) + T(3)) * ns + T(5);
       }
       const T r = mrcp(as * bs);
-      un[16] = rl_rate(u[16], bs * r, ns * as * r, dt);
+      un[16] = rl_rate(u[16], bs * r, ns * as * r, dtl);
     }
     // d: inf = 1/(1 + e^(-8/7.5)/y15^2) = y15^2/(y15^2 + e^(-8/7.5));
     // tau = (1.4/(1+ea) + 0.25) 1.4/(1+eb) + 1/(1+ec)
     {
       const T y2 = y15 * y15;
       const T ad = y2 + T(kEm8o7p5);
-      const T da = T(1) + mexp((T(-35) - V) * T(1.0 / 13.0));
+      const T da = T(1) + mexp2((T(-35) - V) * T(kLog2e / 13.0));
       const T db = T(1) + x02 * T(kE1);
       const T dc = T(1) + xm005 * T(kE2p5);
       const T bd = (T(1.4) + T(0.25) * da) * T(1.4) * dc + da * db;
       const T r = mrcp(ad * bd);
-      un[12] = rl_rate(u[12], y2 * bd * r, da * db * dc * ad * r, dt);
+      un[12] = rl_rate(u[12], y2 * bd * r, da * db * dc * ad * r, dtl);
     }
     // f and f2 share fb = 1 + exp((V+30)/10) = F/xm01 with F = xm01 + e^3;
     // tau_f = 1102.5 g + 200/(1+ea) + 180/(1+fb) + 20, tau_f2 = 600 g' + 31/(1+ga) + 16/(1+fb)
@@ -647,18 +674,18 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
       const T af = T(1) + x17 * T(kE20o7);
       const T vf27 = V + T(27);
       const T fa = T(1) + xm01 * T(kE1p3);
-      const T num = (T(1102.5) * mexp(vf27 * vf27 * T(-1.0 / 225.0)) + T(20)) * fa * F + T(200) * F +
+      const T num = (T(1102.5) * mexp2(vf27 * vf27 * T(-kLog2e / 225.0)) + T(20)) * fa * F + T(200) * F +
                     T(180) * fa * xm01;
       const T r = mrcp(af * num);
-      un[13] = rl_rate(u[13], num * r, fa * F * af * r, dt);
+      un[13] = rl_rate(u[13], num * r, fa * F * af * r, dtl);
     }
     {
       const T af2 = T(1) + x17 * T(kE5);
       const T vf25 = V + T(25);
       const T ga = T(1) + xm01 * T(kE2p5);
-      const T num = T(600) * mexp(vf25 * vf25 * T(-1.0 / 170.0)) * ga * F + T(31) * F + T(16) * ga * xm01;
+      const T num = T(600) * mexp2(vf25 * vf25 * T(-kLog2e / 170.0)) * ga * F + T(31) * F + T(16) * ga * xm01;
       const T r = mrcp(af2 * num);
-      un[14] = rl_rate(u[14], T(0.67) * num * r + T(0.33), ga * F * af2 * r, dt);
+      un[14] = rl_rate(u[14], T(0.67) * num * r + T(0.33), ga * F * af2 * r, dtl);
     }
     // fCass: inf = 0.6 q + 0.4, 1/tau = 1/(80 q + 2) = s2/(80 + 2 s2), q = 1/s2, s2 = 1 + (CaSS/0.05)^2
     {
@@ -666,7 +693,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
       const T s2 = T(1) + cs * cs;
       const T b = T(80) + T(2) * s2;
       const T r = mrcp(s2 * b);
-      un[15] = rl_rate(u[15], T(0.6) * (b * r) + T(0.4), s2 * s2 * r, dt);
+      un[15] = rl_rate(u[15], T(0.6) * (b * r) + T(0.4), s2 * s2 * r, dtl);
     }
   }
   // I_ion at (V^k, u^{k+1}); FP64 carries the slow concentrations' logarithms over (see above)
@@ -737,8 +764,8 @@ static __global__ void __launch_bounds__(256) exp_selftest_kernel(int64_t n, con
   exp2_table_init();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  y_fast[i] = fn == 2 ? rcp_nr(x[i]) : fn == 1 ? log_tang(x[i]) : exp_tang(x[i]);
-  y_ref[i] = fn == 2 ? 1.0 / x[i] : fn == 1 ? log(x[i]) : exp(x[i]);
+  y_fast[i] = fn == 3 ? exp2_tang(x[i]) : fn == 2 ? rcp_nr(x[i]) : fn == 1 ? log_tang(x[i]) : exp_tang(x[i]);
+  y_ref[i] = fn == 3 ? exp2(x[i]) : fn == 2 ? 1.0 / x[i] : fn == 1 ? log(x[i]) : exp(x[i]);
 }
 
 }  // namespace tc

@@ -9,6 +9,10 @@ r^4/24; c2 = 1/2 + d takes the best multiple of r^2 off that term: r^4/24 - d r^
 equioscillates (its value at r = a equals minus its interior extremum -6 d^2 at r^2 = 12 d) for
 d = (sqrt(2) - 1) a^2 / 12.  That leaves a maximum error of 5.9e-18 against 3.4e-17 for 1/2.
 
+The base-2 form used by the ionic kernel evaluates 2^r - 1 on |r| <= 2^-12 as
+r (a1 + r (a2 + r a3)) with a1 = ln 2, a2 = c2 (ln 2)^2, a3 = (ln 2)^3 / 6: the same polynomial in
+s = r ln 2 (maximum error 5.9e-18).
+
     python math_tables.py           print every table
     python math_tables.py --write   rewrite exp2_table.inc beside this file
 """
@@ -26,6 +30,13 @@ def pair(v):
 def exp_quadratic():
     a = mpmath.log(2) / 4096
     return float(mpmath.mpf(1) / 2 + (mpmath.sqrt(2) - 1) * a * a / 12)
+
+
+def exp2_coefficients():
+    ln2 = mpmath.log(2)
+    a = ln2 / 4096
+    c2 = mpmath.mpf(1) / 2 + (mpmath.sqrt(2) - 1) * a * a / 12
+    return float(ln2), float(c2 * ln2 ** 2), float(ln2 ** 3 / 6)
 
 
 def exp_tables():
@@ -55,6 +66,8 @@ def main():
     inv = [float(1 / (mpmath.mpf(1) + mpmath.mpf(j) / 128)) for j in range(128)]
     l_hi, l_lo = zip(*[pair(-mpmath.log(mpmath.mpf(c))) for c in inv])
     print(f"kExpC2 = {exp_quadratic().hex()};")
+    a1, a2, a3 = exp2_coefficients()
+    print(f"kExp2A1 = {a1.hex()}, kExp2A2 = {a2.hex()}, kExp2A3 = {a3.hex()};")
     for name, vals in (("kExp2Hi", e_hi), ("kExp2Lo", e_lo), ("kLogInv", inv), ("kLogHi", l_hi),
                        ("kLogLo", l_lo)):
         print(f"{name} = {{\n{body(vals)}\n}};")

@@ -1624,6 +1624,10 @@ tc_status tc_selftest_rcp(const double* x, double* y_fast, double* y_ref, int64_
   return selftest_math(x, y_fast, y_ref, n, 2);
 }
 
+tc_status tc_selftest_exp2(const double* x, double* y_fast, double* y_ref, int64_t n) {
+  return selftest_math(x, y_fast, y_ref, n, 3);
+}
+
 const char* tc_version(void) { return "tc_b300 0.4 (sm_103a)"; }
 
 }  // extern "C"

@@ -93,6 +93,7 @@ _SIGS = {
     "tc_selftest_exp": [_D, _D, _D, C.c_int64],
     "tc_selftest_log": [_D, _D, _D, C.c_int64],
     "tc_selftest_rcp": [_D, _D, _D, C.c_int64],
+    "tc_selftest_exp2": [_D, _D, _D, C.c_int64],
     "tc_mlp_create": [C.c_uint64, C.POINTER(_P)],
     "tc_mlp_n_params": [_P, _I64],
     "tc_mlp_get_params": [_P, C.POINTER(C.c_float), C.c_int64],
@@ -511,6 +512,15 @@ def selftest_rcp(x):
     a = np.empty_like(x)
     b = np.empty_like(x)
     _check(lib().tc_selftest_rcp(_d(x), _d(a), _d(b), x.size))
+    return a, b
+
+
+def selftest_exp2(x):
+    """(device base-2 exponential used by the ionic kernels, CUDA library exp2) at x."""
+    x = _f64(x)
+    a = np.empty_like(x)
+    b = np.empty_like(x)
+    _check(lib().tc_selftest_exp2(_d(x), _d(a), _d(b), x.size))
     return a, b
 
 

@@ -204,3 +204,6 @@ def test_math_tables_match_their_definition():
     c2 = re.search(r"kExpC2 = (\S+);", src).group(1)
     assert float.fromhex(c2) == float.fromhex(re.search(r"kExpC2 = (\S+);", gen).group(1))
     assert 0.0 < float.fromhex(c2) - 0.5 < 2e-9
+    for name in ("kExp2A1", "kExp2A2", "kExp2A3"):
+        assert float.fromhex(re.search(name + r" = (0x[0-9a-fA-F.]+p[+-]?\d+)", src).group(1)) == \
+            float.fromhex(re.search(name + r" = (0x[0-9a-fA-F.]+p[+-]?\d+)", gen).group(1)), name

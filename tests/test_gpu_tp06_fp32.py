@@ -144,6 +144,27 @@ def test_device_exp_accuracy():
     assert np.isnan(tc.selftest_exp(np.array([np.nan]))[0][0])
 
 
+def test_device_exp2_accuracy():
+    # the base-2 FP64 exponential the TP06 kernel evaluates its exp(c x) with (as 2^((c log2 e) x)):
+    # within 1 ulp of the exact value (mpmath, 40 digits) on a sample, within 2 ulp of the CUDA
+    # library exp2 on half a million inputs, the library's result outside |y| < 704
+    import mpmath
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-90.0, 90.0, 400000), rng.uniform(-1074.0, 1023.0, 100000),
+                        np.linspace(-1e-3, 1e-3, 20001), [0.0, -0.0, 1.0, -1.0, 703.99, -703.99, 0.5]])
+    fast, ref = tc.selftest_exp2(x)
+    assert np.all(np.abs(fast - ref) <= 2.0 * np.spacing(np.abs(ref)) + 1e-300)
+    mpmath.mp.dps = 40
+    idx = rng.choice(x.size, 6000, replace=False)
+    worst = 0.0
+    for i in idx:
+        exact = mpmath.power(2, mpmath.mpf(float(x[i])))
+        ulp = np.spacing(abs(float(exact))) if exact != 0 else 5e-324
+        worst = max(worst, float(abs(mpmath.mpf(float(fast[i])) - exact)) / ulp)
+    assert worst <= 1.0, worst
+    assert fast[-1] == np.sqrt(2.0) or abs(fast[-1] - np.sqrt(2.0)) <= np.spacing(np.sqrt(2.0))
+
+
 def test_device_reciprocal_accuracy():
     # the FP64 reciprocal of the ionic kernels (hardware estimate refined by two Newton-Raphson
     # steps): within 1 ulp of the correctly rounded 1/x (numpy's IEEE division) on every sample
