@@ -221,8 +221,8 @@ static __constant__ double kLogLo[128] = {
     -0x1.bca7da80b6f7ep-55, -0x1.58376a5f4b135p-57,
 };
 
-static __shared__ double s_exp2_hi[2048];
-static __shared__ double s_exp2_lo[2048];
+// 2^(j/2048) as (hi, lo) pairs: one 16-byte shared-memory load per exponential
+static __shared__ double2 s_exp2[2048];
 static __shared__ double s_log_inv[128];
 static __shared__ double s_log_hi[128];
 static __shared__ double s_log_lo[128];
@@ -231,8 +231,7 @@ static __shared__ double s_log_lo[128];
 // log_tang, with every thread of the block).
 __device__ __forceinline__ void exp2_table_init() {
   for (int j = threadIdx.x; j < 2048; j += blockDim.x) {
-    s_exp2_hi[j] = kExp2Hi[j];
-    s_exp2_lo[j] = kExp2Lo[j];
+    s_exp2[j] = make_double2(kExp2Hi[j], kExp2Lo[j]);
   }
   for (int j = threadIdx.x; j < 128; j += blockDim.x) {
     s_log_inv[j] = kLogInv[j];
@@ -273,7 +272,8 @@ __device__ __forceinline__ double exp_tang(double x) {
   double r = fma(-nd, kLhi, x);
   r = fma(-nd, kLlo, r);
   const double p = fma(r * r, fma(r, 1.0 / 6.0, kExpC2), r);
-  const double th = s_exp2_hi[n & 2047], tl = s_exp2_lo[n & 2047];
+  const double2 tt = s_exp2[n & 2047];
+  const double th = tt.x, tl = tt.y;
   const double y = th + fma(th, p, tl);
   const int m = n >> 11;   // floor(n / 2048): n = 2048 m + (n & 2047)
   const double out =
@@ -294,7 +294,8 @@ __device__ __forceinline__ double exp2_tang(double y) {
   const int n = __double2loint(t);
   const double r = fma(-nd, 1.0 / 2048.0, y);
   const double p = r * fma(r, fma(r, kExp2A3, kExp2A2), kExp2A1);
-  const double th = s_exp2_hi[n & 2047], tl = s_exp2_lo[n & 2047];
+  const double2 tt = s_exp2[n & 2047];
+  const double th = tt.x, tl = tt.y;
   const double out0 = th + fma(th, p, tl);
   const int m = n >> 11;
   const double out =
