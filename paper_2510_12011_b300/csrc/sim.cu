@@ -459,10 +459,12 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
     marks->push_back((*ev)++);
   }
   const int ion_blocks = (int)((s->n_int + kIonicThreads - 1) / kIonicThreads);
-  if (s->model == TC_MODEL_MS)
+  if (s->model == TC_MODEL_MS) {
     ionic_ms_kernel<T><<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
-  else
-    ionic_tp06_kernel<T><<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
+  } else {
+    const int tpb = Tp06Launch<T>::threads;
+    ionic_tp06_kernel<T><<<(unsigned)((s->n_int + tpb - 1) / tpb), tpb, 0, s->stream>>>(ia);
+  }
   CUDA_TRY(cudaGetLastError());
   PcgArgs<T> pa;
   pa.n = s->n_int;
