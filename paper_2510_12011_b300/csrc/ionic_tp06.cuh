@@ -712,17 +712,18 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
 // (a1) Ionic update of the tissue, TP06.  With a learned surrogate attached, nodes flagged for it
 // carry the window's effective current instead (their states already hold the surrogate's
 // end-of-window prediction); all other nodes take the exact step.
-// Launch shape per precision.  FP64: 128-thread blocks, five per SM (20 warps, at most 102
-// registers), 2 % faster than two 256-thread blocks at 126 registers - the warps wait on FP64
-// results (short-scoreboard stalls), so more resident warps keep the FP64 pipe busier despite a
-// small spill.  FP32: 256-thread blocks, three per SM (the FP32 step was 10 % slower at 128 x 5).
+// Launch shape per precision (measured on the 40x16x6 mm slab).  FP64: 128-thread blocks, four
+// per SM (16 warps, 128 registers, no spill) - 2.5 % faster than two 256-thread blocks with the
+// same warps (finer blocks even out the SMs' share of the 1,000-instruction-per-node work); five
+// or six per SM (fewer registers, spills) were slower.  FP32: 256-thread blocks, three per SM
+// (10 % slower at 128 x 5).
 template <typename T>
 struct Tp06Launch {
   static constexpr int threads = 256, min_blocks = 3;
 };
 template <>
 struct Tp06Launch<double> {
-  static constexpr int threads = 128, min_blocks = 5;
+  static constexpr int threads = 128, min_blocks = 4;
 };
 
 template <typename T>
