@@ -714,8 +714,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
 // end-of-window prediction); all other nodes take the exact step.
 // Launch shape per precision (measured on the 40x16x6 mm slab).  FP64: 128-thread blocks, four
 // per SM (16 warps, 128 registers, no spill) - 2.5 % faster than two 256-thread blocks with the
-// same warps (finer blocks even out the SMs' share of the 1,000-instruction-per-node work); five
-// or six per SM (fewer registers, spills) were slower.  FP32: 256-thread blocks, three per SM
+// same warps; five or six per SM (fewer registers, spills) were slower.  FP32: 256-thread blocks, three per SM
 // (10 % slower at 128 x 5).
 template <typename T>
 struct Tp06Launch {
