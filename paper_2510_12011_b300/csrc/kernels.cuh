@@ -547,12 +547,13 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
     __syncthreads();
     const T alpha = T(s_sc[0]);
     // x += alpha p, r -= alpha q, z = D^-1 r, rho' = r^T z, ||z||^2.  Each thread takes rows
-    // i, i + THREADS, ... in that order (the same sums either way).  FP64: the loads of p, q, x, r
-    // for four rows are issued before their arithmetic (2.4 % faster PCG on the 40x16x6 mm
-    // slab); FP32: two rows per round (the four-row form was 5 % slower there).
+    // i, i + THREADS, ... in that order (the same sums either way).  FP64 and 1,024-thread FP32:
+    // the loads of p, q, x, r for four rows are issued before their arithmetic (FP64 PCG 2.4 %,
+    // FP32 1.6 % faster on the 40x16x6 mm slab); 512-thread FP32 (the batched form's shape): two
+    // rows per round (the four-row form was 10 % slower there).
     rho_t = T(0);
     zz_t = T(0);
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8 || THREADS == 1024) {
       for (int64_t i = r0 + tid; i < r1; i += 4 * THREADS) {
         T pv[4], qv[4], xv[4], rv[4];
 #pragma unroll
