@@ -563,11 +563,12 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   // minus, or minus twice, a shared slope) are the shared exp(a V) times literal exp(b).
   {
     const T dtl = dt * T(kLog2e);
-    const T x02 = mexp2(T(0.2 * kLog2e) * V);                  // exp(V/5)
-    const T xm01 = mexp2(T(-0.1 * kLog2e) * V);                // exp(-V/10)
+    // exp(-V/20), exp(-V/10) = its square, exp(V/5) = 1/exp(-V/10)^2: one exponential for three
+    const T xm005 = mexp2(T(-0.05 * kLog2e) * V);
+    const T xm01 = xm005 * xm005;                    // exp(-V/10)
+    const T x02 = mrcp(xm01 * xm01);                 // exp(V/5)
     const T xm16 = mexp2(V * T(-kLog2e / 6.0));
     const T x17 = mexp2(V * T(kLog2e / 7.0));
-    const T xm005 = mexp2(T(-0.05 * kLog2e) * V);
     const T y15 = mexp2(V * T(kLog2e / 15.0));
     // m: inf = 1/(1+e1)^2; 1/tau = (1 + e^-12/x02) eb ec / (0.1 (eb + ec))
     //                            = (x02 + e^-12) eb ec / (0.1 x02 (eb + ec))
