@@ -317,8 +317,8 @@ tc_status tc_mlp_diagnostics(const tc_mlp* mlp, tc_mlp_diag* out);
 tc_status tc_gemm_bf16_nt(const void* a_dev, const void* b_dev, float* c_dev, int32_t M, int32_t N, int32_t K,
                           void* cuda_stream);
 
-/* tc_tp06_window: the exact model over a window, for data generation and as the judge of the
- * surrogate: from in [19][n] (18 states then V, device FP32) and a constant stimulus istim [n]
+/* tc_tp06_window: the exact model over a window, for data generation and as the reference the
+ * surrogate is measured against: from in [19][n] (18 states then V, device FP32) and a constant stimulus istim [n]
  * (pA/pF, or NULL), nsub split steps of the single cell (Eq. 2 with V advanced by forward Euler);
  * out [19][n].  precision TC_FP64 or TC_FP32 arithmetic. */
 tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n, double dt, int32_t nsub,

@@ -938,7 +938,7 @@ tc_status tc_mlp_train(tc_mlp* m, const float* x_dev, const float* y_dev, int64_
   return status;
 }
 
-// Exact single-cell windows (the training targets and the judge of the surrogate):
+// Exact single-cell windows (the training targets and the reference the surrogate is checked against):
 // in [19][n] (18 states then V), istim [n] pA/pF or NULL, out [19][n]; device arrays, FP32
 // storage, arithmetic in FP64 (precision = TC_FP64) or FP32.
 tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n, double dt, int32_t nsub,
