@@ -325,6 +325,12 @@ __device__ __forceinline__ double mexp(double x) { return exp_tang(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
 __device__ __forceinline__ double mexp2(double y) { return exp2_tang(y); }
 __device__ __forceinline__ float mexp2(float y) { return exp2f(y); }
+// c x + d as one FMA (exponent arguments c (x + a) are written with d = a c folded at compile time)
+template <typename T>
+__device__ __forceinline__ T affine(T x, double c, double d) { return fmaT(x, T(c), T(d)); }
+// c (x + b)^2 = (c x + 2 b c) x + b^2 c: two FMAs
+template <typename T>
+__device__ __forceinline__ T gauss_arg(T x, double c, double b) { return fmaT(x, fmaT(x, T(c), T(2 * b * c)), T(b * b * c)); }
 __device__ __forceinline__ double mlog(double x) { return log_tang(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
 __device__ __forceinline__ double mrcp(double x) { return rcp_nr(x); }
@@ -375,7 +381,7 @@ __device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
   const T dn = T(1) + T(0.1245) * mexp2(T(-0.1) * vf2) + T(0.0353) * q;
   const T den = T((kKmNai * kKmNai * kKmNai + kNao * kNao * kNao) * (kKmCa + kCao)) *
                 (T(1) + T(kKsat) * eg1);
-  const T dp = T(1) + mexp2((T(25) - V) * T(kLog2e / 5.98));
+  const T dp = T(1) + mexp2(affine(V, -kLog2e / 5.98, 25 * kLog2e / 5.98));
   const T rr = mrcp(dn * den * dp);
   f.nak = T(kPNaK * kKo / (kKo + kKmK)) * (den * dp * rr);
   const T rden = dn * dp * rr;
@@ -404,10 +410,10 @@ struct Tp06Nernst {
 
 template <typename T>
 __device__ __forceinline__ void tp06_k1_exps(Tp06Nernst<T>& n) {
-  n.ea = mexp2(T(0.06 * kLog2e) * (n.dv - T(200)));
+  n.ea = mexp2(affine(n.dv, 0.06 * kLog2e, -200 * 0.06 * kLog2e));
   n.eb = mexp2(T(-0.5 * kLog2e) * n.dv);
-  n.e3 = mexp2(T(0.0002 * kLog2e) * (n.dv + T(100)));
-  n.e10 = mexp2(T(0.1 * kLog2e) * (n.dv - T(10)));
+  n.e3 = mexp2(affine(n.dv, 0.0002 * kLog2e, 100 * 0.0002 * kLog2e));
+  n.e10 = mexp2(affine(n.dv, 0.1 * kLog2e, -10 * 0.1 * kLog2e));
 }
 
 // Nernst potentials as differences of logarithms (the constants' logarithms folded at compile
@@ -573,24 +579,24 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     // m: inf = 1/(1+e1)^2; 1/tau = (1 + e^-12/x02) eb ec / (0.1 (eb + ec))
     //                            = (x02 + e^-12) eb ec / (0.1 x02 (eb + ec))
     {
-      const T e1 = T(1) + mexp2((T(-56.86) - V) * T(kLog2e / 9.03));
+      const T e1 = T(1) + mexp2(affine(V, -kLog2e / 9.03, -56.86 * kLog2e / 9.03));
       const T p1 = e1 * e1;
       const T eb = T(1) + x02 * T(kE7);
-      const T ec = T(1) + mexp2((V - T(50)) * T(kLog2e / 200.0));
+      const T ec = T(1) + mexp2(affine(V, kLog2e / 200.0, -50 * kLog2e / 200.0));
       const T qm = T(0.1) * x02 * (eb + ec);
       const T r = mrcp(p1 * qm);
       un[9] = rl_rate(u[9], qm * r, (x02 + T(kEm12)) * eb * ec * p1 * r, dtl);
     }
     // h and j: inf = 1/(1+e2)^2 for both; rates alpha + beta
     {
-      const T e2 = T(1) + mexp2((V + T(71.55)) * T(kLog2e / 7.43));
+      const T e2 = T(1) + mexp2(affine(V, kLog2e / 7.43, 71.55 * kLog2e / 7.43));
       const T p2 = e2 * e2;
       T hinf, rh, rj;
       if (V < T(-40)) {
-        rh = T(0.057) * mexp2((V + T(80)) * T(-kLog2e / 6.8)) + T(2.7) * mexp2(T(0.079 * kLog2e) * V) +
+        rh = T(0.057) * mexp2(affine(V, -kLog2e / 6.8, -80 * kLog2e / 6.8)) + T(2.7) * mexp2(T(0.079 * kLog2e) * V) +
              T(3.1e5) * mexp2(T(0.3485 * kLog2e) * V);
-        const T ja = T(1) + mexp2(T(0.311 * kLog2e) * (V + T(79.23)));
-        const T jb = T(1) + mexp2(T(-0.1378 * kLog2e) * (V + T(40.14)));
+        const T ja = T(1) + mexp2(affine(V, 0.311 * kLog2e, 79.23 * 0.311 * kLog2e));
+        const T jb = T(1) + mexp2(affine(V, -0.1378 * kLog2e, -40.14 * 0.1378 * kLog2e));
         const T jab = ja * jb;
         const T r = mrcp(p2 * jab);
         hinf = jab * r;
@@ -598,7 +604,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
               T(0.02424) * mexp2(T(-0.01052 * kLog2e) * V) * ja) *
              p2 * r;
       } else {
-        const T dh = T(1) + mexp2((V + T(10.66)) * T(-kLog2e / 11.1));
+        const T dh = T(1) + mexp2(affine(V, -kLog2e / 11.1, -10.66 * kLog2e / 11.1));
         const T dj = T(1) + xm01 * T(kEm3p2);
         const T dhj = dh * dj;
         const T r = mrcp(p2 * dhj);
@@ -614,11 +620,11 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     //                                         = (1 + xm005 e^-3)(xm005 + e^-3)/(3.36 xm005)
     {
       const T a1 = x17 + T(kEm26o7);
-      const T b2 = T(1) + mexp2((V + T(88)) * T(kLog2e / 24.0));
+      const T b2 = T(1) + mexp2(affine(V, kLog2e / 24.0, 88 * kLog2e / 24.0));
       const T a1b2 = a1 * b2;
       const T r = mrcp(a1b2 * xm005);
       un[6] = rl_rate(u[6], x17 * b2 * xm005 * r,
-                      (T(1) + xm01 * T(kEm4p5)) * (T(1) + mexp2((V + T(30)) * T(kLog2e / 11.5))) *
+                      (T(1) + xm01 * T(kEm4p5)) * (T(1) + mexp2(affine(V, kLog2e / 11.5, 30 * kLog2e / 11.5))) *
                           T(1.0 / 2700.0),
                       dtl);
       un[7] = rl_rate(u[7], a1 * xm005 * r,
@@ -626,7 +632,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     }
     // xs: tau = 1400/(sqrt(1+e)(1+e')) + 80, so 1/tau = sx/(1400 + 80 sx)
     {
-      const T axs = T(1) + mexp2((T(-5) - V) * T(kLog2e / 14.0));
+      const T axs = T(1) + mexp2(affine(V, -kLog2e / 14.0, -5 * kLog2e / 14.0));
       const T sx = msqrt(T(1) + xm16 * T(kE5o6)) * (T(1) + y15 * T(kEm35o15));
       const T bxs = T(1400) + T(80) * sx;
       const T r = mrcp(axs * bxs);
@@ -634,9 +640,8 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     }
     // r: inf = 1/(1 + xm16 e^(20/6)), tau = 9.5 exp(-(V+40)^2/1800) + 0.8
     {
-      const T vr = V + T(40);
       const T ar = T(1) + xm16 * T(kE20o6);
-      const T br = T(9.5) * mexp2(vr * vr * T(-kLog2e / 1800.0)) + T(0.8);
+      const T br = T(9.5) * mexp2(gauss_arg(V, -kLog2e / 1800.0, 40.0)) + T(0.8);
       const T r = mrcp(ar * br);
       un[17] = rl_rate(u[17], br * r, ar * r, dtl);
     }
@@ -645,14 +650,12 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
       T as, bs, ns;
       if (cell == 0) {
         as = T(1) + x02 * T(kE5p6);
-        const T vs = V + T(67);
-        bs = T(1000) * mexp2(vs * vs * T(-kLog2e / 1000.0)) + T(8);
+        bs = T(1000) * mexp2(gauss_arg(V, -kLog2e / 1000.0, 67.0)) + T(8);
         ns = T(1);
       } else {
         as = T(1) + x02 * T(kE4);
-        const T vs = V + T(45);
         ns = T(1) + x02 * T(kEm4);
-        bs = (T(85) * mexp2(vs * vs * T(-kLog2e / 320.0)) + T(3)) * ns + T(5);
+        bs = (T(85) * mexp2(gauss_arg(V, -kLog2e / 320.0, 45.0)) + T(3)) * ns + T(5);
       }
       const T r = mrcp(as * bs);
       un[16] = rl_rate(u[16], bs * r, ns * as * r, dtl);
@@ -662,7 +665,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     {
       const T y2 = y15 * y15;
       const T ad = y2 + T(kEm8o7p5);
-      const T da = T(1) + mexp2((T(-35) - V) * T(kLog2e / 13.0));
+      const T da = T(1) + mexp2(affine(V, -kLog2e / 13.0, -35 * kLog2e / 13.0));
       const T db = T(1) + x02 * T(kE1);
       const T dc = T(1) + xm005 * T(kE2p5);
       const T bd = (T(1.4) + T(0.25) * da) * T(1.4) * dc + da * db;
@@ -674,18 +677,16 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     const T F = xm01 + T(kE3);
     {
       const T af = T(1) + x17 * T(kE20o7);
-      const T vf27 = V + T(27);
       const T fa = T(1) + xm01 * T(kE1p3);
-      const T num = (T(1102.5) * mexp2(vf27 * vf27 * T(-kLog2e / 225.0)) + T(20)) * fa * F + T(200) * F +
+      const T num = (T(1102.5) * mexp2(gauss_arg(V, -kLog2e / 225.0, 27.0)) + T(20)) * fa * F + T(200) * F +
                     T(180) * fa * xm01;
       const T r = mrcp(af * num);
       un[13] = rl_rate(u[13], num * r, fa * F * af * r, dtl);
     }
     {
       const T af2 = T(1) + x17 * T(kE5);
-      const T vf25 = V + T(25);
       const T ga = T(1) + xm01 * T(kE2p5);
-      const T num = T(600) * mexp2(vf25 * vf25 * T(-kLog2e / 170.0)) * ga * F + T(31) * F + T(16) * ga * xm01;
+      const T num = T(600) * mexp2(gauss_arg(V, -kLog2e / 170.0, 25.0)) * ga * F + T(31) * F + T(16) * ga * xm01;
       const T r = mrcp(af2 * num);
       un[14] = rl_rate(u[14], T(0.67) * num * r + T(0.33), ga * F * af2 * r, dtl);
     }
