@@ -393,10 +393,10 @@ __device__ __forceinline__ Tp06VFactors<T> tp06_vfactors(T V) {
 
 template <typename T>
 struct Tp06Currents {
-  T ik1, ito, ikr, iks, ipk, ina, ibna, inak, inaca, ical, ibca, ipca;
-  __device__ __forceinline__ T total() const {
-    return ik1 + ito + ikr + iks + ina + ibna + ical + ibca + inak + inaca + ipca + ipk;
-  }
+  T ik;    // I_K1 + I_to + I_Kr + I_pK (all through V - E_K)
+  T ina;   // I_Na + I_bNa (both through V - E_Na)
+  T iks, inak, inaca, ical, ibca, ipca;
+  __device__ __forceinline__ T total() const { return ik + ina + iks + ical + ibca + inak + inaca + ipca; }
 };
 
 // The concentration-dependent transcendental part of a current evaluation: the logarithms of the
@@ -489,18 +489,19 @@ __device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int ce
   Tp06Currents<T> c;
   const T gto = cell == 0 ? T(0.073) : T(0.294);
   const T gks = cell == 1 ? T(0.098) : T(0.392);
-  c.ik1 = T(kGK1) * na * (d23 * rr) * dv;   // sqrt(Ko/5.4) = 1 at Ko = 5.4 mM
-  c.ito = gto * u[17] * u[16] * dv;
-  c.ikr = T(kGKr) * u[6] * u[7] * dv;
+  // the currents that share a driving force as one conductance sum times it: I_K1 (with
+  // sqrt(Ko/5.4) = 1 at Ko = 5.4 mM), I_to, I_Kr and I_pK through V - E_K; I_Na and I_bNa
+  // through V - E_Na
+  const T gk = fmaT(T(kGKr) * u[6], u[7], fmaT(gto * u[17], u[16], fmaT(T(kGK1) * na, d23 * rr, T(kGpK) * f.ipk)));
+  c.ik = gk * dv;
+  const T m = u[9];
+  c.ina = fmaT(T(kGNa) * m * m * m * u[10], u[11], T(kGbNa)) * (V - ena);
   c.iks = gks * u[8] * u[8] * (V - eks);
-  c.ina = T(kGNa) * u[9] * u[9] * u[9] * u[10] * u[11] * (V - ena);
-  c.ibna = T(kGbNa) * (V - ena);
   c.ical = T(kGCaL) * u[12] * u[13] * u[14] * u[15] * (f.ghk_cass * cass + f.ghk);
   c.ibca = T(kGbCa) * (V - eca);
   c.inak = f.nak * nai * (d1 * d3 * rr);
   c.inaca = f.naca_a * (nai * nai * nai) * T(kCao) - f.naca_b * cai;
   c.ipca = T(kGpCa) * cai * (d1 * d2 * rr);
-  c.ipk = T(kGpK) * f.ipk * dv;
   return c;
 }
 
@@ -547,8 +548,8 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
     const T fsr = bsr2 * (pa * dss * r2);
     const T fss = bss2 * (pa * dsr * r2);
     const T cvf = T(kCap / (kVc * kF));
-    const T dki = -(c.ik1 + c.ito + c.ikr + c.iks + c.ipk - T(2) * c.inak) * cvf;
-    const T dnai = -(c.ina + c.ibna + T(3) * c.inak + T(3) * c.inaca) * cvf;
+    const T dki = -(c.ik + c.iks - T(2) * c.inak) * cvf;
+    const T dnai = -(c.ina + T(3) * (c.inak + c.inaca)) * cvf;
     const T dcai = fi * ((ileak - iup) * T(kVsr / kVc) + ixfer -
                          (c.ibca + c.ipca - T(2) * c.inaca) * T(kCap / (2 * kVc * kF)));
     const T dcasr = fsr * (iup - (irel + ileak));
