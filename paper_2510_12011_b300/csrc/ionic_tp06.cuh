@@ -470,6 +470,46 @@ __device__ __forceinline__ Tp06Nernst<double> tp06_nernst_next(double V, const d
   return n;
 }
 
+// The same from logarithms held over from the previous step (lg: ln Ki, ln Nai, ln(Ki + pKNa Nai),
+// ln Cai of the current states, computed by tp06_nernst_next_direct at the end of that step).
+template <typename T>
+__device__ __forceinline__ Tp06Nernst<T> tp06_nernst_logs(T V, const T* lg) {
+  using namespace tp06;
+  Tp06Nernst<T> n;
+  n.lki = lg[0];
+  n.lnai = lg[1];
+  n.lks = lg[2];
+  n.lcai = lg[3];
+  n.dv = V - T(kRTF) * (T(kLnKo) - n.lki);
+  tp06_k1_exps(n);
+  return n;
+}
+
+// After the states' step: the logarithms directly (so that the next step can take them as they
+// are and still agree bit for bit with a step that computes them) and the I_K1 exponentials
+// carried over from the evaluation before the step when dv moved by less than 2^-12 (as in
+// tp06_nernst_next).
+__device__ __forceinline__ Tp06Nernst<double> tp06_nernst_next_direct(double V, const double* u1,
+                                                                      const Tp06Nernst<double>& n0) {
+  using namespace tp06;
+  Tp06Nernst<double> n;
+  n.lki = mlog(u1[0]);
+  n.lnai = mlog(u1[1]);
+  n.lks = mlog(u1[0] + kPKNa * u1[1]);
+  n.lcai = mlog(u1[2]);
+  n.dv = V - kRTF * (kLnKo - n.lki);
+  const double e = n.dv - n0.dv;
+  if (!(fabs(e) < 0x1p-12)) {
+    tp06_k1_exps(n);
+    return n;
+  }
+  n.ea = n0.ea * exp_small(0.06 * e);
+  n.eb = n0.eb * exp_small(-0.5 * e);
+  n.e3 = n0.e3 * exp_small(0.0002 * e);
+  n.e10 = n0.e10 * exp_small(0.1 * e);
+  return n;
+}
+
 template <typename T>
 __device__ __forceinline__ Tp06Currents<T> tp06_currents(T V, const T* u, int cell, const Tp06VFactors<T>& f,
                                                          const Tp06Nernst<T>& n) {
@@ -513,12 +553,14 @@ __device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dtl) {
 }
 
 // One operator-split step of a single cell: u (18 states, in/out) advances from (V, u^k) to
-// u^{k+1}; returns I_ion(V, u^{k+1}) in pA/pF.
+// u^{k+1}; returns I_ion(V, u^{k+1}) in pA/pF.  With lg (FP64), the four concentration
+// logarithms are held across steps: read from lg at the start when lg_valid, written to lg for
+// u^{k+1} at the end.
 template <typename T>
-__device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
+__device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = nullptr, bool lg_valid = false) {
   using namespace tp06;
   const Tp06VFactors<T> vf = tp06_vfactors(V);
-  const Tp06Nernst<T> nern = tp06_nernst(V, u);
+  const Tp06Nernst<T> nern = lg && lg_valid ? tp06_nernst_logs(V, lg) : tp06_nernst(V, u);
   const Tp06Currents<T> c = tp06_currents(V, u, cell, vf, nern);
 
   // concentrations and Rbar: forward Euler from the rates at (V^k, u^k)
@@ -702,10 +744,19 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt) {
   }
   // I_ion at (V^k, u^{k+1}); FP64 carries the slow concentrations' logarithms over (see above)
   Tp06Nernst<T> nern1;
-  if constexpr (sizeof(T) == 8)
-    nern1 = tp06_nernst_next(V, un, u[0], u[1], nern);
-  else
+  if constexpr (sizeof(T) == 8) {
+    if (lg) {
+      nern1 = tp06_nernst_next_direct(V, un, nern);
+      lg[0] = nern1.lki;
+      lg[1] = nern1.lnai;
+      lg[2] = nern1.lks;
+      lg[3] = nern1.lcai;
+    } else {
+      nern1 = tp06_nernst_next(V, un, u[0], u[1], nern);
+    }
+  } else {
     nern1 = tp06_nernst(V, un);
+  }
   const T iion = tp06_currents(V, un, cell, vf, nern1).total();
 #pragma unroll
   for (int j = 0; j < kTP06States; ++j) u[j] = un[j];
@@ -744,9 +795,21 @@ __global__ void __launch_bounds__(Tp06Launch<T>::threads, Tp06Launch<T>::min_blo
     T u[kTP06States];
 #pragma unroll
     for (int j = 0; j < kTP06States; ++j) u[j] = a.state[j * n + i];
-    iion = T(a.cm) * tp06_cell_step(V, u, a.cell, T(a.dt));
+    // the concentration logarithms of u^k, left by the previous step (FP64, when valid)
+    T lg[4];
+    const bool cache = a.log_cache != nullptr;
+    const bool valid = cache && *a.log_valid != 0;
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lg[q] = a.log_cache[q * n + i];
+    }
+    iion = T(a.cm) * tp06_cell_step(V, u, a.cell, T(a.dt), cache ? lg : nullptr, valid);
 #pragma unroll
     for (int j = 0; j < kTP06States; ++j) a.state[j * n + i] = u[j];
+    if (cache) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a.log_cache[q * n + i] = lg[q];
+    }
   }
   const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, *a.k_base + a.k_off));
   rhs_epilogue(a, i, V, Vp, iion, is);

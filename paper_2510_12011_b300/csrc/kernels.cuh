@@ -71,6 +71,8 @@ struct IonicArgs {
   int n_bar;              // follows on the stream
   const uint8_t* sur_flag;   // learned-surrogate nodes of the current window (or null)
   const float* sur_iion;     // their effective ionic current over the window, pA/pF
+  T* log_cache;              // TP06 FP64: [4][n] concentration logarithms of the states (or null)
+  const int* log_valid;      // nonzero: log_cache holds the logarithms of the current states
 };
 
 template <typename T>
@@ -106,6 +108,7 @@ struct PcgArgs {
   int max_iter;
   long long wait_limit;
   float l2_keep;              // fraction of A's and the index array's lines kept in L2 (0: none)
+  int* log_valid;             // set once the preceding ionic kernel has refreshed its log cache
   const long long* k_base;
   int k_off;
   double dt, thr;
@@ -444,6 +447,8 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   unsigned epoch = 0;
   double rho = 0.0, z0n = 0.0, zn = 0.0;   // meaningful in thread 0
   const uint64_t pol_a = l2_policy_keep(a.l2_keep);
+  // the ionic kernel launched before this one has left the logarithms of the new states
+  if (a.log_valid && b == 0 && tid == 0) *a.log_valid = 1;
   int it = 0;
 
   // r0 = chi M (w - Cm x0) - dt K ((1-theta) V + theta x0) = M g1 - K g2

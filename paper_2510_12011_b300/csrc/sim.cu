@@ -62,6 +62,11 @@ struct tc_sim {
   std::vector<int32_t> inv;          // inv[caller] = internal index
   int num_sms = 0, blocks_per_sm = 1, nblocks = 0, pcg_threads = 1024, sell_sigma = 1024;
   float l2_keep = 0.f;   // fraction of A and the index array kept in L2 by the PCG (FP64)
+  // TP06 FP64: the four concentration logarithms of the states, [4][n_int], left by each ionic
+  // launch for the next, and a device flag that says they match the states (set by the PCG
+  // launch after every ionic launch, cleared whenever the states are written from outside)
+  void* log_cache = nullptr;
+  int* log_valid = nullptr;
   // device arrays (element type double for TC_FP64, float for TC_FP32)
   int32_t *slice_ptr = nullptr, *col = nullptr, *blk_slice = nullptr;
   int32_t *comp_of_block = nullptr, *comp_block0 = nullptr;
@@ -452,6 +457,10 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   ia.n_bar = s->n_comp;
   ia.sur_flag = s->sur ? s->sur_flag : nullptr;
   ia.sur_iion = s->sur ? s->sur_iion : nullptr;
+  ia.log_cache = s->model == TC_MODEL_TP06 && s->precision == TC_FP64 && !s->sur && s->log_cache
+                     ? static_cast<T*>(s->log_cache)
+                     : nullptr;
+  ia.log_valid = s->log_valid;
   if (ev) {
     cudaEvent_t e = pooled_event(s, *ev);
     if (!e) return fail(TC_ERR_CUDA, "cudaEventCreate failed");
@@ -501,6 +510,7 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   pa.max_iter = s->max_iter;
   pa.wait_limit = s->wait_limit;
   pa.l2_keep = s->l2_keep;
+  pa.log_valid = ia.log_cache ? s->log_valid : nullptr;
   pa.k_base = s->k_dev;
   pa.k_off = k_off;
   pa.dt = s->dt;
@@ -1062,6 +1072,13 @@ tc_status tc_set_ionic(tc_sim* s, int32_t model, const double* params, int32_t n
     drop_graphs(s);
   }
   if (!s->state) TRY(dalloc_bytes(s, &s->state, (size_t)ns * s->n_int * s->esz));
+  if (model == TC_MODEL_TP06 && s->precision == TC_FP64 && !s->log_cache) {
+    TRY(dalloc_bytes(s, &s->log_cache, (size_t)4 * s->n_int * sizeof(double)));
+    void* flag = nullptr;
+    TRY(dalloc_bytes(s, &flag, sizeof(int)));
+    s->log_valid = static_cast<int*>(flag);
+  }
+  if (s->log_valid) CUDA_TRY(cudaMemsetAsync(s->log_valid, 0, sizeof(int), s->stream));
   s->model = model;
   s->n_states = ns;
   drop_graphs(s);   // model constants are baked into captured launches
@@ -1375,6 +1392,8 @@ tc_status tc_write_state(tc_sim* s, int32_t field, const double* src, int64_t n)
   CUDA_TRY(cudaStreamSynchronize(s->stream));   // the staging buffer may still feed a copy
   // nodes the learned surrogate holds for the current window restart on the exact model
   if (s->sur_flag) CUDA_TRY(cudaMemsetAsync(s->sur_flag, 0, s->n_int, s->stream));
+  // the held-over concentration logarithms no longer match the states
+  if (s->log_valid) CUDA_TRY(cudaMemsetAsync(s->log_valid, 0, sizeof(int), s->stream));
   return write_caller_field(s, dst, false, src);
 }
 
@@ -1498,6 +1517,7 @@ tc_status tc_autotune(tc_sim* s, int32_t trial_steps, int32_t* pcg_threads, int3
     }
     clear_error();
     for (auto& b : bufs) cudaMemcpy(b.dev, b.copy, b.bytes, cudaMemcpyDeviceToDevice);
+    if (s->log_valid) cudaMemsetAsync(s->log_valid, 0, sizeof(int), s->stream);   // the states went back
     s->k = k0;
     s->iv = iv0;
     s->thr_locked = thr_locked0;
