@@ -52,6 +52,56 @@ def test_tp06_fp64_parity_500_steps(tp06_runs):
     assert st["not_converged"] == 0
 
 
+def test_tp06_fp64_restart_and_autotune_are_bit_exact():
+    """The FP64 TP06 step holds the concentration logarithms of the states across steps; writing
+    the states (a checkpoint restart) or the autotuner's state restore drops them, and the step
+    that recomputes them must give the same bits as an uninterrupted run."""
+    w = _tp06_slab()
+    fields = [tc.TC_FIELD_V, tc.TC_FIELD_V_PREV] + [tc.TC_FIELD_STATE + j for j in range(18)]
+    ref = tc.from_workload(w)
+    ref.step(120)
+    a = tc.from_workload(w)
+    a.step(60)
+    saved = {f: a.read(f) for f in fields}
+    b = tc.from_workload(w)
+    for f, v in saved.items():
+        b.write(f, v)
+    b.step_index = a.step_index
+    b.step(60)
+    c = tc.from_workload(w)
+    c.step(60)
+    c.autotune(5)
+    lay = ref.layout()   # the reductions' block partition follows the launch shape: keep ref's
+    c.set_launch(lay["pcg_threads"], lay["blocks_per_sm"])
+    c.step(60)
+    for f in fields:
+        assert np.array_equal(b.read(f), ref.read(f)), f
+        assert np.array_equal(c.read(f), ref.read(f)), f
+
+
+def test_tp06_fp64_fast_concentration_changes_match_oracle():
+    """Half the nodes start with small Ki and Nai, so that a step changes them by more than 2^-20
+    of their value and moves E_K by more than 2^-12 mV: the I_K1 exponentials after the step take
+    the full evaluation there.  Against the oracle started from the same states."""
+    w = _tp06_slab()
+    o = Monodomain(w)
+    g = tc.from_workload(w)
+    n = w.mesh.n_nodes
+    small = np.arange(n) % 2 == 1
+    ki, nai = o.state[0].copy(), o.state[1].copy()
+    ki[small] = 0.5 + 0.001 * np.arange(small.sum())
+    nai[small] = 0.05 + 0.0001 * np.arange(small.sum())
+    o.state[0][:] = ki
+    o.state[1][:] = nai
+    g.write(tc.TC_FIELD_STATE + 0, ki)
+    g.write(tc.TC_FIELD_STATE + 1, nai)
+    o.run(20)
+    g.step(20)
+    assert np.abs(g.read() - o.V).max() <= 1e-8
+    for j in range(18):
+        assert np.allclose(g.read(tc.TC_FIELD_STATE + j), o.state[j], rtol=1e-10, atol=1e-14), j
+
+
 @pytest.mark.parametrize("model", ["ms", "tp06"])
 def test_fp32_form_against_fp64_oracle(model):
     w = I.slab_small_ms() if model == "ms" else _tp06_slab()
