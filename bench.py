@@ -37,8 +37,8 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 # FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
 # profiles/ (sm__inst_executed_pipe_fp64.sum x 32 lanes / nodes); used to turn the live launch
 # time into an achieved FP64 instruction rate.
-TP06_FP64_INSTR_PER_NODE = 925.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 141.79e6   # dram read + write of the same capture
+TP06_FP64_INSTR_PER_NODE = 918.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 141.53e6   # dram read + write of the same capture
 # dram read + write of one pcg_step_kernel<1024, double> launch on the large slab (ncu capture in
 # profiles/, a launch of a 23-step run averaging 8.65 CG iterations per launch)
 PCG_FP64_DRAM_BYTES_PER_LAUNCH = 0.637e9

@@ -552,6 +552,21 @@ __device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dtl) {
   return inf + (u - inf) * mexp2(-dtl * rate);
 }
 
+// The same for a slow gate, whose tau has a lower bound over every V (x_s 80 ms, f 98.8 ms, f2
+// 6.13 ms, the last at V = 8 mV): for dt <= 0.025 ms, z = dt/tau <= 4.1e-3 and exp(-z) is its
+// degree-5 Taylor polynomial (error below z^6/720 < 7e-18); other steps take the exponential.
+template <typename T>
+__device__ __forceinline__ T rl_rate_slow(T u, T inf, T rate, T dt, T dtl, bool short_step) {
+  T e;
+  if (short_step) {
+    const T z = dt * rate;
+    e = fmaT(z, fmaT(z, fmaT(z, fmaT(z, fmaT(z, T(-1.0 / 120.0), T(1.0 / 24.0)), T(-1.0 / 6.0)), T(0.5)), T(-1.0)), T(1.0));
+  } else {
+    e = mexp2(-dtl * rate);
+  }
+  return inf + (u - inf) * e;
+}
+
 // One operator-split step of a single cell: u (18 states, in/out) advances from (V, u^k) to
 // u^{k+1}; returns I_ion(V, u^{k+1}) in pA/pF.  With lg (FP64), the four concentration
 // logarithms are held across steps: read from lg at the start when lg_valid, written to lg for
@@ -612,6 +627,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = n
   // minus, or minus twice, a shared slope) are the shared exp(a V) times literal exp(b).
   {
     const T dtl = dt * T(kLog2e);
+    const bool short_step = dt <= T(0.025);
     // exp(-V/20), exp(-V/10) = its square, exp(V/5) = 1/exp(-V/10)^2: one exponential for three
     const T xm005 = mexp2(T(-0.05 * kLog2e) * V);
     const T xm01 = xm005 * xm005;                    // exp(-V/10)
@@ -679,7 +695,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = n
       const T sx = msqrt(T(1) + xm16 * T(kE5o6)) * (T(1) + y15 * T(kEm35o15));
       const T bxs = T(1400) + T(80) * sx;
       const T r = mrcp(axs * bxs);
-      un[8] = rl_rate(u[8], bxs * r, sx * axs * r, dtl);
+      un[8] = rl_rate_slow(u[8], bxs * r, sx * axs * r, dt, dtl, short_step);
     }
     // r: inf = 1/(1 + xm16 e^(20/6)), tau = 9.5 exp(-(V+40)^2/1800) + 0.8
     {
@@ -724,14 +740,14 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = n
       const T num = (T(1102.5) * mexp2(gauss_arg(V, -kLog2e / 225.0, 27.0)) + T(20)) * fa * F + T(200) * F +
                     T(180) * fa * xm01;
       const T r = mrcp(af * num);
-      un[13] = rl_rate(u[13], num * r, fa * F * af * r, dtl);
+      un[13] = rl_rate_slow(u[13], num * r, fa * F * af * r, dt, dtl, short_step);
     }
     {
       const T af2 = T(1) + x17 * T(kE5);
       const T ga = T(1) + xm01 * T(kE2p5);
       const T num = T(600) * mexp2(gauss_arg(V, -kLog2e / 170.0, 25.0)) * ga * F + T(31) * F + T(16) * ga * xm01;
       const T r = mrcp(af2 * num);
-      un[14] = rl_rate(u[14], T(0.67) * num * r + T(0.33), ga * F * af2 * r, dtl);
+      un[14] = rl_rate_slow(u[14], T(0.67) * num * r + T(0.33), ga * F * af2 * r, dt, dtl, short_step);
     }
     // fCass: inf = 0.6 q + 0.4, 1/tau = 1/(80 q + 2) = s2/(80 + 2 s2), q = 1/s2, s2 = 1 + (CaSS/0.05)^2
     {
