@@ -189,17 +189,16 @@ class ClockSampler:
 def cpu_baseline(w, seconds):
     """Time the FP64 oracle, as it stands, on a bounded number of steps of the same workload."""
     from oracle.monodomain import Monodomain
-    if True:
-        sim = Monodomain(w)        # assembly: not timed
-        t0 = time.perf_counter()
+    sim = Monodomain(w)        # assembly: not timed
+    t0 = time.perf_counter()
+    sim.step()
+    first = time.perf_counter() - t0
+    extra = max(0, int(seconds / max(first, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    for _ in range(extra):
         sim.step()
-        first = time.perf_counter() - t0
-        extra = max(0, int(seconds / max(first, 1e-6)) - 1)
-        t0 = time.perf_counter()
-        for _ in range(extra):
-            sim.step()
-        el = time.perf_counter() - t0
-        steps, total = (extra, el) if extra > 0 else (1, first)
+    el = time.perf_counter() - t0
+    steps, total = (extra, el) if extra > 0 else (1, first)
     model = None
     try:
         for line in open("/proc/cpuinfo"):
