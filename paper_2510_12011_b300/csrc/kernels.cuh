@@ -279,7 +279,8 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 //                also the FP32 PCG, whose working set stays in L2.
 //  kSellUnroll4  four entries per round, then the last w mod 4 one at a time; fewer live
 //                registers.  The FP64 PCG (1,024-thread blocks, 64 registers at most) runs 5 %
-//                faster with it than with kSellChunk8.
+//                faster with it than with kSellChunk8, and 2 % faster than with predicated
+//                rounds of four (a 15-entry row in four rounds, no entry loaded on its own).
 // Entries past a row's width are neither loaded nor added; the predicates are uniform across the
 // warp (one width per slice).
 constexpr int kSellUnroll4 = 0;
@@ -430,11 +431,12 @@ static __global__ void tick_kernel(long long* k_base, int add) { *k_base += add;
 // blocks and runs its own PCG (own barrier, reductions, alpha, beta, stopping decision), so a
 // batch of meshes advances in one launch without any instance waiting for another.
 template <int THREADS, typename T>
-__global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   constexpr int NW = THREADS / 32;
   __shared__ double s_red[2 * THREADS];
   __shared__ double s_sc[4];   // scalars computed by thread 0, then broadcast
   __shared__ int s_flag;       // 0 = iterate, 1 = converged, 2 = non-finite
+  __shared__ T s_part[THREADS];   // partial row products of a split last round
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned b = blockIdx.x;
   const int comp = a.comp_of_block[b];
@@ -490,12 +492,40 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
   __syncthreads();
   int flag = s_flag;
   T beta = T(0);
+  // The block's slices go to its warps in rounds of NW.  A short last round of R slices leaves
+  // NW - R warps idle while the others take whole slices (3 1/3 slices per warp on the
+  // 40x16x6 mm slab).  FP64: with R <= NW/2 each of those slices is split into G column ranges,
+  // one warp each, whose partial products are added in range order through shared memory (PCG
+  // launch 0.471 -> 0.462 ms on the slab).  FP32 keeps whole slices (the split was 2.6 % slower:
+  // its cheaper product does not pay for the extra block barrier).
+  const int n_sl = s1 - s0;
+  const int tail_r = n_sl % NW;
+  const int tail_g = tail_r == 0 ? 1 : min(NW / tail_r, 8);
+  const bool split = sizeof(T) == 8 && tail_g >= 2;
+  const int n_whole = split ? n_sl - tail_r : n_sl;
   while (flag == 0 && it < a.max_iter) {
     // p = z + beta p and q = A p, formed as q = A z + beta q (A p_k = A z_k + beta A p_{k-1}):
     // the product gathers z, complete since the last barrier, so p and q are updated row by row
     // without a barrier of their own; then p^T q
     T pq_t = T(0);
-    for (int s = s0 + warp; s < s1; s += NW) {
+    auto load_row = [&](int64_t row, T& zr, T& pr, T& qr) {
+      zr = a.z[row];
+      if (it > 0) {
+        pr = a.p[row];
+        qr = a.q[row];
+      }
+    };
+    auto store_row = [&](int64_t row, T acc, T zr, T pr, T qr) {
+      T pn = zr, qn = acc;
+      if (it > 0) {
+        pn = fmaT(beta, pr, zr);
+        qn = fmaT(beta, qr, acc);
+      }
+      a.p[row] = pn;
+      a.q[row] = qn;
+      pq_t = fmaT(pn, qn, pq_t);
+    };
+    for (int s = s0 + warp; s < s0 + n_whole; s += NW) {
       const int beg = a.slice_ptr[s] + lane;
       const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
       const int64_t row = (int64_t)s * 32 + lane;
@@ -506,33 +536,36 @@ __global__ void __launch_bounds__(THREADS) pcg_step_kernel(const PcgArgs<T> a) {
       // product would spill at 1,024 threads.
       T zr = T(0), pr = T(0), qr = T(0);
       if constexpr (sizeof(T) == 4) {
-        if (real) {
-          zr = a.z[row];
-          if (it > 0) {
-            pr = a.p[row];
-            qr = a.q[row];
-          }
-        }
+        if (real) load_row(row, zr, pr, qr);
       }
       const T acc = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, a.z, pol_a);
       if constexpr (sizeof(T) == 8) {
-        if (real) {
-          zr = a.z[row];
-          if (it > 0) {
-            pr = a.p[row];
-            qr = a.q[row];
-          }
-        }
+        if (real) load_row(row, zr, pr, qr);
       }
-      if (real) {
-        T pn = zr, qn = acc;
-        if (it > 0) {
-          pn = fmaT(beta, pr, zr);
-          qn = fmaT(beta, qr, acc);
+      if (real) store_row(row, acc, zr, pr, qr);
+    }
+    if (split) {
+      const int t = warp / tail_g, c = warp - t * tail_g;
+      const int s = s0 + n_whole + t;
+      const int64_t row = (int64_t)s * 32 + lane;
+      const bool real = t < tail_r && row < a.n;
+      T zr = T(0), pr = T(0), qr = T(0);
+      if (t < tail_r) {
+        const int beg = a.slice_ptr[s] + lane;
+        const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
+        const int per = (w + tail_g - 1) / tail_g;
+        const int j0 = min(w, c * per), j1 = min(w, j0 + per);
+        if constexpr (sizeof(T) == 4) {
+          if (c == 0 && real) load_row(row, zr, pr, qr);
         }
-        a.p[row] = pn;
-        a.q[row] = qn;
-        pq_t = fmaT(pn, qn, pq_t);
+        s_part[warp * 32 + lane] = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg + 32 * j0, j1 - j0, a.z, pol_a);
+      }
+      __syncthreads();
+      if (c == 0 && real) {
+        T acc = s_part[warp * 32 + lane];
+        for (int k = 1; k < tail_g; ++k) acc += s_part[(warp + k) * 32 + lane];
+        if constexpr (sizeof(T) == 8) load_row(row, zr, pr, qr);
+        store_row(row, acc, zr, pr, qr);
       }
     }
     {

@@ -136,6 +136,22 @@ def test_tiny_meshes(n_tets):
     assert np.abs(g.activation_times() - o.act).max() <= ACT_TOL
 
 
+@pytest.mark.parametrize("dims", [(2.0, 1.0, 1.0), (3.0, 2.0, 1.0), (4.0, 2.0, 1.5), (5.0, 3.0, 1.5)])
+def test_few_slice_meshes(dims):
+    """Meshes of 2 to 10 SELL slices (45 to 308 nodes, the last slice ragged): one PCG block whose
+    only round of slices is short, so every slice's row product is split over several warps by
+    column range (8, 8, 5 and 3 warps per slice) and added back through shared memory."""
+    m = I.slab_mesh(*dims, 0.5, jitter=0.15, seed=3)
+    w = I.Workload("few_slices", m, 0.17, 0.019, 140.0, 0.01, 0.5, 0.01, 1.0, "ms",
+                   stimuli=[I.Stimulus(I.corner_nodes(m, 0.5), 0.0, 0.5, 2.0)],
+                   atol=0.0, rtol=1e-10, max_iter=1000)
+    o = Monodomain(w).run(300)
+    g = _sim(w)
+    g.step(300)
+    assert np.abs(g.read() - o.V).max() <= V_TOL
+    assert np.abs(g.activation_times() - o.act).max() <= ACT_TOL
+
+
 def test_iteration_cap_and_zero_residual():
     w = I.slab_small_ms()
     g = _sim(w)
