@@ -308,8 +308,8 @@ tc_status upload_stimuli(tc_sim* s) {
 
 template <typename T>
 const void* pcg_kernel_ptr(int threads) {
-  return threads == 1024 ? (const void*)pcg_step_kernel<1024, T>
-                         : (const void*)pcg_step_kernel<512, T>;
+  return threads == 1024 ? (const void*)pcg_step_kernel_1024<T>
+                         : (const void*)pcg_step_kernel_512<T>;
 }
 
 const void* pcg_kernel(const tc_sim* s) {
