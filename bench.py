@@ -39,7 +39,7 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 # time into an achieved FP64 instruction rate.
 TP06_FP64_INSTR_PER_NODE = 918.0
 TP06_FP64_DRAM_BYTES_PER_LAUNCH = 141.53e6   # dram read + write of the same capture
-# dram read + write of one pcg_step_kernel<1024, double> launch on the large slab (ncu capture in
+# dram read + write of one pcg_step_kernel_1024<double> launch on the large slab (ncu capture in
 # profiles/, a launch of a 23-step run averaging 8.65 CG iterations per launch)
 PCG_FP64_DRAM_BYTES_PER_LAUNCH = 0.637e9
 PCG_FP64_CAPTURE_ITERATIONS = 8.65
