@@ -79,6 +79,24 @@ def test_single_cell_reduction_converges_first_order():
     assert 1.6 < r1 < 2.4 and 1.6 < r2 < 2.4
 
 
+def test_ms_upper_fixed_point():
+    """With the gate held open (tau_close -> infinity) a stimulated cell settles where
+    h v (1 - v) / tau_in = v / tau_out with h = 1: v* = (1 + sqrt(1 - 4 tau_in / tau_out)) / 2
+    (0.947 for the default constants).  Forward Euler keeps the ODE's fixed points, so the
+    decoupled monodomain step reaches V* = V_min + (V_max - V_min) v* to rounding."""
+    w = I.slab_custom(1.0, 1.0, 1.0, 0.5, dt=0.01, rtol=1e-14, t_end=60.0, stim_mm=0.0)
+    w.sigma_l = w.sigma_t = 0.0
+    w.ms = I.MSParams(tau_close=1e12)
+    w.stimuli = [I.Stimulus(np.array([0], dtype=np.int32), 0.0, 1.0, 0.5)]
+    s = Monodomain(w)
+    for _ in range(w.n_steps):
+        s.step()
+    v_star = (1.0 + np.sqrt(1.0 - 4.0 * P.tau_in / P.tau_out)) / 2.0
+    assert abs(v_star - 0.9472135955) < 1e-10
+    assert abs(s.V[0] - (-80.0 + 100.0 * v_star)) < 1e-8
+    assert np.allclose(s.V[1:], -80.0, rtol=0, atol=1e-10)
+
+
 def test_stimulus_window():
     nodes = np.array([1, 3], dtype=np.int32)
     st = [I.Stimulus(nodes, 0.5, 2.0, 0.7), I.Stimulus(np.array([3]), 1.0, 0.05, 0.1)]
