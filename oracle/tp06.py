@@ -14,6 +14,14 @@ Time step (operator splitting as Eq. 2 and the paragraph after it read):
   * concentrations 0..4 and Rbar advance by forward Euler;
   * the current returned is I_ion(V^k, u^{k+1}).
 The stimulus current is not added to Ki (in tissue it enters through the PDE source).
+
+The f2 gate's time constant is taken in the form
+    tau_f2 = 562 exp(-(V+27)^2/240) + 31/(1 + exp((25-V)/10)) + 80/(1 + exp((V+30)/10)),
+the one under which the publication's initial state (REST_U, REST_V) is the end-diastolic
+state of the epicardial cell paced at a 550 ms cycle: every gate and V return to their
+printed values after a beat.  The variant 600 exp(-(V+25)^2/170) + 31/(...) + 16/(...) leaves
+f2 at 0.9995 at the end of every diastole (tau ~16 ms at rest) and cannot reproduce the
+printed 0.9755 at any cycle length.
 """
 import numpy as np
 
@@ -127,8 +135,8 @@ def gate_inf_tau(V, u, cell):
     tau[F] = 1102.5 * np.exp(-(V + 27.0) ** 2 / 225.0) + 200.0 / (1.0 + np.exp((13.0 - V) / 10.0)) + \
         180.0 / (1.0 + np.exp((V + 30.0) / 10.0)) + 20.0
     inf[F2] = 0.67 / (1.0 + np.exp((V + 35.0) / 7.0)) + 0.33
-    tau[F2] = 600.0 * np.exp(-(V + 25.0) ** 2 / 170.0) + 31.0 / (1.0 + np.exp((25.0 - V) / 10.0)) + \
-        16.0 / (1.0 + np.exp((V + 30.0) / 10.0))
+    tau[F2] = 562.0 * np.exp(-(V + 27.0) ** 2 / 240.0) + 31.0 / (1.0 + np.exp((25.0 - V) / 10.0)) + \
+        80.0 / (1.0 + np.exp((V + 30.0) / 10.0))
     cs = (u[:, CASS] / 0.05) ** 2
     inf[FCASS] = 0.6 / (1.0 + cs) + 0.4
     tau[FCASS] = 80.0 / (1.0 + cs) + 2.0

@@ -1,12 +1,15 @@
 """Pins of the oracle's ten Tusscher-Panfilov 2006 model.
 
 The paper names the model (Section 2.2) but prints none of it, so the equations are pinned by
-(1) an exact identity of the model: the total membrane charge balance, which ties every current
-to its ionic fluxes; (2) the Rush-Larsen closed form of the gates at a frozen potential;
-(3) first-order convergence of the split step to an accurate ODE solution; and (4) published
-action-potential features of the model (resting potential, overshoot, APD90 ordering and
-range of the three cell types) as bands.  The individual rate constants are otherwise
-unpinned against the paper."""
+(1) the model publication's printed initial state: the gates whose time constant at rest is a
+few ms or less (m, h, d, r, x_r2, and s outside the endocardium) sit at their steady states there,
+and the whole state (V, all 18 variables) is the end-diastolic state of the epicardial cell paced
+at a 550 ms cycle, which ties every gate's steady state and time constant and every flux to the
+printed values; (2) an exact identity of the model: the total membrane charge balance, which
+ties every current to its ionic fluxes; (3) the Rush-Larsen closed form of the gates at a frozen
+potential; (4) first-order convergence of the split step to an accurate ODE solution; and
+(5) action-potential features (resting potential, overshoot, APD90 ordering of the three cell
+types) as bands."""
 import numpy as np
 import pytest
 from scipy.integrate import solve_ivp
@@ -54,6 +57,117 @@ def test_rest_is_near_equilibrium():
     for cell in (0, 1, 2):
         dv, du = T.derivatives(V[:1], u[:1], cell)
         assert abs(dv[0]) < 0.01
+
+
+# Gates whose time constant at the published resting potential is at most ~8 ms are at their
+# steady state in the printed initial state.  Tolerance per gate: half a unit of the printed
+# value's last digit (relative) plus the steady state's change over half a unit of the printed
+# potential (-85.23 mV, +-0.005 mV), rounded up; h carries 1e-3 (its printed 0.7444 sits 7e-4
+# below h_inf: tau_h = 7.9 ms at rest is still relaxing).  s is at rest only outside the
+# endocardium (tau_s = 725 ms there, 8.5 ms otherwise).
+_STEADY_GATES = [(T.M, 4e-3, (0, 1, 2)), (T.H, 1e-3, (0, 1, 2)), (T.D, 1e-3, (0, 1, 2)),
+                 (T.R, 3e-3, (0, 1, 2)), (T.XR2, 3e-4, (0, 1, 2)), (T.S, 1e-5, (1, 2))]
+
+
+@pytest.mark.parametrize("gate,tol,cells", _STEADY_GATES)
+def test_fast_gates_are_steady_at_the_published_rest(gate, tol, cells):
+    V, u = T.rest(1)
+    for cell in cells:
+        inf, tau = T.gate_inf_tau(V, u, cell)
+        assert tau[gate][0] < 10.0, (gate, cell)
+        rel = (inf[gate][0] - u[0, gate]) / u[0, gate]
+        assert abs(rel) <= tol, (gate, cell, rel)
+        # and so the gate does not move: |du/dt| <= tol u / tau
+        _, du = T.derivatives(V, u, cell)
+        assert abs(du[0, gate]) <= tol * u[0, gate] / tau[gate][0] * 1.0001, (gate, cell)
+
+
+def _paced(cell, bcl, beats, amp=-52.0, dur=1.0, model=T):
+    """V and the 18 states after `beats` cycles of length bcl (ms) from the published initial
+    state, each cycle starting with a dur-ms stimulus of amp pA/pF (LSODA, tight tolerances)."""
+    V0, u0 = model.rest(1)
+
+    def rhs_on(t, y):
+        dv, du = model.derivatives(np.array([y[0]]), y[1:].reshape(1, 18), cell)
+        return np.concatenate([dv - amp, du[0]])
+
+    def rhs_off(t, y):
+        dv, du = model.derivatives(np.array([y[0]]), y[1:].reshape(1, 18), cell)
+        return np.concatenate([dv, du[0]])
+
+    y = np.concatenate([V0, u0[0]])
+    for _ in range(beats):
+        y = solve_ivp(rhs_on, (0.0, dur), y, method="LSODA", rtol=1e-9, atol=1e-12, max_step=0.05).y[:, -1]
+        y = solve_ivp(rhs_off, (dur, bcl), y, method="LSODA", rtol=1e-9, atol=1e-12, max_step=0.5).y[:, -1]
+    return y
+
+
+# Bounds of the return to the printed state after one 550 ms beat, relative.  x_r1 deactivates
+# from its plateau value with tau = 47 ms at rest, so its end-diastolic value moves by 2 % per ms
+# of cycle length and by about 2 % per beat as the concentrations load: 8 %.  The other slow
+# gates return within 1 % (x_s, j, f: 2 %); the fast ones are checked at rest above.  Ki and Nai
+# change by < 0.1 % per beat; Cai, CaSS, CaSR and Rbar load over minutes of pacing (3-6 %).
+_ORBIT_BOUNDS = {T.XR1: 0.08, T.XS: 0.02, T.J: 0.02, T.F: 0.02, T.F2: 0.01, T.FCASS: 0.01,
+                 T.KI: 0.005, T.NAI: 0.005, T.CAI: 0.06, T.CASS: 0.06, T.CASR: 0.03, T.RBAR: 0.03}
+
+
+def _orbit_misses(y, model=T):
+    """The printed values that one paced beat does not return to (state index -> relative
+    difference), and V's difference in mV under key -1 when it exceeds 0.06 mV."""
+    V0, u0 = model.rest(1)
+    rel = (y[1:] - u0[0]) / u0[0]
+    out = {j: float(rel[j]) for j, tol in _ORBIT_BOUNDS.items() if not abs(rel[j]) <= tol}
+    if not abs(y[0] - V0[0]) <= 0.06:
+        out[-1] = float(y[0] - V0[0])
+    return out
+
+
+def test_published_state_is_the_end_diastole_of_550ms_pacing():
+    """The printed initial state is the end-diastolic state of the epicardial cell paced at a
+    550 ms cycle: one paced beat from it comes back to it.  The slow gates (x_r1, x_s, j, f, f2,
+    fCass; time constants 47-200 ms at rest) carry the whole beat's history, so their return pins
+    their steady states and time constants over the action potential; V's return pins the
+    action potential's duration (x_r1 fixes the cycle to about a millisecond)."""
+    assert _orbit_misses(_paced(2, 550.0, 1)) == {}
+
+
+class _Mutated:
+    """The oracle's model with one gate's steady state or time constant replaced (a planted
+    mistake, to show that the paced-orbit pin catches it)."""
+
+    def __init__(self, gate, which, fn):
+        self.gate, self.which, self.fn = gate, which, fn
+
+    def rest(self, n):
+        return T.rest(n)
+
+    def derivatives(self, V, u, cell):
+        orig = T.gate_inf_tau
+
+        def patched(V_, u_, cell_):
+            inf, tau = orig(V_, u_, cell_)
+            d = inf if self.which == "inf" else tau
+            d[self.gate] = self.fn(V_, d[self.gate])
+            return inf, tau
+        T.gate_inf_tau = patched
+        try:
+            return T.derivatives(V, u, cell)
+        finally:
+            T.gate_inf_tau = orig
+
+
+@pytest.mark.parametrize("mutant", [
+    # the other printed form of tau_f2: 600 exp(-(V+25)^2/170) + 31/(1+...) + 16/(1+exp((V+30)/10))
+    _Mutated(T.F2, "tau", lambda V, t: 600.0 * np.exp(-(V + 25.0) ** 2 / 170.0) +
+             31.0 / (1.0 + np.exp((25.0 - V) / 10.0)) + 16.0 / (1.0 + np.exp((V + 30.0) / 10.0))),
+    # a typo in x_r1's time-constant scale (450 -> 405) and in x_s's offset (80 -> 72)
+    _Mutated(T.XR1, "tau", lambda V, t: 0.9 * t),
+    _Mutated(T.XS, "tau", lambda V, t: t - 8.0),
+    # f's half-activation potential off by 1 mV
+    _Mutated(T.F, "inf", lambda V, t: 1.0 / (1.0 + np.exp((V + 21.0) / 7.0))),
+], ids=["tau_f2_other_form", "tau_xr1_scale", "tau_xs_offset", "f_inf_half"])
+def test_paced_orbit_pin_catches_planted_mistakes(mutant):
+    assert _orbit_misses(_paced(2, 550.0, 1, model=mutant)) != {}
 
 
 def test_action_potential_features(aps):
