@@ -553,8 +553,8 @@ __device__ __forceinline__ T rl_rate(T u, T inf, T rate, T dtl) {
 }
 
 // The same for a slow gate, whose tau has a lower bound over every V (x_s 80 ms, f 98.8 ms, f2
-// 6.13 ms, the last at V = 8 mV): for dt <= 0.025 ms, z = dt/tau <= 4.1e-3 and exp(-z) is its
-// degree-5 Taylor polynomial (error below z^6/720 < 7e-18); other steps take the exponential.
+// 8.79 ms, the last at V = 11.4 mV): for dt <= 0.025 ms, z = dt/tau <= 2.9e-3 and exp(-z) is its
+// degree-5 Taylor polynomial (error below z^6/720 < 1e-18); other steps take the exponential.
 template <typename T>
 __device__ __forceinline__ T rl_rate_slow(T u, T inf, T rate, T dt, T dtl, bool short_step) {
   T e;
@@ -732,7 +732,8 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = n
       un[12] = rl_rate(u[12], y2 * bd * r, da * db * dc * ad * r, dtl);
     }
     // f and f2 share fb = 1 + exp((V+30)/10) = F/xm01 with F = xm01 + e^3;
-    // tau_f = 1102.5 g + 200/(1+ea) + 180/(1+fb) + 20, tau_f2 = 600 g' + 31/(1+ga) + 16/(1+fb)
+    // tau_f = 1102.5 g + 200/(1+ea) + 180/(1+fb) + 20, tau_f2 = 562 g' + 31/(1+ga) + 80/(1+fb)
+    // with g = exp(-(V+27)^2/225), g' = exp(-(V+27)^2/240)
     const T F = xm01 + T(kE3);
     {
       const T af = T(1) + x17 * T(kE20o7);
@@ -745,7 +746,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = n
     {
       const T af2 = T(1) + x17 * T(kE5);
       const T ga = T(1) + xm01 * T(kE2p5);
-      const T num = T(600) * mexp2(gauss_arg(V, -kLog2e / 170.0, 25.0)) * ga * F + T(31) * F + T(16) * ga * xm01;
+      const T num = T(562) * mexp2(gauss_arg(V, -kLog2e / 240.0, 27.0)) * ga * F + T(31) * F + T(80) * ga * xm01;
       const T r = mrcp(af2 * num);
       un[14] = rl_rate_slow(u[14], T(0.67) * num * r + T(0.33), ga * F * af2 * r, dt, dtl, short_step);
     }
