@@ -86,6 +86,8 @@ typedef struct {
  * |det J| <= 1e-12 * (longest edge)^3, i.e. a degenerate element). */
 tc_status tc_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                          const double* fibres, const int32_t* region, tc_mesh** out);
+/* tc_mesh_destroy: release a mesh (simulations assembled from it stay valid: they hold their own
+ * copies).  NULL is a no-op. */
 void tc_mesh_destroy(tc_mesh* mesh);
 
 /* Number of stored entries of M, K and A (one shared pattern: every node pair of an element). */
@@ -141,6 +143,8 @@ tc_status tc_mesh_ordering(const tc_mesh* mesh, int32_t sell_sigma, int32_t* per
 tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* sigma_t,
                       int32_t n_regions, double chi, double cm, double theta, double dt,
                       int32_t precision, void* cuda_stream, tc_sim** out);
+/* tc_sim_destroy: release the simulation's device and host memory (after waiting for its stream);
+ * the mesh it was assembled from is not touched.  NULL is a no-op. */
 void tc_sim_destroy(tc_sim* sim);
 
 tc_status tc_sim_size(const tc_sim* sim, int64_t* n_nodes, int64_t* nnz, int64_t* padded_nnz,
@@ -195,19 +199,31 @@ tc_status tc_set_solver(tc_sim* sim, double atol, double rtol, int32_t max_iter)
 tc_status tc_set_activation_threshold(tc_sim* sim, double v_threshold);
 
 /* tc_step: advance n_steps >= 0 time steps on the simulation's stream and wait for them.
+ * One step k -> k+1 is the operator-split scheme of Section 2.2:
+ *   the ionic update u^{k+1} = f(V^k, u^k) and I_ion(V^k, u^{k+1})       (Eq. 2, first row),
+ *   b = chi M (Cm V^k - dt I_ion + dt I_stim) - (1 - theta) dt K V^k      (definition after Eq. 3),
+ *   A V^{k+1} = b, A = chi Cm M + theta dt K, solved by Jacobi-PCG           (Eq. 3, Algorithm 1)
+ *     from the extrapolated guess 2 V^k - V^{k-1}                          (end of Section 2.2),
+ *   then the activation (LAT) and repolarisation (LRT) capture             (Section 2.1).
  * Errors: TC_ERR_STATE (no ionic model), TC_ERR_TIMEOUT (a device wait hit its limit; the
  * state is then undefined), TC_ERR_NAN, TC_ERR_CUDA. */
 tc_status tc_step(tc_sim* sim, int64_t n_steps, tc_step_stats* stats);
 
-/* tc_read_state / tc_write_state: copy one field to/from a host array of n = n_nodes doubles
- * in caller node order (TC_FIELD_V = V^k, TC_FIELD_V_PREV = V^{k-1},
- * TC_FIELD_STATE + j = ionic state j). */
+/* tc_read_state / tc_write_state: the solution output of Section 2.1 (the transmembrane
+ * potential written every plot interval) and its inverse, for checkpoint/restart.  Copy one field
+ * to/from a host array of n = n_nodes doubles in caller node order (TC_FIELD_V = V^k,
+ * TC_FIELD_V_PREV = V^{k-1}, the second history level of the extrapolated guess at the end of
+ * Section 2.2; TC_FIELD_STATE + j = ionic state j of Eq. 2's u).  Errors: TC_ERR_ARG (null
+ * pointer, n != n_nodes, unknown field), TC_ERR_CUDA.  tc_write_state returns nodes held by the
+ * learned surrogate to the exact model. */
 tc_status tc_read_state(const tc_sim* sim, int32_t field, double* host_dst, int64_t n);
 tc_status tc_write_state(tc_sim* sim, int32_t field, const double* host_src, int64_t n);
 
-/* tc_activation_times: per node, the first time (ms) V crossed v_threshold upwards, linearly
- * interpolated within the step; 0 if V^0 >= threshold; -1 if never.  v_threshold must equal the
- * capture threshold (TC_ERR_STATE otherwise). */
+/* tc_activation_times: the local activation times (LAT) of Section 2.1 - per node, the first
+ * time (ms) V crossed v_threshold upwards (0 mV by default: "first becomes positive"), linearly
+ * interpolated within the step; 0 if V^0 >= threshold; -1 if never.  host_dst: n = n_nodes
+ * doubles, caller order.  v_threshold must equal the capture threshold (TC_ERR_STATE
+ * otherwise); TC_ERR_ARG on a null pointer or n != n_nodes. */
 tc_status tc_activation_times(const tc_sim* sim, double v_threshold, double* host_dst, int64_t n);
 
 /* Repolarisation (Section 2.1, LRT: V returns below -70 mV with a negative time derivative).
@@ -239,13 +255,17 @@ tc_status tc_apply_operator_dev(tc_sim* sim, int32_t op, const void* x_dev, void
  * allocate device memory while they run (a process whose device memory is reserved by another
  * allocator, so cudaMalloc would fail, or a caller that cannot afford the device-wide
  * synchronisation cudaFree implies).  The paper has no counterpart; it is a library facility.
- * x and y are host arrays [n_nodes] in caller order.  Device staging for x and y is a static
- * 4 MiB array inside the library (2 x 262,144 doubles) that every GPU loading the library holds
- * until the process exits; meshes with more than 262,144 nodes are rejected with TC_ERR_ARG.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array: calls that overlap on
- * the GPU (e.g. from two threads or two streams) race.  Allocates nothing; waits for the
- * simulation's stream before and after the copy. */
+ * TC_FP64 simulations only (others get TC_ERR_ARG).  x and y are host arrays [n_nodes] in caller
+ * order (n != n_nodes gives TC_ERR_ARG).  Device staging for x and y is a static 4 MiB array
+ * inside the library (2 x 262,144 doubles) that every GPU loading the library holds until the
+ * process exits; a simulation whose padded device layout has more than 262,144 rows (each
+ * connected component is padded to a multiple of 32 rows, so up to 31 more rows than nodes per
+ * component) is rejected with TC_ERR_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and keeps it for the life of the device's primary
+ * context (a cudaDeviceReset between calls is not supported); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU (e.g. from two
+ * threads or two streams) race.  Allocates nothing; waits for the simulation's stream before and
+ * after the copy. */
 tc_status tc_apply_operator_static(tc_sim* sim, int32_t op, const double* x, double* y, int64_t n);
 
 /* Profiling: when on, tc_step records CUDA events around every launch on the simulation's

@@ -5,8 +5,9 @@ advanced first, then I_ion is evaluated at (V^k, u^{k+1}).  Gating variables use
 Rush-Larsen step u^{k+1} = u_inf + (u^k - u_inf) exp(-dt/tau), which is exact for a gate with
 constant u_inf and tau over the step; other states use forward Euler as Eq. 2 states.
 
-Mitchell-Schaeffer (Mitchell & Schaeffer 2003), not written out in the paper, is mapped to mV
-as follows (reading stated here and in the design notes):
+Mitchell-Schaeffer (Mitchell & Schaeffer 2003) is named by the workloads but not written out in
+the paper, and its variable v is dimensionless; the reading taken maps it to mV with the
+potential range [v_min, v_max] of the tissue model:
     v = (V - v_min) / (v_max - v_min)
     J_in = h v^2 (1 - v) / tau_in,   J_out = -v / tau_out
     I_ion = -Cm (v_max - v_min) (J_in + J_out)            [uA/mm^2 with Cm in uF/mm^2]

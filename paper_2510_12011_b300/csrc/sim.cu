@@ -1691,7 +1691,9 @@ __global__ void __launch_bounds__(256) spmv_sell_static_kernel(
   }
 }
 
-// Device address of the staging array on the current device (looked up once per device).
+// Device address of the staging array on the current device, looked up once per device and kept
+// for the life of that device's primary context (a cudaDeviceReset between calls may move the
+// array; the header states that this is not supported).
 tc_status static_scratch_address(int device, double** out) {
   if (device < 0 || device >= kStaticMaxDevices)
     return fail(TC_ERR_ARG, "device ordinal too large for the static staging table");
@@ -1717,8 +1719,8 @@ extern "C" tc_status tc_apply_operator_static(tc_sim* s, int32_t op, const doubl
     return fail(TC_ERR_ARG, "tc_apply_operator_static serves TC_FP64 simulations only");
   if (s->n_int > kStaticMaxNodes)
     return fail(TC_ERR_ARG, "tc_apply_operator_static handles at most " +
-                                std::to_string(kStaticMaxNodes) + " nodes; this mesh has " +
-                                std::to_string(s->n_int) + " in its device layout (use tc_apply_operator)");
+                                std::to_string(kStaticMaxNodes) + " rows of the padded device layout; this "
+                                "simulation has " + std::to_string(s->n_int) + " (use tc_apply_operator)");
   const double* val = static_cast<const double*>(op_values(s, op));
   if (!val) return fail(TC_ERR_ARG, "unknown operator");
   CUDA_TRY(cudaSetDevice(s->device));

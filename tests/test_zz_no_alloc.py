@@ -39,3 +39,20 @@ def test_static_operator_rejects_meshes_above_its_limit():
     with pytest.raises(tc.TcError) as e:
         sim2.apply_static(tc.TC_OP_A, np.zeros(big.mesh.n_nodes))
     assert e.value.status == tc.TC_ERR_ARG and "262144" in e.value.message
+
+
+def test_static_operator_rejects_fp32_simulations_and_wrong_sizes():
+    """The documented argument contract: TC_FP64 simulations only, n equal to the node count."""
+    w = I.slab_small_ms()
+    sim32 = tc.from_workload(w, precision=tc.TC_FP32)
+    x = I.random_vector(w.mesh.n_nodes, 11)
+    with pytest.raises(tc.TcError) as e:
+        sim32.apply_static(tc.TC_OP_A, x)
+    assert e.value.status == tc.TC_ERR_ARG and "FP64" in e.value.message
+    sim = tc.from_workload(w)
+    for bad in (x[:-1], np.concatenate([x, [0.0]])):
+        with pytest.raises(tc.TcError) as e:
+            sim.apply_static(tc.TC_OP_A, bad)
+        assert e.value.status == tc.TC_ERR_ARG
+    # a rejected call leaves the entry point usable
+    assert np.array_equal(sim.apply_static(tc.TC_OP_A, x), sim.apply(tc.TC_OP_A, x))
