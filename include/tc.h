@@ -155,6 +155,17 @@ tc_status tc_sim_size(const tc_sim* sim, int64_t* n_nodes, int64_t* nnz, int64_t
 tc_status tc_sim_layout(const tc_sim* sim, int32_t* n_components, int64_t* n_internal,
                         int32_t* pcg_threads, int32_t* blocks_per_sm);
 
+/* tc_sim_staging: how the PCG launch gathers the vector of its A-products (Algorithm 1's q = A p).
+ * Each block of the cooperative launch owns a contiguous range of SELL slices; under the RCM
+ * order the columns those rows touch form a band (the block's window).  When the window fits the
+ * shared memory left per block at the launch shape, the block copies it into shared memory after
+ * each grid barrier and its gathers read shared memory; otherwise they read global memory.  The
+ * results are bitwise the same either way.  Reports the number of blocks, how many stage their
+ * window, the largest window (entries) and the launch's dynamic shared memory (bytes); any pointer
+ * may be NULL.  The environment variable TC_PCG_STAGE=0, read at tc_assemble, turns staging off. */
+tc_status tc_sim_staging(const tc_sim* sim, int32_t* blocks, int32_t* staged_blocks, int32_t* max_window,
+                         int64_t* smem_bytes);
+
 /* tc_set_launch: PCG launch shape (512 or 1024 threads per block, blocks per SM, capped by the
  * occupancy of the cooperative launch).  Errors: TC_ERR_ARG (shape or too many components). */
 tc_status tc_set_launch(tc_sim* sim, int32_t pcg_threads, int32_t blocks_per_sm);
@@ -344,7 +355,8 @@ tc_status tc_gemm_bf16_nt(const void* a_dev, const void* b_dev, float* c_dev, in
 tc_status tc_tp06_window(const float* in_dev, const float* istim_dev, int64_t n, double dt, int32_t nsub,
                          int32_t cell, int32_t precision, float* out_dev, void* cuda_stream);
 
-/* tc_set_surrogate: attach (mlp != NULL) or detach the surrogate to a TC_FP32 TP06 simulation.
+/* tc_set_surrogate: attach (mlp != NULL) or detach the surrogate to a TP06 simulation (TC_FP32 or
+ * TC_FP64 tissue; the network itself computes in BF16 with FP32 accumulation).
  * Every `window` steps each node's surrogate prediction is checked (finite, concentrations > 0,
  * gates in [0,1] within 0.01, |V' - V| <= dv_max over the window, |dV/dt| <= dvdt_max on the
  * step before, no stimulus during the window, and - with dv_neighbour > 0 - no neighbour in the

@@ -13,6 +13,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace tc {
 
@@ -87,6 +88,8 @@ struct PcgArgs {
   const int32_t* blk_slice;   // gridDim.x + 1 slice boundaries
   const int32_t* comp_of_block;   // connected component (independent problem) of each block
   const int32_t* comp_block0;     // first block of each component, n_comp + 1 entries
+  const int32_t* blk_win;         // per block (lo, len): the block's window of gathered columns,
+                                  // staged in shared memory when len > 0
   const T* g1;
   const T* g2;
   T* x;                       // in: x0, out: V^{k+1}
@@ -130,29 +133,34 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
 // barrier number e of the launch is passed once the counter reaches e * nblocks.  Arrival is a
 // release reduction, the wait an acquire poll, so the block's writes before the barrier are
 // visible to every block after it.  Every wait is bounded: after wait_limit polls the block
-// records kErrTimeout and leaves; a block that sees any error flag returns false so that the
-// kernel can exit without further waits.
+// records kErrTimeout and leaves.  The error word is read only every 64 polls (not on the path
+// of a barrier that completes): a block that sees it set leaves too, so that after one block
+// gives up every other block leaves at its next barrier instead of waiting out its own limit.
 __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, unsigned& epoch,
                                           long long wait_limit, int* err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = *(volatile int*)err ? 0 : 1;   // after an error, leave without waiting
+    int ok = 1;
     epoch += 1;
-    if (ok && nblocks > 1) {
+    if (nblocks > 1) {
       const unsigned target = epoch * nblocks;
       red_release_add_u32(&bar->count, 1u);
       long long polls = 0;
       while (ld_acquire_u32(&bar->count) < target) {
-        if (++polls > wait_limit) {
+        ++polls;
+        if (polls > wait_limit) {
           atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        if ((polls & 63) == 0 && *(volatile int*)err) {
           ok = 0;
           break;
         }
         if (polls > 2048) __nanosleep(20);
       }
     }
-    if (ok && *(volatile int*)err) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
@@ -191,36 +199,54 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
 }
 
 // Warp 0 of every block reduces the per-block partials in the same order; lane 0 of warp 0
-// holds the totals.  Every block obtains bitwise the same totals.
+// holds the totals.  Every block obtains bitwise the same totals.  Up to 160 partials (one wave
+// of 148 blocks) every lane issues all its loads before adding them: one round trip to L2.
 __device__ __forceinline__ void grid_sum_warp0(const double* part, int stride, unsigned nb,
                                                double& a, double& b, bool two) {
   const int lane = threadIdx.x & 31;
   double sa = 0.0, sb = 0.0;
-  unsigned i = lane;
-  for (; i + 96 < nb; i += 128) {   // four loads in flight per lane
-    const double a0 = __ldcg(&part[(size_t)i * stride]);
-    const double a1 = __ldcg(&part[(size_t)(i + 32) * stride]);
-    const double a2 = __ldcg(&part[(size_t)(i + 64) * stride]);
-    const double a3 = __ldcg(&part[(size_t)(i + 96) * stride]);
-    double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-    if (two) {
-      b0 = __ldcg(&part[(size_t)i * stride + 1]);
-      b1 = __ldcg(&part[(size_t)(i + 32) * stride + 1]);
-      b2 = __ldcg(&part[(size_t)(i + 64) * stride + 1]);
-      b3 = __ldcg(&part[(size_t)(i + 96) * stride + 1]);
+  if (nb <= 160) {
+    double va[5], vb[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const unsigned i = lane + 32 * k;
+      va[k] = i < nb ? __ldcg(&part[(size_t)i * stride]) : 0.0;
+      vb[k] = two && i < nb ? __ldcg(&part[(size_t)i * stride + 1]) : 0.0;
     }
-    sa += a0;
-    sa += a1;
-    sa += a2;
-    sa += a3;
-    sb += b0;
-    sb += b1;
-    sb += b2;
-    sb += b3;
-  }
-  for (; i < nb; i += 32) {
-    sa += __ldcg(&part[(size_t)i * stride]);
-    if (two) sb += __ldcg(&part[(size_t)i * stride + 1]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      if (lane + 32 * k < nb) {
+        sa += va[k];
+        sb += vb[k];
+      }
+    }
+  } else {
+    unsigned i = lane;
+    for (; i + 96 < nb; i += 128) {   // four loads in flight per lane
+      const double a0 = __ldcg(&part[(size_t)i * stride]);
+      const double a1 = __ldcg(&part[(size_t)(i + 32) * stride]);
+      const double a2 = __ldcg(&part[(size_t)(i + 64) * stride]);
+      const double a3 = __ldcg(&part[(size_t)(i + 96) * stride]);
+      double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+      if (two) {
+        b0 = __ldcg(&part[(size_t)i * stride + 1]);
+        b1 = __ldcg(&part[(size_t)(i + 32) * stride + 1]);
+        b2 = __ldcg(&part[(size_t)(i + 64) * stride + 1]);
+        b3 = __ldcg(&part[(size_t)(i + 96) * stride + 1]);
+      }
+      sa += a0;
+      sa += a1;
+      sa += a2;
+      sa += a3;
+      sb += b0;
+      sb += b1;
+      sb += b2;
+      sb += b3;
+    }
+    for (; i < nb; i += 32) {
+      sa += __ldcg(&part[(size_t)i * stride]);
+      if (two) sb += __ldcg(&part[(size_t)i * stride + 1]);
+    }
   }
   a = warp_sum(sa);
   b = two ? warp_sum(sb) : 0.0;
@@ -286,9 +312,9 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 constexpr int kSellUnroll4 = 0;
 constexpr int kSellChunk8 = 1;
 
-template <int SHAPE, typename T>
-__device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
-                                     int beg, int w, const T* x, uint64_t pol = 0) {
+template <int SHAPE, typename T, typename XF>
+__device__ __forceinline__ T sell_dot_f(const int32_t* __restrict__ col, const T* __restrict__ val,
+                                        int beg, int w, XF xf, uint64_t pol = 0) {
   T acc0 = T(0), acc1 = T(0);
   if constexpr (SHAPE == kSellChunk8) {
     for (int j = 0; j < w; j += 8) {
@@ -302,7 +328,7 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
       }
       T xv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) xv[u] = j + u < w ? x[c[u]] : T(0);
+      for (int u = 0; u < 8; ++u) xv[u] = j + u < w ? xf(c[u]) : T(0);
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         if (j + u < w) acc0 = fmaT(v[u], xv[u], acc0);
@@ -318,7 +344,7 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
                 c3 = ld_hint(col + e + 96, pol);
       const T v0 = ld_hint(val + e, pol), v1 = ld_hint(val + e + 32, pol), v2 = ld_hint(val + e + 64, pol),
               v3 = ld_hint(val + e + 96, pol);
-      const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+      const T x0 = xf(c0), x1 = xf(c1), x2 = xf(c2), x3 = xf(c3);
       acc0 = fmaT(v0, x0, acc0);
       acc1 = fmaT(v1, x1, acc1);
       acc0 = fmaT(v2, x2, acc0);
@@ -329,13 +355,43 @@ __device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* 
     // fifth more FP64 work on a 15-entry row); the final sum is symmetric
     for (; j < w; ++j) {
       const int e = beg + 32 * j;
-      acc0 = fmaT(ld_hint(val + e, pol), x[ld_hint(col + e, pol)], acc0);
+      acc0 = fmaT(ld_hint(val + e, pol), xf(ld_hint(col + e, pol)), acc0);
       const T t = acc0;
       acc0 = acc1;
       acc1 = t;
     }
   }
   return acc0 + acc1;
+}
+
+// The product gathering from a global vector x.
+template <int SHAPE, typename T>
+__device__ __forceinline__ T sell_dot(const int32_t* __restrict__ col, const T* __restrict__ val,
+                                     int beg, int w, const T* x, uint64_t pol = 0) {
+  return sell_dot_f<SHAPE>(col, val, beg, w, [x](int c) { return x[c]; }, pol);
+}
+
+// Copy x[lo, lo + len) into shared memory xs (lo and len multiples of 4, so every access is a
+// 16-byte vector), bypassing L1: the vector was written by other blocks of the launch before
+// the grid barrier that precedes this copy.  Four vectors per thread are loaded before they are
+// stored, so that a thread has four loads in flight.
+template <int THREADS, typename T>
+__device__ __forceinline__ void stage_window(T* xs, const T* __restrict__ x, int lo, int len) {
+  using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+  constexpr int PER = 16 / sizeof(T);
+  const V* src = reinterpret_cast<const V*>(x + lo);
+  V* dst = reinterpret_cast<V*>(xs);
+  const int nv = len / PER;
+  int i = threadIdx.x;
+  for (; i + 3 * THREADS < nv; i += 4 * THREADS) {
+    const V a0 = __ldcg(src + i), a1 = __ldcg(src + i + THREADS), a2 = __ldcg(src + i + 2 * THREADS),
+            a3 = __ldcg(src + i + 3 * THREADS);
+    dst[i] = a0;
+    dst[i + THREADS] = a1;
+    dst[i + 2 * THREADS] = a2;
+    dst[i + 3 * THREADS] = a3;
+  }
+  for (; i < nv; i += THREADS) dst[i] = __ldcg(src + i);
 }
 
 // The shape of the PCG's product per storage type (see above).
@@ -503,6 +559,12 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
   const int tail_g = tail_r == 0 ? 1 : min(NW / tail_r, 8);
   const bool split = sizeof(T) == 8 && tail_g >= 2;
   const int n_whole = split ? n_sl - tail_r : n_sl;
+  // The block's window of z in shared memory (blk_win: lo, len; len = 0 when it does not fit):
+  // the product's gathers then read shared memory instead of waiting on L2 for every entry.
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  T* s_x = reinterpret_cast<T*>(s_dyn);
+  const int win_lo = a.blk_win[2 * b], win_len = a.blk_win[2 * b + 1];
+  const bool staged = win_len > 0;
   while (flag == 0 && it < a.max_iter) {
     // p = z + beta p and q = A p, formed as q = A z + beta q (A p_k = A z_k + beta A p_{k-1}):
     // the product gathers z, complete since the last barrier, so p and q are updated row by row
@@ -525,49 +587,65 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
       a.q[row] = qn;
       pq_t = fmaT(pn, qn, pq_t);
     };
-    for (int s = s0 + warp; s < s0 + n_whole; s += NW) {
-      const int beg = a.slice_ptr[s] + lane;
-      const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
-      const int64_t row = (int64_t)s * 32 + lane;
-      const bool real = row < a.n;
-      // FP32: the row's own z, p, q are loaded before the product so that their latency
-      // overlaps its loads (loaded after it they cost a round trip per slice: 15 % on the
-      // 64-slab batch, about 35 slices per warp).  FP64: after it - holding them across the
-      // product would spill at 1,024 threads.
-      T zr = T(0), pr = T(0), qr = T(0);
-      if constexpr (sizeof(T) == 4) {
-        if (real) load_row(row, zr, pr, qr);
-      }
-      const T acc = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, a.z, pol_a);
-      if constexpr (sizeof(T) == 8) {
-        if (real) load_row(row, zr, pr, qr);
-      }
-      if (real) store_row(row, acc, zr, pr, qr);
+    if (staged) {
+      stage_window<THREADS>(s_x, a.z, win_lo, win_len);
+      __syncthreads();
     }
-    if (split) {
-      const int t = warp / tail_g, c = warp - t * tail_g;
-      const int s = s0 + n_whole + t;
-      const int64_t row = (int64_t)s * 32 + lane;
-      const bool real = t < tail_r && row < a.n;
-      T zr = T(0), pr = T(0), qr = T(0);
-      if (t < tail_r) {
+    // the product over the block's slices; `from_smem` selects the gather source at compile time
+    auto product = [&](auto from_smem) {
+      constexpr bool kSmem = decltype(from_smem)::value;
+      auto xf = [&](int c) -> T {
+        if constexpr (kSmem) return s_x[c - win_lo];
+        else return a.z[c];
+      };
+      for (int s = s0 + warp; s < s0 + n_whole; s += NW) {
         const int beg = a.slice_ptr[s] + lane;
         const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
-        const int per = (w + tail_g - 1) / tail_g;
-        const int j0 = min(w, c * per), j1 = min(w, j0 + per);
+        const int64_t row = (int64_t)s * 32 + lane;
+        const bool real = row < a.n;
+        // FP32: the row's own z, p, q are loaded before the product so that their latency
+        // overlaps its loads (loaded after it they cost a round trip per slice: 15 % on the
+        // 64-slab batch, about 35 slices per warp).  FP64: after it - holding them across the
+        // product would spill at 1,024 threads.
+        T zr = T(0), pr = T(0), qr = T(0);
         if constexpr (sizeof(T) == 4) {
-          if (c == 0 && real) load_row(row, zr, pr, qr);
+          if (real) load_row(row, zr, pr, qr);
         }
-        s_part[warp * 32 + lane] = sell_dot<pcg_sell_shape<T>()>(a.col, a.vA, beg + 32 * j0, j1 - j0, a.z, pol_a);
+        const T acc = sell_dot_f<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, xf, pol_a);
+        if constexpr (sizeof(T) == 8) {
+          if (real) load_row(row, zr, pr, qr);
+        }
+        if (real) store_row(row, acc, zr, pr, qr);
       }
-      __syncthreads();
-      if (c == 0 && real) {
-        T acc = s_part[warp * 32 + lane];
-        for (int k = 1; k < tail_g; ++k) acc += s_part[(warp + k) * 32 + lane];
-        if constexpr (sizeof(T) == 8) load_row(row, zr, pr, qr);
-        store_row(row, acc, zr, pr, qr);
+      if (split) {
+        const int t = warp / tail_g, c = warp - t * tail_g;
+        const int s = s0 + n_whole + t;
+        const int64_t row = (int64_t)s * 32 + lane;
+        const bool real = t < tail_r && row < a.n;
+        T zr = T(0), pr = T(0), qr = T(0);
+        if (t < tail_r) {
+          const int beg = a.slice_ptr[s] + lane;
+          const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
+          const int per = (w + tail_g - 1) / tail_g;
+          const int j0 = min(w, c * per), j1 = min(w, j0 + per);
+          if constexpr (sizeof(T) == 4) {
+            if (c == 0 && real) load_row(row, zr, pr, qr);
+          }
+          s_part[warp * 32 + lane] = sell_dot_f<pcg_sell_shape<T>()>(a.col, a.vA, beg + 32 * j0, j1 - j0, xf, pol_a);
+        }
+        __syncthreads();
+        if (c == 0 && real) {
+          T acc = s_part[warp * 32 + lane];
+          for (int k = 1; k < tail_g; ++k) acc += s_part[(warp + k) * 32 + lane];
+          if constexpr (sizeof(T) == 8) load_row(row, zr, pr, qr);
+          store_row(row, acc, zr, pr, qr);
+        }
       }
-    }
+    };
+    if (staged)
+      product(std::true_type{});
+    else
+      product(std::false_type{});
     {
       double v1[1] = {double(pq_t)};
       block_sum<THREADS, 1>(v1, s_red);
@@ -719,7 +797,7 @@ __global__ void __launch_bounds__(1024, 1) pcg_step_kernel_1024(const PcgArgs<T>
   pcg_step<1024, T>(a);
 }
 template <typename T>
-__global__ void __launch_bounds__(512) pcg_step_kernel_512(const PcgArgs<T> a) {
+__global__ void __maxnreg__(64) pcg_step_kernel_512(const PcgArgs<T> a) {
   pcg_step<512, T>(a);
 }
 

@@ -6,6 +6,7 @@
 // have no matrix entries and a zero Jacobi inverse, so their residual, direction and update stay
 // zero and their potential stays at the resting value; they never reach the caller.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -69,6 +70,13 @@ struct tc_sim {
   int* log_valid = nullptr;
   // device arrays (element type double for TC_FP64, float for TC_FP32)
   int32_t *slice_ptr = nullptr, *col = nullptr, *blk_slice = nullptr;
+  // per SELL slice, the smallest and largest column it stores (padding included); per PCG block,
+  // the window (lo, len) of z it stages in shared memory (len 0: gathers from global memory)
+  std::vector<int32_t> slice_cmin, slice_cmax;
+  int32_t* blk_win = nullptr;
+  size_t pcg_dyn_smem = 0;     // dynamic shared memory of the PCG launch (the largest staged window)
+  int pcg_stage = 1;           // stage windows when they fit (TC_PCG_STAGE=0 turns it off)
+  int32_t win_staged = 0, win_max = 0;   // blocks staged, largest window (entries) of the partition
   int32_t *comp_of_block = nullptr, *comp_block0 = nullptr;
   void *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
   void* V[3] = {nullptr, nullptr, nullptr};
@@ -376,9 +384,61 @@ tc_status set_partition(tc_sim* s) {
   }
   bs.push_back((int32_t)(s->n_int / 32));
   s->nblocks = cb0[s->n_comp];
+  // Shared-memory windows of z: a block's gathers touch the columns between the smallest and
+  // largest column of its slices (under RCM a band about the block's rows).  The window is
+  // aligned to 4 entries (16-byte vectors) and staged when it fits the shared memory left per
+  // block at this launch shape; the dynamic shared memory of the launch is the largest staged one.
+  std::vector<int32_t> win(2 * (size_t)s->nblocks, 0);
+  size_t dyn = 0;
+  s->win_staged = 0;
+  s->win_max = 0;
+  if (s->pcg_stage && !s->slice_cmin.empty()) {
+    cudaFuncAttributes fa{};
+    CUDA_TRY(cudaFuncGetAttributes(&fa, pcg_kernel(s)));
+    int sm_per_sm = 0, sm_optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sm_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&sm_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
+    const int64_t per_block = std::min<int64_t>(sm_optin, sm_per_sm / per_sm - 1024) - (int64_t)fa.sharedSizeBytes;
+    int64_t cap = per_block > 0 ? (per_block / (int64_t)s->esz) / 4 * 4 : 0;
+    // TC_PCG_STAGE_CAP (entries) lowers the capacity, so that tests can mix staged and unstaged blocks
+    const int env_cap = env_int("TC_PCG_STAGE_CAP", 0);
+    if (env_cap > 0) cap = std::min<int64_t>(cap, env_cap);
+    int64_t used = 0;
+    for (int b = 0; b < s->nblocks; ++b) {
+      int32_t lo = INT32_MAX, hi = -1;
+      for (int32_t sl = bs[b]; sl < bs[b + 1]; ++sl) {
+        lo = std::min(lo, s->slice_cmin[sl]);
+        hi = std::max(hi, s->slice_cmax[sl]);
+      }
+      if (hi < 0) continue;
+      lo = lo / 4 * 4;
+      const int64_t len = std::min<int64_t>(((int64_t)hi + 1 - lo + 3) / 4 * 4, s->n_int - lo);
+      s->win_max = std::max<int32_t>(s->win_max, (int32_t)len);
+      if (len <= cap) {
+        win[2 * b] = lo;
+        win[2 * b + 1] = (int32_t)len;
+        used = std::max(used, len);
+        s->win_staged += 1;
+      }
+    }
+    dyn = (size_t)used * s->esz;
+    if (dyn > 0) {
+      CUDA_TRY(cudaFuncSetAttribute(pcg_kernel(s), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+      int bps2 = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, pcg_kernel(s), s->pcg_threads, dyn));
+      if (bps2 < per_sm) {   // cannot stay co-resident with the windows: gather from global memory
+        std::fill(win.begin(), win.end(), 0);
+        dyn = 0;
+        s->win_staged = 0;
+      }
+    }
+  }
+  s->pcg_dyn_smem = dyn;
   for (void* p : {(void*)s->blk_slice, (void*)s->partA, (void*)s->partB, (void*)s->comp_of_block,
-                  (void*)s->comp_block0})
+                  (void*)s->comp_block0, (void*)s->blk_win})
     dfree(s, p);
+  TRY(dalloc(s, &s->blk_win, win.size()));
+  CUDA_TRY(cudaMemcpy(s->blk_win, win.data(), win.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   TRY(dalloc(s, &s->blk_slice, bs.size()));
   TRY(dalloc(s, &s->comp_of_block, cob.size()));
   TRY(dalloc(s, &s->comp_block0, cb0.size()));
@@ -457,7 +517,7 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   ia.n_bar = s->n_comp;
   ia.sur_flag = s->sur ? s->sur_flag : nullptr;
   ia.sur_iion = s->sur ? s->sur_iion : nullptr;
-  ia.log_cache = s->model == TC_MODEL_TP06 && s->precision == TC_FP64 && !s->sur && s->log_cache
+  ia.log_cache = s->model == TC_MODEL_TP06 && s->precision == TC_FP64 && s->log_cache
                      ? static_cast<T*>(s->log_cache)
                      : nullptr;
   ia.log_valid = s->log_valid;
@@ -484,6 +544,7 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   pa.vA = static_cast<const T*>(s->vA);
   pa.dinv = static_cast<const T*>(s->dinv);
   pa.blk_slice = s->blk_slice;
+  pa.blk_win = s->blk_win;
   pa.comp_of_block = s->comp_of_block;
   pa.comp_block0 = s->comp_block0;
   pa.g1 = static_cast<const T*>(s->g1);
@@ -520,7 +581,7 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
     (*ev)++;
   }
   void* args[] = {&pa};
-  CUDA_TRY(cudaLaunchCooperativeKernel(pcg_kernel(s), s->nblocks, s->pcg_threads, args, 0,
+  CUDA_TRY(cudaLaunchCooperativeKernel(pcg_kernel(s), s->nblocks, s->pcg_threads, args, s->pcg_dyn_smem,
                                        s->stream));
   if (ev) {
     CUDA_TRY(cudaEventRecord(pooled_event(s, *ev), s->stream));
@@ -550,10 +611,12 @@ tc_status launch_surrogate(tc_sim* s, int iv, int k_off, size_t* ev = nullptr,
     CUDA_TRY(cudaEventRecord(s->evpool[*ev], s->stream));
   }
   q.n = s->n_int;
-  q.state = static_cast<float*>(s->state);
-  q.V = static_cast<const float*>(s->V[iv]);
-  q.Vprev = static_cast<const float*>(s->V[(iv + 2) % 3]);
-  q.dinv = static_cast<const float*>(s->dinv);
+  q.fp64 = s->precision == TC_FP64;
+  q.state = s->state;
+  q.V = s->V[iv];
+  q.Vprev = s->V[(iv + 2) % 3];
+  q.dinv = s->dinv;
+  q.log_cache = q.fp64 && s->log_cache ? static_cast<double*>(s->log_cache) : nullptr;
   q.stim_off = s->stim_off;
   q.stim_ids = s->stim_ids;
   q.stims = s->stims;
@@ -884,6 +947,18 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   }
   s->nslices = sell.nslices;
   s->padded = sell.padded;
+  s->pcg_stage = env_int("TC_PCG_STAGE", 1) != 0;
+  try {
+    s->slice_cmin.assign(sell.nslices, INT32_MAX);
+    s->slice_cmax.assign(sell.nslices, -1);
+    for (int64_t sl = 0; sl < sell.nslices; ++sl)
+      for (int64_t e = sell.slice_ptr[sl]; e < sell.slice_ptr[sl + 1]; ++e) {
+        s->slice_cmin[sl] = std::min(s->slice_cmin[sl], sell.col[e]);
+        s->slice_cmax[sl] = std::max(s->slice_cmax[sl], sell.col[e]);
+      }
+  } catch (const std::bad_alloc&) {
+    return bail(fail(TC_ERR_NOMEM, "out of host memory"));
+  }
   cudaError_t ce = cudaGetDevice(&s->device);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
   ce = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -1012,6 +1087,17 @@ tc_status tc_sim_layout(const tc_sim* s, int32_t* n_components, int64_t* n_inter
   return TC_OK;
 }
 
+tc_status tc_sim_staging(const tc_sim* s, int32_t* blocks, int32_t* staged_blocks, int32_t* max_window,
+                         int64_t* smem_bytes) {
+  clear_error();
+  if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  if (blocks) *blocks = s->nblocks;
+  if (staged_blocks) *staged_blocks = s->win_staged;
+  if (max_window) *max_window = s->win_max;
+  if (smem_bytes) *smem_bytes = (int64_t)s->pcg_dyn_smem;
+  return TC_OK;
+}
+
 tc_status tc_set_launch(tc_sim* s, int32_t pcg_threads, int32_t blocks_per_sm) {
   clear_error();
   if (!s || (pcg_threads != 512 && pcg_threads != 1024) || blocks_per_sm < 1)
@@ -1082,7 +1168,7 @@ tc_status tc_set_ionic(tc_sim* s, int32_t model, const double* params, int32_t n
   s->model = model;
   s->n_states = ns;
   drop_graphs(s);   // model constants are baked into captured launches
-  // the learned surrogate serves FP32 TP06 only; a re-initialised model starts exact
+  // the learned surrogate serves TP06 only; a re-initialised model starts exact
   if (model != TC_MODEL_TP06) s->sur = nullptr;
   if (s->sur_flag) CUDA_TRY(cudaMemset(s->sur_flag, 0, s->n_int));
   std::vector<double> col(s->n_int);
@@ -1302,8 +1388,8 @@ tc_status tc_set_surrogate(tc_sim* s, tc_mlp* mlp, int32_t window, double dv_max
     s->sur = nullptr;
     return TC_OK;
   }
-  if (s->precision != TC_FP32 || s->model != TC_MODEL_TP06)
-    return fail(TC_ERR_ARG, "the learned surrogate serves TC_FP32 simulations of TP06");
+  if (s->model != TC_MODEL_TP06)
+    return fail(TC_ERR_ARG, "the learned surrogate serves simulations of TP06");
   if (window < 1 || !(dv_max > 0) || !(dvdt_max > 0) || !(dv_neighbour >= 0) || !(rest_band >= 0))
     return fail(TC_ERR_ARG, "need window >= 1, dv_max > 0, dvdt_max > 0, dv_neighbour >= 0, rest_band >= 0");
   CUDA_TRY(cudaSetDevice(s->device));

@@ -65,6 +65,7 @@ _SIGS = {
                     C.c_int32, _P, C.POINTER(_P)],
     "tc_sim_size": [_P, _I64, _I64, _I64, _I32],
     "tc_sim_layout": [_P, _I32, _I64, _I32, _I32],
+    "tc_sim_staging": [_P, _I32, _I32, _I32, _I64],
     "tc_set_launch": [_P, C.c_int32, C.c_int32],
     "tc_autotune": [_P, C.c_int32, _I32, _I32, _D],
     "tc_set_graphs": [_P, C.c_int32],
@@ -340,6 +341,11 @@ class Simulation:
         _check(lib().tc_sim_layout(self._h, C.byref(nc), C.byref(ni), C.byref(th), C.byref(bps)))
         return {"n_components": nc.value, "n_internal": ni.value, "pcg_threads": th.value,
                 "blocks_per_sm": bps.value}
+
+    def staging(self):
+        nb, ns, mw, sm = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().tc_sim_staging(self._h, C.byref(nb), C.byref(ns), C.byref(mw), C.byref(sm)))
+        return {"blocks": nb.value, "staged_blocks": ns.value, "max_window": mw.value, "smem_bytes": sm.value}
 
     def set_launch(self, pcg_threads, blocks_per_sm):
         _check(lib().tc_set_launch(self._h, pcg_threads, blocks_per_sm))
