@@ -419,8 +419,23 @@ def surrogate_form(w, K, W, preroll, ms64, ms32, act64, stream, torch, apd=True,
                  "nodes": t.mesh.n_nodes,
                  "network_share": u["surrogate"] / max(1, u["surrogate"] + u["exact"]),
                  "seconds_fp64": ref["seconds"], "seconds_fp32_surrogate": got["seconds"]}
+    # the same network in FP64 tissue: what it gains at the same precision as the exact FP64 run
+    sim = tc.from_workload(w, stream=stream.cuda_stream, precision=tc.TC_FP64)
+    sim.set_surrogate(m, *SURROGATE_CHECK)
+    ms_d, st_d, prof_d = timed_steps(sim, w, K, W, stream, torch, preroll=preroll, usage=True)
+    act_d = sim.activation_times()
+    sim.close()
+    ut_d = st_d["usage_timed"]
+    both_d = (act_d >= 0) & (act64 >= 0)
+    fp64_tissue = {"value": n * K / (ms_d * 1e-3), "unit": "node-steps/s", "ms_per_step": ms_d / K,
+                   "speedup_vs_fp64_exact": ms64 / ms_d, "dtype": "f64 tissue, bf16 network (fp32 accumulate)",
+                   "network_share": ut_d["surrogate"] / max(1, ut_d["surrogate"] + ut_d["exact"]),
+                   "act_err_ms_max": float(np.abs(act_d[both_d] - act64[both_d]).max()) if both_d.any() else None,
+                   "kernels": {"ionic_ms": prof_d["ionic_ms"], "pcg_ms": prof_d["pcg_ms"],
+                               "surrogate_ms": prof_d["surrogate_ms"], "mlp_ms": prof_d["mlp_ms"]}}
     return {"value": n * K / (ms * 1e-3), "unit": "node-steps/s", "ms_per_step": ms / K,
             "speedup_vs_fp64": ms64 / ms, "speedup_vs_fp32": ms32 / ms if ms32 else None,
+            "fp64_tissue": fp64_tissue,
             "dtype": "f32 tissue, bf16 network (fp32 accumulate)",
             "timed_window_ms": [(preroll + W) * w.dt, (preroll + W + K) * w.dt],
             "window_steps": SURROGATE_CHECK[0],

@@ -815,10 +815,11 @@ __global__ void __launch_bounds__(Tp06Launch<T>::threads, Tp06Launch<T>::min_blo
     // the concentration logarithms of u^k, left by the previous step (FP64, when valid)
     T lg[4];
     const bool cache = a.log_cache != nullptr;
-    const bool valid = cache && *a.log_valid != 0;
+    bool valid = cache && *a.log_valid != 0;
     if (valid) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) lg[q] = a.log_cache[q * n + i];
+      valid = lg[0] == lg[0];   // NaN: the surrogate replaced this node's states since they were taken
     }
     iion = T(a.cm) * tp06_cell_step(V, u, a.cell, T(a.dt), cache ? lg : nullptr, valid);
 #pragma unroll

@@ -1005,24 +1005,25 @@ namespace tc {
 // cell, not the diffusion that drives the front).  Candidates get a compacted input row (18
 // states, V, window-mean stimulus; normalized, split BF16) at a position taken from *count, and
 // idx[pos] = node; everyone else stays with the exact model (flag 0) and is counted as such.
-__global__ void sur_features_kernel(int64_t n, const float* state, const float* V, const float* Vprev,
-                                    const float* dinv, const int32_t* stim_off, const int32_t* stim_ids,
+template <typename T>
+__global__ void sur_features_kernel(int64_t n, const T* state, const T* V, const T* Vprev,
+                                    const T* dinv, const int32_t* stim_off, const int32_t* stim_ids,
                                     const StimDev* stims, const long long* k_base, int k_off, int win, double cm,
                                     double dt, float dvdt_max, float v_rest, float rest_band, float dv_nbr,
                                     const int32_t* slice_ptr, const int32_t* col, const float* norm,
                                     __nv_bfloat16* a0, float* raw, int32_t* idx, int* count, uint8_t* flag,
                                     unsigned long long* counts) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool real = i < n && dinv[i] != 0.f;
+  const bool real = i < n && dinv[i] != T(0);
   bool cand = real;
   float vi = 0.f, is = 0.f;
   if (cand) {
-    vi = V[i];
+    vi = (float)V[i];
     const long long k0 = *k_base + k_off;
     double acc = 0.0;
     for (int s = 0; s < win; ++s) acc += stimulus_at(stim_off, stim_ids, stims, i, k0 + s);
     is = (float)(acc / win / cm);   // uA/mm^2 -> pA/pF
-    cand = is == 0.f && fabsf(vi - Vprev[i]) <= dvdt_max * (float)dt &&
+    cand = is == 0.f && fabsf(vi - (float)Vprev[i]) <= dvdt_max * (float)dt &&
            !(rest_band > 0.f && fabsf(vi - v_rest) <= rest_band);
   }
   if (cand && dv_nbr > 0.f) {
@@ -1030,7 +1031,7 @@ __global__ void sur_features_kernel(int64_t n, const float* state, const float* 
     const int beg = slice_ptr[s] + (int)(i & 31);
     const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
     float d = 0.f;
-    for (int j = 0; j < w; ++j) d = fmaxf(d, fabsf(V[col[beg + 32 * j]] - vi));
+    for (int j = 0; j < w; ++j) d = fmaxf(d, fabsf((float)V[col[beg + 32 * j]] - vi));
     cand = d <= dv_nbr;
   }
   if (i < n) flag[i] = 0;
@@ -1048,7 +1049,7 @@ __global__ void sur_features_kernel(int64_t n, const float* state, const float* 
   idx[pos] = (int32_t)i;
   float f[kMlpIn];
 #pragma unroll
-  for (int j = 0; j < 18; ++j) f[j] = state[j * n + i];
+  for (int j = 0; j < 18; ++j) f[j] = (float)state[j * n + i];
   f[18] = vi;
   f[19] = is;
   float xn[kMlpIn];
@@ -1067,9 +1068,11 @@ __global__ void sur_features_kernel(int64_t n, const float* state, const float* 
 // Candidates: decode the prediction (row pos, node idx[pos]), check it (finite, concentrations
 // positive, gates inside [0, 1] up to a small margin, |V' - V| <= dv_max) and commit: states <-
 // prediction, flag, the window's effective current.
+template <typename T>
 __global__ void sur_commit_kernel(const int* count, int64_t n, const int32_t* idx, const float* zout,
                                   const float* raw, const float* norm, double dt, int win, float dv_max,
-                                  float* state, uint8_t* flag, float* iion, unsigned long long* counts) {
+                                  T* state, uint8_t* flag, float* iion, unsigned long long* counts,
+                                  double* log_cache) {
   const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool have = pos < *count;
   bool ok = false;
@@ -1093,7 +1096,9 @@ __global__ void sur_commit_kernel(const int* count, int64_t n, const int32_t* id
     flag[i] = ok ? 1 : 0;
     if (ok) {
 #pragma unroll
-      for (int j = 0; j < 18; ++j) state[j * n + i] = j >= 5 ? fminf(fmaxf(y[j], 0.f), 1.f) : y[j];
+      for (int j = 0; j < 18; ++j) state[j * n + i] = T(j >= 5 ? fminf(fmaxf(y[j], 0.f), 1.f) : y[j]);
+      // the held logarithms no longer describe the states: the node's next exact step takes them anew
+      if (log_cache) log_cache[i] = __longlong_as_double(0x7ff8000000000000ll);
       // single cell: dV/dt = -I_ion + I_stim over the window (no stimulus here)
       iion[i] = raw[19 * n + i] - dv / (float)(win * dt);
     }
@@ -1113,10 +1118,18 @@ tc_status surrogate_prepare(tc_mlp* m, int64_t n) {
 
 tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
   CUDA_TRY(cudaMemsetAsync(q.count, 0, sizeof(int), st));
-  sur_features_kernel<<<blocks_for(q.n), 256, 0, st>>>(
-      q.n, q.state, q.V, q.Vprev, q.dinv, q.stim_off, q.stim_ids, q.stims, q.k_base, q.k_off, q.win, q.cm, q.dt,
-      q.dvdt_max, q.v_rest, q.rest_band, q.dv_nbr, q.slice_ptr, q.col, m->norm, q.a0, q.raw, q.idx, q.count,
-      q.flag, q.counts);
+  if (q.fp64)
+    sur_features_kernel<double><<<blocks_for(q.n), 256, 0, st>>>(
+        q.n, static_cast<const double*>(q.state), static_cast<const double*>(q.V),
+        static_cast<const double*>(q.Vprev), static_cast<const double*>(q.dinv), q.stim_off, q.stim_ids, q.stims,
+        q.k_base, q.k_off, q.win, q.cm, q.dt, q.dvdt_max, q.v_rest, q.rest_band, q.dv_nbr, q.slice_ptr, q.col,
+        m->norm, q.a0, q.raw, q.idx, q.count, q.flag, q.counts);
+  else
+    sur_features_kernel<float><<<blocks_for(q.n), 256, 0, st>>>(
+        q.n, static_cast<const float*>(q.state), static_cast<const float*>(q.V), static_cast<const float*>(q.Vprev),
+        static_cast<const float*>(q.dinv), q.stim_off, q.stim_ids, q.stims, q.k_base, q.k_off, q.win, q.cm, q.dt,
+        q.dvdt_max, q.v_rest, q.rest_band, q.dv_nbr, q.slice_ptr, q.col, m->norm, q.a0, q.raw, q.idx, q.count,
+        q.flag, q.counts);
   CUDA_TRY(cudaGetLastError());
   if (q.ev_mlp[0]) CUDA_TRY(cudaEventRecord(q.ev_mlp[0], st));
   if (m->gemm == kGemmTcgen05) {
@@ -1128,8 +1141,14 @@ tc_status surrogate_infer(tc_mlp* m, const SurrogateStep& q, cudaStream_t st) {
     CUDA_TRY(cudaMemcpyAsync(q.zout, m->z[kMlpLayers - 1], q.n * kMlpPad * sizeof(float), cudaMemcpyDeviceToDevice, st));
   }
   if (q.ev_mlp[1]) CUDA_TRY(cudaEventRecord(q.ev_mlp[1], st));
-  sur_commit_kernel<<<blocks_for(q.n), 256, 0, st>>>(q.count, q.n, q.idx, q.zout, q.raw, m->norm, q.dt, q.win,
-                                                     q.dv_max, q.state, q.flag, q.iion, q.counts);
+  if (q.fp64)
+    sur_commit_kernel<double><<<blocks_for(q.n), 256, 0, st>>>(q.count, q.n, q.idx, q.zout, q.raw, m->norm, q.dt,
+                                                               q.win, q.dv_max, static_cast<double*>(q.state),
+                                                               q.flag, q.iion, q.counts, q.log_cache);
+  else
+    sur_commit_kernel<float><<<blocks_for(q.n), 256, 0, st>>>(q.count, q.n, q.idx, q.zout, q.raw, m->norm, q.dt,
+                                                              q.win, q.dv_max, static_cast<float*>(q.state), q.flag,
+                                                              q.iion, q.counts, nullptr);
   CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }

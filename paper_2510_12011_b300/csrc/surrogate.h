@@ -11,13 +11,16 @@
 
 namespace tc {
 
-// One window start of the surrogate inside a TP06 FP32 simulation.
+// One window start of the surrogate inside a TP06 simulation (FP32 or FP64 tissue).
 struct SurrogateStep {
   int64_t n;                    // internal rows
-  float* state;                 // [18][n] TP06 states (written for nodes that pass the check)
-  const float* V;               // V^k
-  const float* Vprev;           // V^{k-1}
-  const float* dinv;            // 0 on padding rows (neither flagged nor counted)
+  int fp64;                     // element type of state, V, Vprev, dinv: double when set, else float
+  void* state;                  // [18][n] TP06 states (written for nodes that pass the check)
+  const void* V;                // V^k
+  const void* Vprev;            // V^{k-1}
+  const void* dinv;             // 0 on padding rows (neither flagged nor counted)
+  double* log_cache;            // FP64 tissue: [4][n] held concentration logarithms (or null); a
+                                // committed node's entry is marked stale (NaN in row 0)
   const int32_t* stim_off;
   const int32_t* stim_ids;
   const StimDev* stims;
