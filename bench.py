@@ -660,7 +660,11 @@ def batched_form(steps, stream, torch):
     by = pcg_launch_bytes(w.mesh.n_nodes, size["nnz"], n_int // 32, it_mean, vb=4)
     peak, kind = measured_peaks()
     out["kernels"] = {"ionic_ms_per_launch": prof["ionic_ms"] / max(prof["ionic_launches"], 1),
-                      "pcg_ms_per_launch": pcg_ms, "launches_per_step": 2}
+                      "pcg_ms_per_launch": pcg_ms,
+                      "launches_per_step": (prof["ionic_launches"] + prof["pcg_launches"]) / 30.0,
+                      "note": "the Mitchell-Schaeffer update runs inside the PCG launch (one persistent "
+                              "launch per time step)" if prof["ionic_launches"] == 0 else None}
+    by += 7 * 4 * w.mesh.n_nodes if prof["ionic_launches"] == 0 else 0   # fused update: V, V^{k-1}, h in; h, g1, g2, x0 out
     out["roofline_pcg"] = {"kernel": "pcg_step_kernel_512<float>", "bound": "hbm",
                            "achieved": by / (pcg_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                            "frac": by / (pcg_ms * 1e-3) / 1e9 / peak, "bytes_per_launch": by,

@@ -116,6 +116,8 @@ struct PcgArgs {
   int k_off;
   double dt, thr;
   double v_rest, lrt_thr;
+  int fuse_ms;                // 1: the Mitchell-Schaeffer update of the step runs inside this launch
+  IonicArgs<T> ion;           // its arguments (g1, g2 and x0 are the ones above)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -454,12 +456,10 @@ __device__ __forceinline__ void rhs_epilogue(const IonicArgs<T>& a, int64_t i, T
   a.x0[i] = T(2) * V - Vp;
 }
 
-// (a1) Ionic update, Mitchell-Schaeffer with a Rush-Larsen gate (state[0] = h).
+// (a1) Ionic update of node i, Mitchell-Schaeffer with a Rush-Larsen gate (state[0] = h), and
+// the node's right-hand-side inputs.
 template <typename T>
-__global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs<T> a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < a.n_bar) a.bar[i].count = 0u;
-  if (i >= a.n) return;
+__device__ __forceinline__ void ms_node(const IonicArgs<T>& a, int64_t i) {
   const T V = a.V[i], Vp = a.Vp[i];
   const MSConst& c = a.ms;
   const T v = (V - T(c.vmin)) * T(c.inv_range);
@@ -472,6 +472,14 @@ __global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs<T> a) {
   const T iion = -T(a.cm) * T(c.range) * (jin + jout);
   const T is = T(stimulus_at(a.stim_off, a.stim_ids, a.stims, i, *a.k_base + a.k_off));
   rhs_epilogue(a, i, V, Vp, iion, is);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ionic_ms_kernel(const IonicArgs<T> a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n_bar) a.bar[i].count = 0u;
+  if (i >= a.n) return;
+  ms_node(a, i);
 }
 
 // Advances the device step index after a group of steps (the last node of a captured graph).
@@ -509,6 +517,12 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
   if (a.log_valid && b == 0 && tid == 0) *a.log_valid = 1;
   int it = 0;
 
+  // (a1) inside the launch (Mitchell-Schaeffer): every block updates its rows, then a barrier,
+  // because the right-hand side gathers neighbours' g1 and g2
+  if (a.fuse_ms) {
+    for (int64_t i = r0 + tid; i < r1; i += THREADS) ms_node(a.ion, i);
+    if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
+  }
   // r0 = chi M (w - Cm x0) - dt K ((1-theta) V + theta x0) = M g1 - K g2
   T rho_t = T(0), zz_t = T(0);
   for (int s = s0 + warp; s < s1; s += NW) {
@@ -772,6 +786,14 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
         a.rep90[i] = t_k + a.dt * (vo - t90) / (vo - vn);
       if (a.lrt[i] < 0.0 && vo >= a.lrt_thr && vn < a.lrt_thr)
         a.lrt[i] = t_k + a.dt * (vo - a.lrt_thr) / (vo - vn);
+    }
+  }
+  // the last block of the component to get here (every block is past its last barrier wait)
+  // returns the barrier words to zero for the next launch on the stream
+  if (tid == 0 && nb > 1) {
+    if (atomicAdd(&bar->gen, 1u) == nb - 1) {
+      bar->count = 0u;
+      bar->gen = 0u;
     }
   }
   if (b == (unsigned)cb0 && tid == 0) {

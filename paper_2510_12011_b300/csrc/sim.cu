@@ -76,6 +76,7 @@ struct tc_sim {
   int32_t* blk_win = nullptr;
   size_t pcg_dyn_smem = 0;     // dynamic shared memory of the PCG launch (the largest staged window)
   int pcg_stage = 1;           // stage windows when they fit (TC_PCG_STAGE=0 turns it off)
+  int fuse_ms = 1;             // Mitchell-Schaeffer update inside the PCG launch (TC_FUSE_IONIC=0: own kernel)
   int32_t win_staged = 0, win_max = 0;   // blocks staged, largest window (entries) of the partition
   int32_t *comp_of_block = nullptr, *comp_block0 = nullptr;
   void *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
@@ -528,7 +529,10 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
     marks->push_back((*ev)++);
   }
   const int ion_blocks = (int)((s->n_int + kIonicThreads - 1) / kIonicThreads);
-  if (s->model == TC_MODEL_MS) {
+  const bool fused = s->model == TC_MODEL_MS && s->fuse_ms;
+  if (fused) {
+    // one launch per step: the update runs as the first phase of the PCG kernel below
+  } else if (s->model == TC_MODEL_MS) {
     ionic_ms_kernel<T><<<ion_blocks, kIonicThreads, 0, s->stream>>>(ia);
   } else {
     const int tpb = Tp06Launch<T>::threads;
@@ -576,6 +580,8 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   pa.k_off = k_off;
   pa.dt = s->dt;
   pa.thr = s->thr;
+  pa.fuse_ms = fused ? 1 : 0;
+  pa.ion = ia;
   if (ev) {
     CUDA_TRY(cudaEventRecord(pooled_event(s, *ev), s->stream));
     (*ev)++;
@@ -948,6 +954,7 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   s->nslices = sell.nslices;
   s->padded = sell.padded;
   s->pcg_stage = env_int("TC_PCG_STAGE", 1) != 0;
+  s->fuse_ms = env_int("TC_FUSE_IONIC", 1) != 0;
   try {
     s->slice_cmin.assign(sell.nslices, INT32_MAX);
     s->slice_cmax.assign(sell.nslices, -1);
@@ -1339,7 +1346,7 @@ tc_status tc_step(tc_sim* s, int64_t n_steps, tc_step_stats* stats) {
       cudaEventElapsedTime(&a, s->evpool[m], s->evpool[m + 1]);
       cudaEventElapsedTime(&b, s->evpool[m + 1], s->evpool[m + 2]);
       s->prof_acc.ionic_ms += a;
-      s->prof_acc.ionic_launches += 1;
+      s->prof_acc.ionic_launches += s->model == TC_MODEL_MS && s->fuse_ms ? 0 : 1;
       s->prof_acc.pcg_ms += b;
       s->prof_acc.pcg_launches += 1;
     }

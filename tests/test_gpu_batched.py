@@ -121,3 +121,29 @@ def test_layout_autotuner_over_sell_window_and_launch_shape():
         vs.append(sim.read())
         sim.close()
     assert np.abs(vs[0] - vs[1]).max() <= 1e-9 * max(1.0, np.abs(vs[1]).max())
+
+
+def test_one_launch_per_step_matches_two_launches():
+    """Mitchell-Schaeffer steps run as one persistent launch (the ionic update is the PCG kernel's
+    first phase; the barrier words are reset by the last block out): bitwise the same as the ionic
+    kernel followed by the PCG kernel, with graphs and with host launches, and one launch per step."""
+    import os
+    b = I.batched_slabs(count=6, seed=7, t_end=5.0)
+    w = b.workload
+    runs = {}
+    for fuse in ("1", "0"):
+        os.environ["TC_FUSE_IONIC"] = fuse
+        try:
+            sim = tc.from_workload(w, precision=tc.TC_FP32)
+        finally:
+            os.environ.pop("TC_FUSE_IONIC", None)
+        sim.step(100)                      # graphs
+        sim.set_profiling(True)
+        sim.reset_profile()
+        sim.step(7)                        # host launches, counted
+        prof = sim.profile()
+        runs[fuse] = (sim.read(), sim.activation_times(), prof)
+        sim.close()
+    assert np.array_equal(runs["1"][0], runs["0"][0]) and np.array_equal(runs["1"][1], runs["0"][1])
+    assert runs["1"][2]["ionic_launches"] == 0 and runs["1"][2]["pcg_launches"] == 7
+    assert runs["0"][2]["ionic_launches"] == 7 and runs["0"][2]["pcg_launches"] == 7
