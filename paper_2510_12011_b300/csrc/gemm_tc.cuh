@@ -352,6 +352,287 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
 }
 
+// ---- the pipelined forward: two row tiles per CTA, warp-specialised roles -------------------
+//
+// The kernel above runs a layer's MMAs and then its epilogue, so the tensor pipe idles while the
+// sixteen epilogue warps read the accumulator back.  This one keeps two 128-row tiles (slots A
+// and B) in flight with their accumulators in the two halves of tensor memory (2 x 256 columns):
+// while the epilogue warps finish layer l of one slot, the tensor cores run the next job of the
+// other.  Roles:
+//   * warp 16, lane 0 (producer): streams the weight images as 64-wide K-panels (one contiguous
+//     bulk copy each, <= 32 KB) through a two-stage ring, in the order the MMAs consume them;
+//   * warp 17, lane 0 (MMA issuer): per job (slot, layer) waits for the slot's operand, then per
+//     panel for its stage, issues the panel's four K-steps and commits to the stage's "empty"
+//     barrier; after the last panel it commits to the slot's "accumulator full" barrier;
+//   * warps 0-15 (epilogue): per job read the accumulator (tcgen05.ld), add the bias, apply SiLU
+//     and write the next layer's BF16 operand into the slot (or the output), then signal the
+//     slot's "operand ready" barrier; after a tile's last layer they load the next tile's inputs.
+// Job order per CTA: tile pairs (2i, 2i + 1) for i = blockIdx.x, blockIdx.x + gridDim.x, ...;
+// per pair layers 0..4, per layer slot A then slot B (B absent when the tile count is odd).
+// Every wait is bounded; a wait that gives up sets a shared abort flag that every role polls, the
+// epilogue warps leave together (a reduction over their named barrier), and the CTA frees its
+// tensor memory after the others have left.
+constexpr int kT2EpiThreads = 512;
+constexpr int kT2Threads = kT2EpiThreads + 64;
+constexpr uint32_t kT2Panel = 256u * 128u;                                  // one K-panel, 256 rows
+constexpr uint32_t kT2SmemBytes = 2 * kTcSmemA + 2 * kT2Panel + 1024 + kTcBias * 4;
+
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < kTcWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  return false;
+}
+
+// OR of `v` over the 512 epilogue threads (named barrier 1); also a barrier among them.
+__device__ __forceinline__ bool epi_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kT2EpiThreads)
+      : "memory");
+  return r != 0;
+}
+
+template <bool STORE>
+__global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFusedArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* const sAct0 = smem;                       // slot A operand, 128 rows x 256 K
+  uint8_t* const sW0 = smem + 2 * kTcSmemA;          // weight ring, two panels
+  float* sBias = reinterpret_cast<float*>(sW0 + 2 * kT2Panel);
+  __shared__ uint64_t full_b[2], empty_b[2], acc_b[2], act_b[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  volatile int* abort = &s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t M = a.M_dev ? (a.M < (int64_t)*a.M_dev ? a.M : (int64_t)*a.M_dev) : a.M;
+  const int64_t ntiles = (M + kTcRows - 1) / kTcRows;
+  const int64_t npairs = (ntiles + 1) / 2;
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full_b[i], 1);
+      mbar_init(&empty_b[i], 1);
+      mbar_init(&acc_b[i], 1);
+      mbar_init(&act_b[i], 1);
+    }
+    s_abort = 0;
+  }
+  {
+    int off = 0;
+    for (int l = 0; l < kMlpLayers; ++l) {
+      for (int c = tid; c < a.out[l]; c += kT2Threads) sBias[off + c] = a.bias[l][c];
+      off += a.out[l];
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  auto tile_exists = [&](int64_t pi, int x) { return 2 * pi + x < ntiles; };
+
+  if (warp == kT2EpiThreads / 32) {
+    // ---- producer: weight panels in consumption order ----
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t pi = blockIdx.x; pi < npairs && ok; pi += gridDim.x)
+        for (int l = 0; l < kMlpLayers && ok; ++l)
+          for (int x = 0; x < 2 && ok; ++x) {
+            if (!tile_exists(pi, x)) continue;
+            const int np = (a.in[l] + 63) / 64;
+            const uint32_t pbytes = (uint32_t)a.out[l] * 128u;
+            for (int pp = 0; pp < np; ++pp, ++g) {
+              const int st = g & 1;
+              if (g >= 2 && !mbar_wait_abort(&empty_b[st], ((g >> 1) - 1) & 1, abort)) {
+                ok = false;
+                *abort = 1;
+                break;
+              }
+              mbar_expect_tx(&full_b[st], pbytes);
+              bulk_copy_g2s(sW0 + st * kT2Panel, a.img[l] + (size_t)pp * pbytes, pbytes, &full_b[st]);
+            }
+          }
+      // the copies in flight land before the CTA's shared memory goes away
+      for (uint32_t k = g > 2 ? g - 2 : 0; k < g; ++k) mbar_wait(&full_b[k & 1], (k >> 1) & 1);
+    }
+  } else if (warp == kT2EpiThreads / 32 + 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      uint32_t g = 0, nact[2] = {0, 0};
+      bool ok = true;
+      for (int64_t pi = blockIdx.x; pi < npairs && ok; pi += gridDim.x)
+        for (int l = 0; l < kMlpLayers && ok; ++l)
+          for (int x = 0; x < 2 && ok; ++x) {
+            if (!tile_exists(pi, x)) continue;
+            if (!mbar_wait_abort(&act_b[x], nact[x] & 1, abort)) {
+              ok = false;
+              *abort = 1;
+              break;
+            }
+            ++nact[x];
+            tc_fence_after();
+            const int np = (a.in[l] + 63) / 64;
+            const uint32_t idesc = umma_idesc_bf16(kTcRows, a.out[l]);
+            const uint32_t tm = tmem + (uint32_t)(x * 256);
+            uint8_t* sAct = sAct0 + x * kTcSmemA;
+            for (int pp = 0; pp < np; ++pp, ++g) {
+              const int st = g & 1;
+              if (!mbar_wait_abort(&full_b[st], (g >> 1) & 1, abort)) {
+                ok = false;
+                *abort = 1;
+                break;
+              }
+              tc_fence_after();
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = umma_desc_sw128(smem_addr(sAct + pp * kTcRows * 128) + kk * 32u);
+                const uint64_t bd = umma_desc_sw128(smem_addr(sW0 + st * kT2Panel) + kk * 32u);
+                umma_bf16(tm, ad, bd, idesc, (pp > 0 || kk > 0) ? 1u : 0u);
+              }
+              umma_commit(&empty_b[st]);
+            }
+            if (ok) umma_commit(&acc_b[x]);
+          }
+      // the MMAs issued complete before tensor memory is freed
+      if (g > 0) mbar_wait(&empty_b[(g - 1) & 1], ((g - 1) >> 1) & 1);
+    }
+  } else {
+    // ---- epilogue warps ----
+    const int q = warp & 3;        // tensor-memory lane quarter of this warp
+    const int cg = warp >> 2;      // column quarter handled by this warp
+    const int row = 32 * q + lane;
+    uint32_t nacc[2] = {0, 0};
+    auto load_inputs = [&](int64_t tile, int x) {
+      uint8_t* sAct = sAct0 + x * kTcSmemA;
+      const int64_t row0 = tile * kTcRows;
+      for (int e = tid; e < kTcRows * 8; e += kT2EpiThreads) {
+        const int r = e >> 3, c = e & 7;
+        const int64_t gr = row0 + r;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gr < M) v = *reinterpret_cast<const uint4*>(a.a0 + gr * kMlpIn0 + c * 8);
+        *reinterpret_cast<uint4*>(sAct + sw128_offset(0, kTcRows, r, c)) = v;
+      }
+      fence_proxy_async_smem();
+      epi_sync_or(false);
+      if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&act_b[x])) : "memory");
+    };
+    bool stop = false;
+    if ((int64_t)blockIdx.x < npairs) {
+      for (int x = 0; x < 2; ++x)
+        if (tile_exists(blockIdx.x, x)) load_inputs(2 * (int64_t)blockIdx.x + x, x);
+    }
+    for (int64_t pi = blockIdx.x; pi < npairs && !stop; pi += gridDim.x) {
+      int boff = 0;
+      for (int l = 0; l < kMlpLayers && !stop; ++l) {
+        const int N = a.out[l];
+        for (int x = 0; x < 2 && !stop; ++x) {
+          if (!tile_exists(pi, x)) continue;
+          const bool ok = mbar_wait_abort(&acc_b[x], nacc[x] & 1, abort);
+          ++nacc[x];
+          if (epi_sync_or(!ok)) {
+            *abort = 1;
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          uint8_t* sAct = sAct0 + x * kTcSmemA;
+          const int64_t grow = (2 * pi + x) * kTcRows + row;
+          const bool valid = grow < M;
+          const int cols = N / 4 >= 32 ? N / 4 : 32;
+          const int cbeg = cg * cols;
+          if (cbeg < N) {
+            // one 32-column chunk per wait (the other slot's MMAs run meanwhile; fewer live registers)
+            const int nch = cols / 32;
+            for (int ch = 0; ch < nch; ++ch) {
+              const int c0 = cbeg + 32 * ch;
+              uint32_t raw[32];
+              tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(x * 256 + c0), raw);
+              tmem_wait_ld();
+              float v[32];
+              const float4* b4 = reinterpret_cast<const float4*>(sBias + boff + c0);
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                const float4 bb = b4[j >> 2];
+                v[j] = __uint_as_float(raw[j]) + bb.x;
+                v[j + 1] = __uint_as_float(raw[j + 1]) + bb.y;
+                v[j + 2] = __uint_as_float(raw[j + 2]) + bb.z;
+                v[j + 3] = __uint_as_float(raw[j + 3]) + bb.w;
+              }
+              if (l + 1 < kMlpLayers) {
+                if (STORE && valid && a.z[l]) {
+                  float* zp = a.z[l] + grow * N + c0;
+#pragma unroll
+                  for (int j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4*>(zp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+                __align__(16) __nv_bfloat162 h[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) h[j] = __floats2bfloat162_rn(silu_fast(v[2 * j]), silu_fast(v[2 * j + 1]));
+                const int panel = c0 >> 6, chunk0 = (c0 & 63) >> 3;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  *reinterpret_cast<uint4*>(sAct + sw128_offset(panel, kTcRows, row, chunk0 + u)) =
+                      reinterpret_cast<const uint4*>(h)[u];
+                if (STORE && valid && a.act[l + 1]) {
+                  __nv_bfloat16* ap = a.act[l + 1] + grow * N + c0;
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) reinterpret_cast<uint4*>(ap)[u] = reinterpret_cast<const uint4*>(h)[u];
+                }
+              } else if (valid) {
+                float* yp = a.y + grow * kMlpPad + c0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 4)
+                  *reinterpret_cast<float4*>(yp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                if (STORE && a.z[l]) {
+                  float* zp = a.z[l] + grow * N + c0;
+#pragma unroll
+                  for (int j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4*>(zp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+              }
+            }
+          }
+          // the accumulator has been read and (below the last layer) the next operand written
+          tc_fence_before();
+          if (l + 1 < kMlpLayers) {
+            fence_proxy_async_smem();
+            epi_sync_or(false);
+            if (tid == 0)
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&act_b[x])) : "memory");
+          } else {
+            epi_sync_or(false);
+            // the slot's last MMA has completed: its operand may take the next pair's inputs
+            const int64_t npi = pi + gridDim.x;
+            if (npi < npairs && tile_exists(npi, x)) load_inputs(2 * npi + x, x);
+          }
+        }
+        boff += N;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *abort) atomicOr(a.err, 1);
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 // Weight image of one layer: W^T [N][Kin] BF16 (row-major) -> swizzled K-major panels of 64
 // (Kin < 64 is zero-padded inside its panel).
 static __global__ void weight_image_kernel(const __nv_bfloat16* wt, int N, int Kin, uint8_t* img) {

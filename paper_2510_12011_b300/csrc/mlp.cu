@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -42,6 +43,7 @@ struct tc_mlp {
   std::vector<float> norm_host;
   int64_t adam_t = 0;
   int gemm = kGemmTcgen05;
+  int fused_kernel = 2;   // forward kernel: 2 = two pipelined tiles per CTA, 1 = one tile (TC_MLP_KERNEL)
   // training workspace (sized for the largest batch seen)
   int64_t ws_rows = 0;
   __nv_bfloat16* act[kMlpLayers] = {nullptr};   // A_l, [rows][op_in_l] (layer 0: split input)
@@ -460,11 +462,20 @@ tc_status forward_tc(tc_mlp* m, int64_t M, const __nv_bfloat16* act0, float* y, 
   a.y = y;
   a.err = err;
   const int64_t tiles = (M + kTcRows - 1) / kTcRows;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, m->num_sms));
-  if (store_hidden)
-    mlp_fused_kernel<true><<<grid, kTcThreads, kTcSmemBytes, st>>>(a);
-  else
-    mlp_fused_kernel<false><<<grid, kTcThreads, kTcSmemBytes, st>>>(a);
+  if (m->fused_kernel == 2) {
+    // two tiles per CTA (pipelined roles)
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, m->num_sms));
+    if (store_hidden)
+      mlp_fused2_kernel<true><<<grid, kT2Threads, kT2SmemBytes, st>>>(a);
+    else
+      mlp_fused2_kernel<false><<<grid, kT2Threads, kT2SmemBytes, st>>>(a);
+  } else {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, m->num_sms));
+    if (store_hidden)
+      mlp_fused_kernel<true><<<grid, kTcThreads, kTcSmemBytes, st>>>(a);
+    else
+      mlp_fused_kernel<false><<<grid, kTcThreads, kTcSmemBytes, st>>>(a);
+  }
   CUDA_TRY(cudaGetLastError());
   return TC_OK;
 }
@@ -629,10 +640,18 @@ tc_status tc_mlp_create(uint64_t seed, tc_mlp** out) {
   }
   if (e == cudaSuccess) e = cudaMalloc(&m->img, img_total);
   cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  {
+    const char* k = std::getenv("TC_MLP_KERNEL");
+    m->fused_kernel = k && std::atoi(k) == 1 ? 1 : 2;
+  }
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   e = cudaFuncSetAttribute(mlp_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_fused2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT2SmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_fused2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT2SmemBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_nt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_nt_smem_bytes(256));
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute"));

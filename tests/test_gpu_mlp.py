@@ -179,3 +179,35 @@ def test_tensor_core_gemm_matches_fp32_reference(M, N, K):
     tol = 1e-5 * K ** 0.5 * (a.float().abs().max() * b.float().abs().max()).item()
     assert (got - ref).abs().max().item() <= max(tol, 1e-4), (got - ref).abs().max().item()
 
+
+
+def test_pipelined_forward_equals_single_tile_forward():
+    """The forward kernel that keeps two row tiles in flight per CTA (warp-specialised producer,
+    MMA and epilogue roles) issues the same MMAs in the same K order and the same epilogue as the
+    one-tile kernel: bitwise the same outputs, for tile counts that are odd, even, a single ragged
+    tile, and more than one pair per CTA; and the same gradients (the training forward stores
+    the hidden layers)."""
+    import os
+    p = _params(seed=9)
+    old = os.environ.get("TC_MLP_KERNEL")
+    try:
+        os.environ["TC_MLP_KERNEL"] = "1"
+        m1 = tc.Mlp(seed=3)
+    finally:
+        if old is None:
+            os.environ.pop("TC_MLP_KERNEL", None)
+        else:
+            os.environ["TC_MLP_KERNEL"] = old
+    m2 = tc.Mlp(seed=3)
+    m1.set_params(p)
+    m2.set_params(p)
+    rng = np.random.default_rng(12)
+    for rows in (1, 127, 128, 129, 3 * 128 + 5, 148 * 2 * 128 * 2 + 77):
+        x = rng.normal(size=(rows, 20)).astype(np.float32)
+        assert np.array_equal(m1.forward(x), m2.forward(x)), rows
+    x = rng.normal(size=(777, 20)).astype(np.float32)
+    t = rng.normal(size=(777, 19)).astype(np.float32)
+    l1, g1 = m1.gradients(x, t)
+    l2, g2 = m2.gradients(x, t)
+    # the loss is summed with FP32 atomics (its order varies run to run); the gradients are not
+    assert abs(l1 - l2) <= 1e-6 * abs(l1) and np.array_equal(g1, g2)
