@@ -39,14 +39,14 @@ from paper_2510_12011_b300 import inputs as I  # noqa: E402
 METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + activation "
           "capture); FP32 precision form alongside")
 # FP64 pipe work of one ionic_tp06_kernel<double> launch per node, from the ncu capture in
-# profiles/ (sm__inst_executed_pipe_fp64.sum x 32 lanes / nodes); used to turn the live launch
-# time into an achieved FP64 instruction rate.
-TP06_FP64_INSTR_PER_NODE = 918.0
-TP06_FP64_DRAM_BYTES_PER_LAUNCH = 141.53e6   # dram read + write of the same capture
+# profiles/ (sm__inst_executed_pipe_fp64 of peak x 2 per clock x 148 SMs x cycles / nodes); used to
+# turn the live launch time into an achieved FP64 instruction rate.
+TP06_FP64_INSTR_PER_NODE = 914.0
+TP06_FP64_DRAM_BYTES_PER_LAUNCH = 142.57e6   # dram read + write of the same capture
 # dram read + write of one pcg_step_kernel_1024<double> launch on the large slab (ncu capture in
-# profiles/, a launch of a 23-step run averaging 8.65 CG iterations per launch)
-PCG_FP64_DRAM_BYTES_PER_LAUNCH = 0.637e9
-PCG_FP64_CAPTURE_ITERATIONS = 8.65
+# profiles/, a launch after the 40 ms pre-roll: 11 CG iterations)
+PCG_FP64_DRAM_BYTES_PER_LAUNCH = 0.679e9
+PCG_FP64_CAPTURE_ITERATIONS = 11.0
 
 
 def parse():
