@@ -160,11 +160,15 @@ tc_status tc_sim_layout(const tc_sim* sim, int32_t* n_components, int64_t* n_int
  * order the columns those rows touch form a band (the block's window).  When the window fits the
  * shared memory left per block at the launch shape, the block copies it into shared memory after
  * each grid barrier and its gathers read shared memory; otherwise they read global memory.  The
- * results are bitwise the same either way.  Reports the number of blocks, how many stage their
- * window, the largest window (entries) and the launch's dynamic shared memory (bytes); any pointer
- * may be NULL.  The environment variable TC_PCG_STAGE=0, read at tc_assemble, turns staging off. */
+ * results are bitwise the same either way.  When every block's columns span fewer than 65,536
+ * entries, the column indices of the RHS pass and the A-products are also read as 16-bit offsets
+ * from the block's window start (half the index stream; again bitwise the same results).  Reports
+ * the number of blocks, how many stage their window, the largest window (entries), the launch's
+ * dynamic shared memory (bytes) and whether the 16-bit offsets are in use; any pointer may be
+ * NULL.  The environment variables TC_PCG_STAGE=0 and TC_PCG_IDX16=0, read at tc_assemble, turn
+ * staging (and with it the offsets) and the offsets off. */
 tc_status tc_sim_staging(const tc_sim* sim, int32_t* blocks, int32_t* staged_blocks, int32_t* max_window,
-                         int64_t* smem_bytes);
+                         int64_t* smem_bytes, int32_t* idx16);
 
 /* tc_set_launch: PCG launch shape (512 or 1024 threads per block, blocks per SM, capped by the
  * occupancy of the cooperative launch).  Errors: TC_ERR_ARG (shape or too many components). */

@@ -89,7 +89,8 @@ struct PcgArgs {
   const int32_t* comp_of_block;   // connected component (independent problem) of each block
   const int32_t* comp_block0;     // first block of each component, n_comp + 1 entries
   const int32_t* blk_win;         // per block (lo, len): the block's window of gathered columns,
-                                  // staged in shared memory when len > 0
+                                  // staged in shared memory when len > 0 (lo set for every block)
+  const uint16_t* col16;          // column - lo of the slice's block (or null: 32-bit columns only)
   const T* g1;
   const T* g2;
   T* x;                       // in: x0, out: V^{k+1}
@@ -281,6 +282,11 @@ __device__ __forceinline__ float ld_hint(const float* p, uint64_t pol) {
   asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ int ld_hint(const uint16_t* p, uint64_t pol) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return (int)v;
+}
 __device__ __forceinline__ int ld_hint(const int32_t* p, uint64_t pol) {
   int v;
   asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
@@ -314,8 +320,8 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 constexpr int kSellUnroll4 = 0;
 constexpr int kSellChunk8 = 1;
 
-template <int SHAPE, typename T, typename XF>
-__device__ __forceinline__ T sell_dot_f(const int32_t* __restrict__ col, const T* __restrict__ val,
+template <int SHAPE, typename T, typename XF, typename I>
+__device__ __forceinline__ T sell_dot_f(const I* __restrict__ col, const T* __restrict__ val,
                                         int beg, int w, XF xf, uint64_t pol = 0) {
   T acc0 = T(0), acc1 = T(0);
   if constexpr (SHAPE == kSellChunk8) {
@@ -325,7 +331,7 @@ __device__ __forceinline__ T sell_dot_f(const int32_t* __restrict__ col, const T
       T v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        c[u] = j + u < w ? __ldg(col + e + 32 * u) : 0;
+        c[u] = j + u < w ? (int)__ldg(col + e + 32 * u) : 0;
         v[u] = j + u < w ? __ldg(val + e + 32 * u) : T(0);
       }
       T xv[8];
@@ -406,8 +412,8 @@ __host__ __device__ constexpr int pcg_sell_shape() {
 }
 
 // Two value streams over the same pattern: am = sum M_ij g1_j, ak = sum K_ij g2_j.
-template <typename T>
-__device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const T* __restrict__ vm,
+template <typename T, typename I>
+__device__ __forceinline__ void sell_dot2(const I* __restrict__ col, const T* __restrict__ vm,
                                           const T* __restrict__ vk, int beg, int w,
                                           const T* __restrict__ g1, const T* __restrict__ g2,
                                           T& am, T& ak) {
@@ -417,7 +423,7 @@ __device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const
   int j = 0;
   for (; j + 2 <= w; j += 2) {
     const int e = beg + 32 * j;
-    const int c0 = __ldg(col + e), c1 = __ldg(col + e + 32);
+    const int c0 = (int)__ldg(col + e), c1 = (int)__ldg(col + e + 32);
     const T m0 = ld_hint(vm + e, pol), m1 = ld_hint(vm + e + 32, pol);
     const T k0 = ld_hint(vk + e, pol), k1 = ld_hint(vk + e + 32, pol);
     const T a0 = __ldg(g1 + c0), a1 = __ldg(g1 + c1);
@@ -429,7 +435,7 @@ __device__ __forceinline__ void sell_dot2(const int32_t* __restrict__ col, const
   }
   for (; j < w; ++j) {
     const int e = beg + 32 * j;
-    const int c = __ldg(col + e);
+    const int c = (int)__ldg(col + e);
     am = fmaT(ld_hint(vm + e, pol), __ldg(g1 + c), am);
     ak = fmaT(ld_hint(vk + e, pol), __ldg(g2 + c), ak);
   }
@@ -523,13 +529,21 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
     for (int64_t i = r0 + tid; i < r1; i += THREADS) ms_node(a.ion, i);
     if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
   }
+  // The block's window (blk_win: lo, len): its columns lie in [lo, lo + span); with col16 every
+  // entry's column is stored as a 16-bit offset from lo (half the index stream).  len > 0 when the
+  // window is staged in shared memory (see the loop below).
+  const int win_lo = a.blk_win[2 * b], win_len = a.blk_win[2 * b + 1];
+  const bool use16 = a.col16 != nullptr;
   // r0 = chi M (w - Cm x0) - dt K ((1-theta) V + theta x0) = M g1 - K g2
   T rho_t = T(0), zz_t = T(0);
   for (int s = s0 + warp; s < s1; s += NW) {
     const int beg = a.slice_ptr[s] + lane;
     const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
     T am, ak;
-    sell_dot2(a.col, a.vM, a.vK, beg, w, a.g1, a.g2, am, ak);
+    if (use16)
+      sell_dot2(a.col16, a.vM, a.vK, beg, w, a.g1 + win_lo, a.g2 + win_lo, am, ak);
+    else
+      sell_dot2(a.col, a.vM, a.vK, beg, w, a.g1, a.g2, am, ak);
     const int64_t row = (int64_t)s * 32 + lane;
     if (row < a.n) {
       const T rr = am - ak;
@@ -577,7 +591,6 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
   // the product's gathers then read shared memory instead of waiting on L2 for every entry.
   extern __shared__ __align__(16) unsigned char s_dyn[];
   T* s_x = reinterpret_cast<T*>(s_dyn);
-  const int win_lo = a.blk_win[2 * b], win_len = a.blk_win[2 * b + 1];
   const bool staged = win_len > 0;
   while (flag == 0 && it < a.max_iter) {
     // p = z + beta p and q = A p, formed as q = A z + beta q (A p_k = A z_k + beta A p_{k-1}):
@@ -605,13 +618,24 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
       stage_window<THREADS>(s_x, a.z, win_lo, win_len);
       __syncthreads();
     }
-    // the product over the block's slices; `from_smem` selects the gather source at compile time
-    auto product = [&](auto from_smem) {
+    // the product over the block's slices; `from_smem` selects the gather source and `idx16` the
+    // index stream at compile time
+    auto product = [&](auto from_smem, auto idx16) {
       constexpr bool kSmem = decltype(from_smem)::value;
+      constexpr bool k16 = decltype(idx16)::value;
       auto xf = [&](int c) -> T {
-        if constexpr (kSmem) return s_x[c - win_lo];
-        else return a.z[c];
+        if constexpr (kSmem) {
+          if constexpr (k16) return s_x[c];
+          else return s_x[c - win_lo];
+        } else {
+          if constexpr (k16) return a.z[win_lo + c];
+          else return a.z[c];
+        }
       };
+      const auto* colp = [&]() {
+        if constexpr (k16) return a.col16;
+        else return a.col;
+      }();
       for (int s = s0 + warp; s < s0 + n_whole; s += NW) {
         const int beg = a.slice_ptr[s] + lane;
         const int w = (a.slice_ptr[s + 1] - a.slice_ptr[s]) >> 5;
@@ -625,7 +649,7 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
         if constexpr (sizeof(T) == 4) {
           if (real) load_row(row, zr, pr, qr);
         }
-        const T acc = sell_dot_f<pcg_sell_shape<T>()>(a.col, a.vA, beg, w, xf, pol_a);
+        const T acc = sell_dot_f<pcg_sell_shape<T>()>(colp, a.vA, beg, w, xf, pol_a);
         if constexpr (sizeof(T) == 8) {
           if (real) load_row(row, zr, pr, qr);
         }
@@ -645,7 +669,7 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
           if constexpr (sizeof(T) == 4) {
             if (c == 0 && real) load_row(row, zr, pr, qr);
           }
-          s_part[warp * 32 + lane] = sell_dot_f<pcg_sell_shape<T>()>(a.col, a.vA, beg + 32 * j0, j1 - j0, xf, pol_a);
+          s_part[warp * 32 + lane] = sell_dot_f<pcg_sell_shape<T>()>(colp, a.vA, beg + 32 * j0, j1 - j0, xf, pol_a);
         }
         __syncthreads();
         if (c == 0 && real) {
@@ -656,10 +680,13 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
         }
       }
     };
-    if (staged)
-      product(std::true_type{});
-    else
-      product(std::false_type{});
+    if (staged) {
+      if (use16) product(std::true_type{}, std::true_type{});
+      else product(std::true_type{}, std::false_type{});
+    } else {
+      if (use16) product(std::false_type{}, std::true_type{});
+      else product(std::false_type{}, std::false_type{});
+    }
     {
       double v1[1] = {double(pq_t)};
       block_sum<THREADS, 1>(v1, s_red);
@@ -821,6 +848,17 @@ __global__ void __launch_bounds__(1024, 1) pcg_step_kernel_1024(const PcgArgs<T>
 template <typename T>
 __global__ void __maxnreg__(64) pcg_step_kernel_512(const PcgArgs<T> a) {
   pcg_step<512, T>(a);
+}
+
+// col16[e] = col[e] - lo of the PCG block that owns entry e's slice (one CTA per PCG block; every
+// column of the block's slices lies in [lo, lo + 65536), checked on the host).
+static __global__ void col16_kernel(const int32_t* __restrict__ blk_slice, const int32_t* __restrict__ slice_ptr,
+                                    const int32_t* __restrict__ col, const int32_t* __restrict__ blk_win,
+                                    uint16_t* __restrict__ col16) {
+  const int b = blockIdx.x;
+  const int lo = blk_win[2 * b];
+  const int e0 = slice_ptr[blk_slice[b]], e1 = slice_ptr[blk_slice[b + 1]];
+  for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x) col16[e] = (uint16_t)(col[e] - lo);
 }
 
 // Standalone y = Op x (the SpMV of Algorithm 1) for operator checks and bandwidth runs.

@@ -78,6 +78,9 @@ struct tc_sim {
   int pcg_stage = 1;           // stage windows when they fit (TC_PCG_STAGE=0 turns it off)
   int fuse_ms = 1;             // Mitchell-Schaeffer update inside the PCG launch (TC_FUSE_IONIC=0: own kernel)
   int32_t win_staged = 0, win_max = 0;   // blocks staged, largest window (entries) of the partition
+  int pcg_idx16 = 1;           // 16-bit column offsets when every window spans < 65536 (TC_PCG_IDX16=0: off)
+  bool use16 = false;
+  uint16_t* col16 = nullptr;   // column - lo of the entry's PCG block (padded entries)
   int32_t *comp_of_block = nullptr, *comp_block0 = nullptr;
   void *vM = nullptr, *vK = nullptr, *vA = nullptr, *dinv = nullptr;
   void* V[3] = {nullptr, nullptr, nullptr};
@@ -391,6 +394,7 @@ tc_status set_partition(tc_sim* s) {
   // block at this launch shape; the dynamic shared memory of the launch is the largest staged one.
   std::vector<int32_t> win(2 * (size_t)s->nblocks, 0);
   size_t dyn = 0;
+  int64_t span_max = INT64_MAX;   // widest column range of a block (16-bit offsets need < 65536)
   s->win_staged = 0;
   s->win_max = 0;
   if (s->pcg_stage && !s->slice_cmin.empty()) {
@@ -405,6 +409,7 @@ tc_status set_partition(tc_sim* s) {
     const int env_cap = env_int("TC_PCG_STAGE_CAP", 0);
     if (env_cap > 0) cap = std::min<int64_t>(cap, env_cap);
     int64_t used = 0;
+    span_max = 0;
     for (int b = 0; b < s->nblocks; ++b) {
       int32_t lo = INT32_MAX, hi = -1;
       for (int32_t sl = bs[b]; sl < bs[b + 1]; ++sl) {
@@ -415,8 +420,9 @@ tc_status set_partition(tc_sim* s) {
       lo = lo / 4 * 4;
       const int64_t len = std::min<int64_t>(((int64_t)hi + 1 - lo + 3) / 4 * 4, s->n_int - lo);
       s->win_max = std::max<int32_t>(s->win_max, (int32_t)len);
+      span_max = std::max<int64_t>(span_max, (int64_t)hi + 1 - lo);
+      win[2 * b] = lo;
       if (len <= cap) {
-        win[2 * b] = lo;
         win[2 * b + 1] = (int32_t)len;
         used = std::max(used, len);
         s->win_staged += 1;
@@ -428,7 +434,7 @@ tc_status set_partition(tc_sim* s) {
       int bps2 = 0;
       CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, pcg_kernel(s), s->pcg_threads, dyn));
       if (bps2 < per_sm) {   // cannot stay co-resident with the windows: gather from global memory
-        std::fill(win.begin(), win.end(), 0);
+        for (int b = 0; b < s->nblocks; ++b) win[2 * b + 1] = 0;
         dyn = 0;
         s->win_staged = 0;
       }
@@ -448,6 +454,15 @@ tc_status set_partition(tc_sim* s) {
   CUDA_TRY(cudaMemcpy(s->blk_slice, bs.data(), bs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(s->comp_of_block, cob.data(), cob.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(s->comp_block0, cb0.data(), cb0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  // 16-bit column offsets from each block's window start (the index stream of the RHS pass and
+  // the A-products at half the bytes), when every block's columns span fewer than 65,536 entries
+  s->use16 = s->pcg_idx16 && s->pcg_stage && span_max <= 65536 && s->padded > 0;
+  if (s->use16) {
+    if (!s->col16) TRY(dalloc(s, &s->col16, (size_t)s->padded));
+    col16_kernel<<<s->nblocks, 256, 0, s->stream>>>(s->blk_slice, s->slice_ptr, s->col, s->blk_win, s->col16);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+  }
   drop_graphs(s);
   return TC_OK;
 }
@@ -549,6 +564,7 @@ tc_status launch_step(tc_sim* s, int iv, int k_off, size_t* ev, std::vector<size
   pa.dinv = static_cast<const T*>(s->dinv);
   pa.blk_slice = s->blk_slice;
   pa.blk_win = s->blk_win;
+  pa.col16 = s->use16 ? s->col16 : nullptr;
   pa.comp_of_block = s->comp_of_block;
   pa.comp_block0 = s->comp_block0;
   pa.g1 = static_cast<const T*>(s->g1);
@@ -955,6 +971,7 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   s->padded = sell.padded;
   s->pcg_stage = env_int("TC_PCG_STAGE", 1) != 0;
   s->fuse_ms = env_int("TC_FUSE_IONIC", 1) != 0;
+  s->pcg_idx16 = env_int("TC_PCG_IDX16", 1) != 0;
   try {
     s->slice_cmin.assign(sell.nslices, INT32_MAX);
     s->slice_cmax.assign(sell.nslices, -1);
@@ -1095,9 +1112,10 @@ tc_status tc_sim_layout(const tc_sim* s, int32_t* n_components, int64_t* n_inter
 }
 
 tc_status tc_sim_staging(const tc_sim* s, int32_t* blocks, int32_t* staged_blocks, int32_t* max_window,
-                         int64_t* smem_bytes) {
+                         int64_t* smem_bytes, int32_t* idx16) {
   clear_error();
   if (!s) return fail(TC_ERR_ARG, "sim must not be NULL");
+  if (idx16) *idx16 = s->use16 ? 1 : 0;
   if (blocks) *blocks = s->nblocks;
   if (staged_blocks) *staged_blocks = s->win_staged;
   if (max_window) *max_window = s->win_max;

@@ -65,7 +65,7 @@ _SIGS = {
                     C.c_int32, _P, C.POINTER(_P)],
     "tc_sim_size": [_P, _I64, _I64, _I64, _I32],
     "tc_sim_layout": [_P, _I32, _I64, _I32, _I32],
-    "tc_sim_staging": [_P, _I32, _I32, _I32, _I64],
+    "tc_sim_staging": [_P, _I32, _I32, _I32, _I64, _I32],
     "tc_set_launch": [_P, C.c_int32, C.c_int32],
     "tc_autotune": [_P, C.c_int32, _I32, _I32, _D],
     "tc_set_graphs": [_P, C.c_int32],
@@ -343,9 +343,10 @@ class Simulation:
                 "blocks_per_sm": bps.value}
 
     def staging(self):
-        nb, ns, mw, sm = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
-        _check(lib().tc_sim_staging(self._h, C.byref(nb), C.byref(ns), C.byref(mw), C.byref(sm)))
-        return {"blocks": nb.value, "staged_blocks": ns.value, "max_window": mw.value, "smem_bytes": sm.value}
+        nb, ns, mw, sm, i16 = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
+        _check(lib().tc_sim_staging(self._h, C.byref(nb), C.byref(ns), C.byref(mw), C.byref(sm), C.byref(i16)))
+        return {"blocks": nb.value, "staged_blocks": ns.value, "max_window": mw.value, "smem_bytes": sm.value,
+                "idx16": bool(i16.value)}
 
     def set_launch(self, pcg_threads, blocks_per_sm):
         _check(lib().tc_set_launch(self._h, pcg_threads, blocks_per_sm))
