@@ -165,8 +165,9 @@ tc_status tc_sim_layout(const tc_sim* sim, int32_t* n_components, int64_t* n_int
  * from the block's window start (half the index stream; again bitwise the same results).  Reports
  * the number of blocks, how many stage their window, the largest window (entries), the launch's
  * dynamic shared memory (bytes) and whether the 16-bit offsets are in use; any pointer may be
- * NULL.  The environment variables TC_PCG_STAGE=0 and TC_PCG_IDX16=0, read at tc_assemble, turn
- * staging (and with it the offsets) and the offsets off. */
+ * NULL.  Staging is off unless the environment variable TC_PCG_STAGE=1 (read at tc_assemble) asks
+ * for it or tc_autotune picks it (measured on B300 it pays only where the windows are small next
+ * to a block's rows: the gathers mostly hit L1 otherwise); TC_PCG_IDX16=0 turns the offsets off. */
 tc_status tc_sim_staging(const tc_sim* sim, int32_t* blocks, int32_t* staged_blocks, int32_t* max_window,
                          int64_t* smem_bytes, int32_t* idx16);
 
@@ -175,8 +176,10 @@ tc_status tc_sim_staging(const tc_sim* sim, int32_t* blocks, int32_t* staged_blo
 tc_status tc_set_launch(tc_sim* sim, int32_t pcg_threads, int32_t blocks_per_sm);
 
 /* tc_autotune: time trial_steps steps with every candidate launch shape (1024x1, 512x1, 512x2),
- * restoring the state after each trial, and keep the fastest.  Reports the choice and its time
- * per step (any pointer may be NULL).  The state and step index are unchanged on return. */
+ * each with and without the PCG's shared-memory windows (tc_sim_staging), restoring the state
+ * after each trial, and keep the fastest.  Reports the launch shape and its time per step (any
+ * pointer may be NULL; the staging choice through tc_sim_staging).  The state and step index are
+ * unchanged on return. */
 tc_status tc_autotune(tc_sim* sim, int32_t trial_steps, int32_t* pcg_threads,
                       int32_t* blocks_per_sm, double* best_ms_per_step);
 

@@ -75,7 +75,7 @@ struct tc_sim {
   std::vector<int32_t> slice_cmin, slice_cmax;
   int32_t* blk_win = nullptr;
   size_t pcg_dyn_smem = 0;     // dynamic shared memory of the PCG launch (the largest staged window)
-  int pcg_stage = 1;           // stage windows when they fit (TC_PCG_STAGE=0 turns it off)
+  int pcg_stage = 0;           // stage windows when they fit (TC_PCG_STAGE=1, or chosen by tc_autotune)
   int fuse_ms = 1;             // Mitchell-Schaeffer update inside the PCG launch (TC_FUSE_IONIC=0: own kernel)
   int32_t win_staged = 0, win_max = 0;   // blocks staged, largest window (entries) of the partition
   int pcg_idx16 = 1;           // 16-bit column offsets when every window spans < 65536 (TC_PCG_IDX16=0: off)
@@ -397,7 +397,7 @@ tc_status set_partition(tc_sim* s) {
   int64_t span_max = INT64_MAX;   // widest column range of a block (16-bit offsets need < 65536)
   s->win_staged = 0;
   s->win_max = 0;
-  if (s->pcg_stage && !s->slice_cmin.empty()) {
+  if (!s->slice_cmin.empty()) {
     cudaFuncAttributes fa{};
     CUDA_TRY(cudaFuncGetAttributes(&fa, pcg_kernel(s)));
     int sm_per_sm = 0, sm_optin = 0;
@@ -422,7 +422,7 @@ tc_status set_partition(tc_sim* s) {
       s->win_max = std::max<int32_t>(s->win_max, (int32_t)len);
       span_max = std::max<int64_t>(span_max, (int64_t)hi + 1 - lo);
       win[2 * b] = lo;
-      if (len <= cap) {
+      if (s->pcg_stage && len <= cap) {
         win[2 * b + 1] = (int32_t)len;
         used = std::max(used, len);
         s->win_staged += 1;
@@ -456,7 +456,7 @@ tc_status set_partition(tc_sim* s) {
   CUDA_TRY(cudaMemcpy(s->comp_block0, cb0.data(), cb0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   // 16-bit column offsets from each block's window start (the index stream of the RHS pass and
   // the A-products at half the bytes), when every block's columns span fewer than 65,536 entries
-  s->use16 = s->pcg_idx16 && s->pcg_stage && span_max <= 65536 && s->padded > 0;
+  s->use16 = s->pcg_idx16 && span_max <= 65536 && s->padded > 0;
   if (s->use16) {
     if (!s->col16) TRY(dalloc(s, &s->col16, (size_t)s->padded));
     col16_kernel<<<s->nblocks, 256, 0, s->stream>>>(s->blk_slice, s->slice_ptr, s->col, s->blk_win, s->col16);
@@ -969,7 +969,7 @@ tc_status tc_assemble(const tc_mesh* mesh, const double* sigma_l, const double* 
   }
   s->nslices = sell.nslices;
   s->padded = sell.padded;
-  s->pcg_stage = env_int("TC_PCG_STAGE", 1) != 0;
+  s->pcg_stage = env_int("TC_PCG_STAGE", 0) != 0;
   s->fuse_ms = env_int("TC_FUSE_IONIC", 1) != 0;
   s->pcg_idx16 = env_int("TC_PCG_IDX16", 1) != 0;
   try {
@@ -1598,10 +1598,12 @@ tc_status tc_autotune(tc_sim* s, int32_t trial_steps, int32_t* pcg_threads, int3
   const long long k0 = s->k;
   const int iv0 = s->iv;
   const bool thr_locked0 = s->thr_locked;
-  const int t0 = s->pcg_threads, b0 = s->blocks_per_sm;
-  const int cand[][2] = {{1024, 1}, {512, 1}, {512, 2}};
+  const int t0 = s->pcg_threads, b0 = s->blocks_per_sm, g0 = s->pcg_stage;
+  // launch shape (threads per block, blocks per SM) and whether the PCG stages its windows of z in
+  // shared memory (it pays where the windows are small next to a block's rows)
+  const int cand[][3] = {{1024, 1, 0}, {512, 1, 0}, {512, 2, 0}, {1024, 1, 1}, {512, 1, 1}, {512, 2, 1}};
   double best = 1e300;
-  int best_t = t0, best_b = b0;
+  int best_t = t0, best_b = b0, best_g = g0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == TC_OK) {
     cudaEventCreate(&e0);
@@ -1611,6 +1613,7 @@ tc_status tc_autotune(tc_sim* s, int32_t trial_steps, int32_t* pcg_threads, int3
     if (st != TC_OK) break;
     s->pcg_threads = c[0];
     s->blocks_per_sm = c[1];
+    s->pcg_stage = c[2];
     if (set_partition(s) != TC_OK) {
       clear_error();
       continue;
@@ -1625,6 +1628,7 @@ tc_status tc_autotune(tc_sim* s, int32_t trial_steps, int32_t* pcg_threads, int3
       best = ms;
       best_t = c[0];
       best_b = c[1];
+      best_g = c[2];
     }
     clear_error();
     for (auto& b : bufs) cudaMemcpy(b.dev, b.copy, b.bytes, cudaMemcpyDeviceToDevice);
@@ -1639,6 +1643,7 @@ tc_status tc_autotune(tc_sim* s, int32_t trial_steps, int32_t* pcg_threads, int3
     if (b.copy) cudaFree(b.copy);
   s->pcg_threads = best_t;
   s->blocks_per_sm = best_b;
+  s->pcg_stage = best_g;
   tc_status st2 = set_partition(s);
   if (st != TC_OK) return st;
   if (st2 != TC_OK) return st2;
