@@ -743,8 +743,11 @@ def run_ours(args):
     if prof["ionic_ms"] > prof["pcg_ms"] and w.model == "tp06" and TP06_FP64_INSTR_PER_NODE:
         ach = TP06_FP64_INSTR_PER_NODE * n / (ion_launch_ms * 1e-3)
         pk = fp64_instr_peak(clk.get("sm_mhz"))
+        rate = tc.measure_fp64_rate()
         roofline = {"kernel": "ionic_tp06_kernel<double>", "bound": "alu", "achieved": ach / 1e12,
                     "peak": pk / 1e12, "unit": "T FP64 thread-instr/s", "frac": ach / pk,
+                    "peak_measured": rate / 1e12, "frac_of_measured": ach / rate,
+                    "peak_measured_source": "tc_measure_fp64_rate: FMA chains, eight per thread, full occupancy",
                     "traffic": TP06_FP64_DRAM_BYTES_PER_LAUNCH * n / 504711,
                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                     "peak_source": "FP64 pipe: 2 instr/clk/SM x 148 SMs x median SM clock of the run",

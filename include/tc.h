@@ -311,6 +311,12 @@ tc_status tc_selftest_rcp(const double* x, double* y_fast, double* y_ref, int64_
  * 2^y) against the CUDA library exp2. */
 tc_status tc_selftest_exp2(const double* x, double* y_fast, double* y_ref, int64_t n);
 
+/* tc_measure_fp64_rate: FP64 FMA instructions per second (thread level) that the current device
+ * sustains in a probe kernel with eight independent FMA chains per thread at full occupancy; the
+ * measured ceiling of kernels bound by B300's FP64 pipe (the TP06 FP64 ionic update).  Allocates
+ * a few KB of device memory; about 40 ms. */
+tc_status tc_measure_fp64_rate(double* fma_per_s);
+
 /* ---- learned ionic surrogate --------------------------------------------------------
  * A multilayer perceptron (20 -> 4 x 256 SiLU -> 19; BF16 weights and activations, FP32
  * accumulation, FP32 master weights) that maps a TP06 cell's (18 states, V, window-mean

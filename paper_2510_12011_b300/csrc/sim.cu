@@ -1766,7 +1766,57 @@ tc_status tc_selftest_exp2(const double* x, double* y_fast, double* y_ref, int64
   return selftest_math(x, y_fast, y_ref, n, 3);
 }
 
-const char* tc_version(void) { return "tc_b300 0.4 (sm_103a)"; }
+const char* tc_version(void) { return "tc_b300 0.5 (sm_103a)"; }
+
+// FP64 arithmetic rate of the current device: every thread runs eight independent chains of
+// dependent FMAs (enough in flight to keep the FP64 pipe busy at full occupancy); the result is
+// written only under a condition the data never meet, which keeps the work alive.
+static __global__ void __launch_bounds__(256) fp64_rate_kernel(int iters, double* sink) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + 32 * k);
+  const double m = 1.0 - 1e-13, c = 1e-14;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == -1.0) sink[blockIdx.x] = s;
+}
+
+tc_status tc_measure_fp64_rate(double* fma_per_s) {
+  clear_error();
+  if (!fma_per_s) return fail(TC_ERR_ARG, "fma_per_s must not be NULL");
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256, iters = 1 << 14;
+  double* sink = nullptr;
+  CUDA_TRY(cudaMalloc(&sink, blocks * sizeof(double)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fp64_rate_kernel<<<blocks, threads>>>(iters, sink);   // warm-up (clocks up)
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    cudaEventRecord(e0);
+    fp64_rate_kernel<<<blocks, threads>>>(iters, sink);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64 rate probe");
+  *fma_per_s = (double)blocks * threads * 8.0 * iters / (best * 1e-3);
+  return TC_OK;
+}
 
 }  // extern "C"
 

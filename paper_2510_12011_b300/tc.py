@@ -95,6 +95,7 @@ _SIGS = {
     "tc_selftest_log": [_D, _D, _D, C.c_int64],
     "tc_selftest_rcp": [_D, _D, _D, C.c_int64],
     "tc_selftest_exp2": [_D, _D, _D, C.c_int64],
+    "tc_measure_fp64_rate": [_D],
     "tc_mlp_create": [C.c_uint64, C.POINTER(_P)],
     "tc_mlp_n_params": [_P, _I64],
     "tc_mlp_get_params": [_P, C.POINTER(C.c_float), C.c_int64],
@@ -552,3 +553,10 @@ def from_workload(w, stream=None, precision=TC_FP64, mesh=None):
         sim.add_stimulus(s.nodes, s.start, s.duration, s.intensity)
     sim.set_solver(w.atol, w.rtol, w.max_iter)
     return sim
+
+
+def measure_fp64_rate():
+    """tc_measure_fp64_rate: FP64 FMA instructions per second the current device sustains."""
+    v = C.c_double()
+    _check(lib().tc_measure_fp64_rate(C.byref(v)))
+    return v.value

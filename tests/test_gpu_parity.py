@@ -274,3 +274,27 @@ def test_nversion_activation_converges_with_refinement():
         act = np.asarray(r["act_ms"])
         assert np.all(np.diff(act) > 0)
     assert res[2]["diff_to_coarser_ms_max"] < res[1]["diff_to_coarser_ms_max"]
+
+
+@pytest.mark.slow
+def test_ellipsoid_full_size_parity():
+    """The precision form's and the surrogate's workload at full size (the truncated ellipsoid,
+    2,136,691 nodes, 12,075,312 tets, TP06 epicardial, five endocardial stimulus sites), solver in
+    parity mode: FP64 against the oracle after 3 steps to the FP64 bar; the FP32 form against the
+    same oracle run to FP32 resolution (a value of V near -85 mV is resolved to 8e-6 mV in FP32;
+    the CG iterations and the ionic update add rounding of that order per step)."""
+    w = I.ellipsoid_tp06(t_end=0.06)
+    w.rtol, w.atol, w.max_iter = 1e-10, 0.0, 1000
+    mesh = tc.Mesh.from_inputs(w.mesh)
+    o = Monodomain(w)
+    o.run(3)
+    g = tc.from_workload(w, mesh=mesh)
+    g.step(3)
+    assert np.abs(g.read() - o.V).max() <= V_TOL
+    for j in (0, 2, 9, 12, 17):   # Ki, Cai, m, d, r
+        assert np.allclose(g.read(tc.TC_FIELD_STATE + j), o.state[j], rtol=1e-12, atol=1e-15), j
+    g.close()
+    g32 = tc.from_workload(w, precision=tc.TC_FP32, mesh=mesh)
+    g32.step(3)
+    assert np.abs(g32.read() - o.V).max() <= 1e-3
+    assert np.allclose(g32.read(tc.TC_FIELD_STATE + 9), o.state[9], rtol=1e-4, atol=1e-8)

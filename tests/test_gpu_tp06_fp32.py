@@ -254,3 +254,14 @@ def test_device_log_accuracy():
     assert np.array_equal(np.isnan(f), np.isnan(r))
     ok = ~np.isnan(r)
     assert np.array_equal(f[ok], r[ok])
+
+
+def test_measured_fp64_rate_is_below_the_pipe_bound():
+    """The FP64 FMA-rate probe the ionic roofline is measured against: positive, and at most the
+    FP64 pipe's nominal rate of two thread instructions per clock per SM at the maximum SM clock."""
+    import torch
+    rate = tc.measure_fp64_rate()
+    props = torch.cuda.get_device_properties(0)
+    nominal = 2.0 * props.multi_processor_count * 2.1e9
+    print("fp64 rate", rate, "nominal at 2.1 GHz", nominal)
+    assert 0.2 * nominal < rate <= nominal
