@@ -121,6 +121,12 @@ def pcg_launch_bytes(n, nnz, nslices, iters, vb=8):
     return rhs + iters * (spmv + vec) + max(iters - 1.0, 0.0) * pq_in + cap
 
 
+def pcg_launch_bytes_minimum(n, nnz, iters):
+    """The minimum bytes of one FP64 PCG launch by the plan's count: the RHS pass 20 nnz + 4 (n + 1)
+    + 24 n + 16 n, and per iteration the matrix 12 nnz + 4 n plus about 72 n of node vectors."""
+    return 20 * nnz + 4 * (n + 1) + 40 * n + iters * (12 * nnz + 4 * n + 72 * n)
+
+
 def spmv_bytes(n, nnz, value_bytes=8):
     """CSR-equivalent algorithmic bytes of one y = A x: values + column indices + row pointers +
     x read once + y written once (value_bytes 8 for FP64, 4 for FP32)."""
@@ -740,6 +746,9 @@ def run_ours(args):
                                  "132.6 MB L2 across iterations (evict-last fraction), the rest and M, K stream from DRAM") if cap else None,
                 "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": bytes_launch,
                 "avg_launch_ms": pcg_launch_ms}
+    by_min = pcg_launch_bytes_minimum(n, size["nnz"], iters)
+    roof_pcg["bytes_minimum_per_launch"] = by_min
+    roof_pcg["frac_of_minimum_bytes"] = by_min / (pcg_launch_ms * 1e-3) / 1e9 / peak
     if prof["ionic_ms"] > prof["pcg_ms"] and w.model == "tp06" and TP06_FP64_INSTR_PER_NODE:
         ach = TP06_FP64_INSTR_PER_NODE * n / (ion_launch_ms * 1e-3)
         pk = fp64_instr_peak(clk.get("sm_mhz"))
