@@ -44,8 +44,9 @@ METRIC = ("node-steps/s (plain FP64 monodomain step: ionic + RHS + Jacobi-PCG + 
 TP06_FP64_INSTR_PER_NODE = 914.0
 TP06_FP64_DRAM_BYTES_PER_LAUNCH = 142.57e6   # dram read + write of the same capture
 # dram read + write of one pcg_step_kernel_1024<double> launch on the large slab (ncu capture in
-# profiles/, a launch after the 40 ms pre-roll: 11 CG iterations)
-PCG_FP64_DRAM_BYTES_PER_LAUNCH = 0.679e9
+# profiles/ of the autotuned launch - windows staged, 16-bit column offsets - near the end of the
+# 40 ms pre-roll: 11 CG iterations)
+PCG_FP64_DRAM_BYTES_PER_LAUNCH = 0.549e9
 PCG_FP64_CAPTURE_ITERATIONS = 11.0
 
 
