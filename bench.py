@@ -385,7 +385,7 @@ def mlp_roofline(prof):
     flops = MLP_FLOP_PER_ROW * rows_per_launch
     peak, kind = mlp_peak()
     ach = flops / (mlp_ms * 1e-3) / 1e12 if mlp_ms > 0 else 0.0
-    return {"kernel": "mlp_fused_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+    return {"kernel": "mlp_fused2_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
             "unit": "TFLOP/s", "frac": ach / peak, "flop_per_launch": flops,
             "rows_per_launch": rows_per_launch, "avg_launch_ms": mlp_ms,
             "peak_source": f"{kind} bf16_tflops_sustained (kernel timed inside the step loop)"}

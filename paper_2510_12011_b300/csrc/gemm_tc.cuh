@@ -369,9 +369,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fused_kernel(const MlpFused
 //     slot's "operand ready" barrier; after a tile's last layer they load the next tile's inputs.
 // Job order per CTA: tile pairs (2i, 2i + 1) for i = blockIdx.x, blockIdx.x + gridDim.x, ...;
 // per pair layers 0..4, per layer slot A then slot B (B absent when the tile count is odd).
-// Every wait is bounded; a wait that gives up sets a shared abort flag that every role polls, the
-// epilogue warps leave together (a reduction over their named barrier), and the CTA frees its
-// tensor memory after the others have left.
+// The epilogue warps do not wait for one another: each arrives on the slot's operand barrier
+// (16 arrivals per phase) when its columns of the next operand are written and its tensor-memory
+// reads are done, and goes on to the other slot's job. A warp is never more than one phase ahead
+// of the slowest, since the MMAs behind its next job need every warp's arrival.
+// Every wait is bounded; a wait that gives up sets a shared abort flag that every role polls, so
+// all roles leave their loops, and the CTA frees its tensor memory after the others have left.
 constexpr int kT2EpiThreads = 512;
 constexpr int kT2Threads = kT2EpiThreads + 64;
 constexpr uint32_t kT2Panel = 256u * 128u;                                  // one K-panel, 256 rows
@@ -392,16 +395,14 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, 
   return false;
 }
 
-// OR of `v` over the 512 epilogue threads (named barrier 1); also a barrier among them.
-__device__ __forceinline__ bool epi_sync_or(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, %2, p;\n"
-      " selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(kT2EpiThreads)
-      : "memory");
-  return r != 0;
+// One epilogue warp's arrival on a slot's operand barrier: every lane's shared-memory writes are
+// made visible to the tensor cores' (async) proxy and its tensor-memory loads are ordered before
+// the arrival.
+__device__ __forceinline__ void epi_warp_arrive(uint64_t* bar, int lane) {
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 template <bool STORE>
@@ -424,14 +425,17 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
       mbar_init(&full_b[i], 1);
       mbar_init(&empty_b[i], 1);
       mbar_init(&acc_b[i], 1);
-      mbar_init(&act_b[i], 1);
+      mbar_init(&act_b[i], kT2EpiThreads / 32);
     }
     s_abort = 0;
   }
   {
+    // hidden layers keep half their bias: h = z/2 = fma(acc, 1/2, b/2) is the rounded (acc + b)/2
+    // (halving is exact), so the SiLU's argument costs one instruction
     int off = 0;
     for (int l = 0; l < kMlpLayers; ++l) {
-      for (int c = tid; c < a.out[l]; c += kT2Threads) sBias[off + c] = a.bias[l][c];
+      const float f = l + 1 < kMlpLayers ? 0.5f : 1.0f;
+      for (int c = tid; c < a.out[l]; c += kT2Threads) sBias[off + c] = f * a.bias[l][c];
       off += a.out[l];
     }
   }
@@ -518,19 +522,20 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
     const int cg = warp >> 2;      // column quarter handled by this warp
     const int row = 32 * q + lane;
     uint32_t nacc[2] = {0, 0};
+    // this warp's eight rows of a tile's layer-0 operand (16-byte chunks, coalesced), then its arrival
     auto load_inputs = [&](int64_t tile, int x) {
       uint8_t* sAct = sAct0 + x * kTcSmemA;
       const int64_t row0 = tile * kTcRows;
-      for (int e = tid; e < kTcRows * 8; e += kT2EpiThreads) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int e = warp * 64 + j * 32 + lane;
         const int r = e >> 3, c = e & 7;
         const int64_t gr = row0 + r;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (gr < M) v = *reinterpret_cast<const uint4*>(a.a0 + gr * kMlpIn0 + c * 8);
         *reinterpret_cast<uint4*>(sAct + sw128_offset(0, kTcRows, r, c)) = v;
       }
-      fence_proxy_async_smem();
-      epi_sync_or(false);
-      if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&act_b[x])) : "memory");
+      epi_warp_arrive(&act_b[x], lane);
     };
     bool stop = false;
     if ((int64_t)blockIdx.x < npairs) {
@@ -543,9 +548,9 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
         const int N = a.out[l];
         for (int x = 0; x < 2 && !stop; ++x) {
           if (!tile_exists(pi, x)) continue;
-          const bool ok = mbar_wait_abort(&acc_b[x], nacc[x] & 1, abort);
+          const bool ok = __all_sync(0xffffffffu, mbar_wait_abort(&acc_b[x], nacc[x] & 1, abort));
           ++nacc[x];
-          if (epi_sync_or(!ok)) {
+          if (!ok) {
             *abort = 1;
             stop = true;
             break;
@@ -564,26 +569,23 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
               uint32_t raw[32];
               tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(x * 256 + c0), raw);
               tmem_wait_ld();
-              float v[32];
               const float4* b4 = reinterpret_cast<const float4*>(sBias + boff + c0);
-#pragma unroll
-              for (int j = 0; j < 32; j += 4) {
-                const float4 bb = b4[j >> 2];
-                v[j] = __uint_as_float(raw[j]) + bb.x;
-                v[j + 1] = __uint_as_float(raw[j + 1]) + bb.y;
-                v[j + 2] = __uint_as_float(raw[j + 2]) + bb.z;
-                v[j + 3] = __uint_as_float(raw[j + 3]) + bb.w;
-              }
               if (l + 1 < kMlpLayers) {
-                if (STORE && valid && a.z[l]) {
-                  float* zp = a.z[l] + grow * N + c0;
-#pragma unroll
-                  for (int j = 0; j < 32; j += 4)
-                    *reinterpret_cast<float4*>(zp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                }
                 __align__(16) __nv_bfloat162 h[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) h[j] = __floats2bfloat162_rn(silu_fast(v[2 * j]), silu_fast(v[2 * j + 1]));
+                for (int j = 0; j < 32; j += 4) {
+                  const float4 hb = b4[j >> 2];
+                  float z[4] = {__uint_as_float(raw[j]), __uint_as_float(raw[j + 1]), __uint_as_float(raw[j + 2]),
+                                __uint_as_float(raw[j + 3])};
+                  if (STORE && valid && a.z[l])
+                    *reinterpret_cast<float4*>(a.z[l] + grow * N + c0 + j) =
+                        make_float4(fmaf(hb.x, 2.0f, z[0]), fmaf(hb.y, 2.0f, z[1]), fmaf(hb.z, 2.0f, z[2]),
+                                    fmaf(hb.w, 2.0f, z[3]));
+                  const float h0 = fmaf(z[0], 0.5f, hb.x), h1 = fmaf(z[1], 0.5f, hb.y);
+                  const float h2 = fmaf(z[2], 0.5f, hb.z), h3 = fmaf(z[3], 0.5f, hb.w);
+                  h[j >> 1] = __floats2bfloat162_rn(fmaf(h0, tanh_approx(h0), h0), fmaf(h1, tanh_approx(h1), h1));
+                  h[(j >> 1) + 1] = __floats2bfloat162_rn(fmaf(h2, tanh_approx(h2), h2), fmaf(h3, tanh_approx(h3), h3));
+                }
                 const int panel = c0 >> 6, chunk0 = (c0 & 63) >> 3;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
@@ -595,6 +597,15 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
                   for (int u = 0; u < 4; ++u) reinterpret_cast<uint4*>(ap)[u] = reinterpret_cast<const uint4*>(h)[u];
                 }
               } else if (valid) {
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                  const float4 bb = b4[j >> 2];
+                  v[j] = __uint_as_float(raw[j]) + bb.x;
+                  v[j + 1] = __uint_as_float(raw[j + 1]) + bb.y;
+                  v[j + 2] = __uint_as_float(raw[j + 2]) + bb.z;
+                  v[j + 3] = __uint_as_float(raw[j + 3]) + bb.w;
+                }
                 float* yp = a.y + grow * kMlpPad + c0;
 #pragma unroll
                 for (int j = 0; j < 32; j += 4)
@@ -608,16 +619,13 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
               }
             }
           }
-          // the accumulator has been read and (below the last layer) the next operand written
-          tc_fence_before();
+          // this warp's part of the accumulator has been read and (below the last layer) its columns
+          // of the next operand written
           if (l + 1 < kMlpLayers) {
-            fence_proxy_async_smem();
-            epi_sync_or(false);
-            if (tid == 0)
-              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&act_b[x])) : "memory");
+            epi_warp_arrive(&act_b[x], lane);
           } else {
-            epi_sync_or(false);
-            // the slot's last MMA has completed: its operand may take the next pair's inputs
+            // the slot's last MMA has completed: its operand may take the next pair's inputs (the
+            // MMAs of that tile also wait for every warp's tensor-memory reads of this layer)
             const int64_t npi = pi + gridDim.x;
             if (npi < npairs && tile_exists(npi, x)) load_inputs(2 * npi + x, x);
           }
