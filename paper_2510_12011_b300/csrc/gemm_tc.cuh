@@ -145,6 +145,28 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 16 consecutive FP32 columns of this thread's tensor-memory lane (valid after tmem_wait_ld16).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// Wait for this thread's tensor-memory loads, with the 16 registers of the latest load tied to
+// the wait so that no use of them is scheduled above it.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                 "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
 // Byte offset of 16-byte chunk `chunk` (0..7 inside a 64-element K panel) of row r in a
 // swizzled operand with `rows` rows per panel.
 __host__ __device__ __forceinline__ uint32_t sw128_offset(int panel, int rows, int r, int chunk) {
@@ -537,6 +559,28 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
       }
       epi_warp_arrive(&act_b[x], lane);
     };
+    // The last layer's accumulator is 32 columns wide and read by warps 0-3; warps 8-15 fetch the
+    // slot's next tile inputs into registers before that job's wait (16 rows each, hiding the
+    // global-load latency behind the last layer's MMAs) and store them once its MMAs are done.
+    uint4 pre[4];
+    auto prefetch_inputs = [&](int64_t tile) {
+      const int64_t row0 = tile * kTcRows;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = (warp - 8) * 128 + j * 32 + lane;
+        const int64_t gr = row0 + (e >> 3);
+        pre[j] = make_uint4(0, 0, 0, 0);
+        if (gr < M) pre[j] = __ldg(reinterpret_cast<const uint4*>(a.a0 + gr * kMlpIn0 + (e & 7) * 8));
+      }
+    };
+    auto store_prefetched = [&](int x) {
+      uint8_t* sAct = sAct0 + x * kTcSmemA;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = (warp - 8) * 128 + j * 32 + lane;
+        *reinterpret_cast<uint4*>(sAct + sw128_offset(0, kTcRows, e >> 3, e & 7)) = pre[j];
+      }
+    };
     bool stop = false;
     if ((int64_t)blockIdx.x < npairs) {
       for (int x = 0; x < 2; ++x)
@@ -548,6 +592,24 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
         const int N = a.out[l];
         for (int x = 0; x < 2 && !stop; ++x) {
           if (!tile_exists(pi, x)) continue;
+          const int64_t npi = pi + gridDim.x;
+          const bool next = l + 1 == kMlpLayers && npi < npairs && tile_exists(npi, x);
+          if (l + 1 == kMlpLayers && warp >= 8) {
+            // no accumulator columns here: move the slot's next inputs
+            if (next) prefetch_inputs(2 * npi + x);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_abort(&acc_b[x], nacc[x] & 1, abort));
+            ++nacc[x];
+            if (!ok) {
+              *abort = 1;
+              stop = true;
+              break;
+            }
+            if (next) {
+              store_prefetched(x);
+              epi_warp_arrive(&act_b[x], lane);
+            }
+            continue;
+          }
           const bool ok = __all_sync(0xffffffffu, mbar_wait_abort(&acc_b[x], nacc[x] & 1, abort));
           ++nacc[x];
           if (!ok) {
@@ -562,18 +624,14 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
           const int cols = N / 4 >= 32 ? N / 4 : 32;
           const int cbeg = cg * cols;
           if (cbeg < N) {
-            // one 32-column chunk per wait (the other slot's MMAs run meanwhile; fewer live registers)
-            const int nch = cols / 32;
-            for (int ch = 0; ch < nch; ++ch) {
-              const int c0 = cbeg + 32 * ch;
-              uint32_t raw[32];
-              tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(x * 256 + c0), raw);
-              tmem_wait_ld();
+            // 16-column pieces, double-buffered: the next piece's tensor-memory load is in flight
+            // while this one is converted
+            auto piece = [&](const uint32_t* raw, int c0) {
               const float4* b4 = reinterpret_cast<const float4*>(sBias + boff + c0);
               if (l + 1 < kMlpLayers) {
-                __align__(16) __nv_bfloat162 h[16];
+                __align__(16) __nv_bfloat162 h[8];
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
+                for (int j = 0; j < 16; j += 4) {
                   const float4 hb = b4[j >> 2];
                   float z[4] = {__uint_as_float(raw[j]), __uint_as_float(raw[j + 1]), __uint_as_float(raw[j + 2]),
                                 __uint_as_float(raw[j + 3])};
@@ -588,18 +646,18 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
                 }
                 const int panel = c0 >> 6, chunk0 = (c0 & 63) >> 3;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 2; ++u)
                   *reinterpret_cast<uint4*>(sAct + sw128_offset(panel, kTcRows, row, chunk0 + u)) =
                       reinterpret_cast<const uint4*>(h)[u];
                 if (STORE && valid && a.act[l + 1]) {
                   __nv_bfloat16* ap = a.act[l + 1] + grow * N + c0;
 #pragma unroll
-                  for (int u = 0; u < 4; ++u) reinterpret_cast<uint4*>(ap)[u] = reinterpret_cast<const uint4*>(h)[u];
+                  for (int u = 0; u < 2; ++u) reinterpret_cast<uint4*>(ap)[u] = reinterpret_cast<const uint4*>(h)[u];
                 }
               } else if (valid) {
-                float v[32];
+                float v[16];
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
+                for (int j = 0; j < 16; j += 4) {
                   const float4 bb = b4[j >> 2];
                   v[j] = __uint_as_float(raw[j]) + bb.x;
                   v[j + 1] = __uint_as_float(raw[j + 1]) + bb.y;
@@ -608,26 +666,38 @@ __global__ void __launch_bounds__(kT2Threads, 1) mlp_fused2_kernel(const MlpFuse
                 }
                 float* yp = a.y + grow * kMlpPad + c0;
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)
+                for (int j = 0; j < 16; j += 4)
                   *reinterpret_cast<float4*>(yp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 if (STORE && a.z[l]) {
                   float* zp = a.z[l] + grow * N + c0;
 #pragma unroll
-                  for (int j = 0; j < 32; j += 4)
+                  for (int j = 0; j < 16; j += 4)
                     *reinterpret_cast<float4*>(zp + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
               }
+            };
+            const int npc = cols / 16;   // 4 (hidden layers) or 2 (last layer): even
+            const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(x * 256 + cbeg);
+            uint32_t r0[16], r1[16];
+            tmem_ld16_nowait(tb, r0);
+            tmem_wait_ld16(r0);
+            for (int pc = 0; pc < npc; pc += 2) {
+              tmem_ld16_nowait(tb + 16u * (pc + 1), r1);
+              piece(r0, cbeg + 16 * pc);
+              tmem_wait_ld16(r1);
+              if (pc + 2 < npc) tmem_ld16_nowait(tb + 16u * (pc + 2), r0);
+              piece(r1, cbeg + 16 * (pc + 1));
+              if (pc + 2 < npc) tmem_wait_ld16(r0);
             }
           }
           // this warp's part of the accumulator has been read and (below the last layer) its columns
           // of the next operand written
           if (l + 1 < kMlpLayers) {
             epi_warp_arrive(&act_b[x], lane);
-          } else {
-            // the slot's last MMA has completed: its operand may take the next pair's inputs (the
-            // MMAs of that tile also wait for every warp's tensor-memory reads of this layer)
-            const int64_t npi = pi + gridDim.x;
-            if (npi < npairs && tile_exists(npi, x)) load_inputs(2 * npi + x, x);
+          } else if (next) {
+            // the slot's last MMAs have completed; the next tile's MMAs also wait for this warp's
+            // tensor-memory reads of this layer
+            epi_warp_arrive(&act_b[x], lane);
           }
         }
         boff += N;
