@@ -170,6 +170,45 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, unsign
   return s_ok != 0;
 }
 
+// The same barrier in two halves, so that a block can do work nobody else waits for between its
+// arrival and its wait: grid_arrive (block barrier, then thread 0's release arrival) and
+// grid_wait (thread 0's bounded acquire poll, then a block barrier).
+__device__ __forceinline__ void grid_arrive(GridBar* bar, unsigned nblocks, unsigned& epoch) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    epoch += 1;
+    if (nblocks > 1) red_release_add_u32(&bar->count, 1u);
+  }
+}
+
+__device__ __forceinline__ bool grid_wait(GridBar* bar, unsigned nblocks, unsigned epoch, long long wait_limit,
+                                          int* err) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (nblocks > 1) {
+      const unsigned target = epoch * nblocks;
+      long long polls = 0;
+      while (ld_acquire_u32(&bar->count) < target) {
+        ++polls;
+        if (polls > wait_limit) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        if ((polls & 63) == 0 && *(volatile int*)err) {
+          ok = 0;
+          break;
+        }
+        if (polls > 2048) __nanosleep(20);
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Fixed-order sums.  warp_sum: lane 0 gets the shfl_down tree sum.
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -705,9 +744,12 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
     const T alpha = T(s_sc[0]);
     // x += alpha p, r -= alpha q, z = D^-1 r, rho' = r^T z, ||z||^2.  Each thread takes rows
     // i, i + THREADS, ... in that order (the same sums either way).  FP64 and 1,024-thread FP32:
-    // the loads of p, q, x, r for four rows are issued before their arithmetic (FP64 PCG 2.4 %,
-    // FP32 1.6 % faster on the 40x16x6 mm slab); 512-thread FP32 (the batched form's shape): two
-    // rows per round (the four-row form was 10 % slower there).
+    // the loads for four rows are issued before their arithmetic (FP64 PCG 2.4 %, FP32 1.6 %
+    // faster on the 40x16x6 mm slab); 512-thread FP32 (the batched form's shape): two rows per
+    // round (the four-row form was 10 % slower there).  FP64 updates x after this block's arrival
+    // at the barrier below, while the other blocks arrive (no other block reads x): FP64 PCG
+    // 0.485 -> 0.472 ms on the slab; FP32 was slower that way (1.9 % slab, 11 % 64-slab batch).
+    constexpr bool kLateX = sizeof(T) == 8;
     rho_t = T(0);
     zz_t = T(0);
     if constexpr (sizeof(T) == 8 || THREADS == 1024) {
@@ -717,16 +759,18 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
         for (int u = 0; u < 4; ++u) {
           const int64_t iu = i + (int64_t)u * THREADS;
           const bool ok = iu < r1;
-          pv[u] = ok ? a.p[iu] : T(0);
+          if constexpr (!kLateX) {
+            pv[u] = ok ? a.p[iu] : T(0);
+            xv[u] = ok ? a.x[iu] : T(0);
+          }
           qv[u] = ok ? a.q[iu] : T(0);
-          xv[u] = ok ? a.x[iu] : T(0);
           rv[u] = ok ? a.r[iu] : T(0);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int64_t iu = i + (int64_t)u * THREADS;
           if (iu < r1) {
-            a.x[iu] = fmaT(alpha, pv[u], xv[u]);
+            if constexpr (!kLateX) a.x[iu] = fmaT(alpha, pv[u], xv[u]);
             const T ri = fmaT(-alpha, qv[u], rv[u]);
             a.r[iu] = ri;
             const T zi = __ldg(&a.dinv[iu]) * ri;
@@ -775,7 +819,24 @@ __device__ __forceinline__ void pcg_step(const PcgArgs<T>& a) {
         a.partB[2 * b + 1] = v2[1];
       }
     }
-    if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
+    if constexpr (kLateX) {
+      grid_arrive(bar, nb, epoch);
+      // x += alpha p while the other blocks arrive
+      for (int64_t i = r0 + tid; i < r1; i += 2 * THREADS) {
+        const int64_t i2 = i + THREADS;
+        const T p0 = a.p[i], x0 = a.x[i];
+        T p1 = T(0), x1 = T(0);
+        if (i2 < r1) {
+          p1 = a.p[i2];
+          x1 = a.x[i2];
+        }
+        a.x[i] = fmaT(alpha, p0, x0);
+        if (i2 < r1) a.x[i2] = fmaT(alpha, p1, x1);
+      }
+      if (!grid_wait(bar, nb, epoch, a.wait_limit, a.err)) return;
+    } else {
+      if (!grid_sync(bar, nb, epoch, a.wait_limit, a.err)) return;
+    }
     ++it;
     if (warp == 0) {
       double rho_new, zz;
