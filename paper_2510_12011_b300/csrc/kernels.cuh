@@ -450,7 +450,10 @@ __host__ __device__ constexpr int pcg_sell_shape() {
   return sizeof(T) == 8 ? TC_PCG_SELL_SHAPE_F64 : kSellChunk8;
 }
 
-// Two value streams over the same pattern: am = sum M_ij g1_j, ak = sum K_ij g2_j.
+// Two value streams over the same pattern: am = sum M_ij g1_j, ak = sum K_ij g2_j, each in entry
+// order.  FP32: predicated chunks of eight entries (indices and values of a chunk first, then its
+// gathers, then its FMAs: a 15-entry row takes two rounds of dependent loads; the predicates are
+// uniform across the warp).  FP64: two entries per round (chunks of four spill at 64 registers).
 template <typename T, typename I>
 __device__ __forceinline__ void sell_dot2(const I* __restrict__ col, const T* __restrict__ vm,
                                           const T* __restrict__ vk, int beg, int w,
@@ -459,24 +462,58 @@ __device__ __forceinline__ void sell_dot2(const I* __restrict__ col, const T* __
   am = T(0);
   ak = T(0);
   const uint64_t pol = l2_policy_stream();   // M and K are read once per step
-  int j = 0;
-  for (; j + 2 <= w; j += 2) {
-    const int e = beg + 32 * j;
-    const int c0 = (int)__ldg(col + e), c1 = (int)__ldg(col + e + 32);
-    const T m0 = ld_hint(vm + e, pol), m1 = ld_hint(vm + e + 32, pol);
-    const T k0 = ld_hint(vk + e, pol), k1 = ld_hint(vk + e + 32, pol);
-    const T a0 = __ldg(g1 + c0), a1 = __ldg(g1 + c1);
-    const T b0 = __ldg(g2 + c0), b1 = __ldg(g2 + c1);
-    am = fmaT(m0, a0, am);
-    ak = fmaT(k0, b0, ak);
-    am = fmaT(m1, a1, am);
-    ak = fmaT(k1, b1, ak);
-  }
-  for (; j < w; ++j) {
-    const int e = beg + 32 * j;
-    const int c = (int)__ldg(col + e);
-    am = fmaT(ld_hint(vm + e, pol), __ldg(g1 + c), am);
-    ak = fmaT(ld_hint(vk + e, pol), __ldg(g2 + c), ak);
+  if constexpr (sizeof(T) == 4) {
+    constexpr int CH = 8;
+    for (int j = 0; j < w; j += CH) {
+      const int e = beg + 32 * j;
+      int c[CH];
+      T m[CH], k[CH], ga[CH], gb[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        c[u] = 0;
+        m[u] = k[u] = T(0);
+        if (j + u < w) {
+          c[u] = (int)__ldg(col + e + 32 * u);
+          m[u] = ld_hint(vm + e + 32 * u, pol);
+          k[u] = ld_hint(vk + e + 32 * u, pol);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        ga[u] = gb[u] = T(0);
+        if (j + u < w) {
+          ga[u] = __ldg(g1 + c[u]);
+          gb[u] = __ldg(g2 + c[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (j + u < w) {
+          am = fmaT(m[u], ga[u], am);
+          ak = fmaT(k[u], gb[u], ak);
+        }
+      }
+    }
+  } else {
+    int j = 0;
+    for (; j + 2 <= w; j += 2) {
+      const int e = beg + 32 * j;
+      const int c0 = (int)__ldg(col + e), c1 = (int)__ldg(col + e + 32);
+      const T m0 = ld_hint(vm + e, pol), m1 = ld_hint(vm + e + 32, pol);
+      const T k0 = ld_hint(vk + e, pol), k1 = ld_hint(vk + e + 32, pol);
+      const T a0 = __ldg(g1 + c0), a1 = __ldg(g1 + c1);
+      const T b0 = __ldg(g2 + c0), b1 = __ldg(g2 + c1);
+      am = fmaT(m0, a0, am);
+      ak = fmaT(k0, b0, ak);
+      am = fmaT(m1, a1, am);
+      ak = fmaT(k1, b1, ak);
+    }
+    for (; j < w; ++j) {
+      const int e = beg + 32 * j;
+      const int c = (int)__ldg(col + e);
+      am = fmaT(ld_hint(vm + e, pol), __ldg(g1 + c), am);
+      ak = fmaT(ld_hint(vk + e, pol), __ldg(g2 + c), ak);
+    }
   }
 }
 
