@@ -789,7 +789,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = n
 // (10 % slower at 128 x 5).
 template <typename T>
 struct Tp06Launch {
-  static constexpr int threads = 256, min_blocks = 3;
+  static constexpr int threads = 256, min_blocks = 4;
 };
 template <>
 struct Tp06Launch<double> {
@@ -799,7 +799,9 @@ struct Tp06Launch<double> {
 template <typename T>
 __global__ void __launch_bounds__(Tp06Launch<T>::threads, Tp06Launch<T>::min_blocks)
     ionic_tp06_kernel(const IonicArgs<T> a) {
-  exp2_table_init();
+  // the FP64 exp and log tables; the FP32 kernel uses the hardware exp2f and logf and stages
+  // nothing (35 KB of copies per block, and the shared memory they held, saved)
+  if constexpr (sizeof(T) == 8) exp2_table_init();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n_bar) a.bar[i].count = 0u;
   if (i >= a.n) return;
