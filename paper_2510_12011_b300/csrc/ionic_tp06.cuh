@@ -789,7 +789,7 @@ __device__ __forceinline__ T tp06_cell_step(T V, T* u, int cell, T dt, T* lg = n
 // (10 % slower at 128 x 5).
 template <typename T>
 struct Tp06Launch {
-  static constexpr int threads = 256, min_blocks = 4;
+  static constexpr int threads = 128, min_blocks = 8;
 };
 template <>
 struct Tp06Launch<double> {
