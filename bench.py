@@ -9,7 +9,9 @@ workload (one time step k -> k+1 of the operator-split scheme).  The default wor
 2006 epicardial model, dt = 0.02 ms.  Every form steps 40 ms from rest (the corner stimulus's wave
 is then crossing the slab), W warm-up steps, then K timed steps.  A second leg runs the
 2,136,691-node truncated ellipsoid for 300 ms in all three forms (FP64, FP32, FP32 + surrogate)
-with activation-time and APD90 errors against the FP64 run.  Inputs are synthetic and seeded.
+with activation-time and APD90 errors against the FP64 run.  The network also runs in FP64
+tissue, on the same timed steps and from rest over the first 120 ms (what it gains at the same
+precision).  Inputs are synthetic and seeded.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -65,6 +67,9 @@ def parse():
                     help="skip the PyTorch version of the paper's own design (context line)")
     ap.add_argument("--no-surrogate-apd", action="store_true",
                     help="skip the surrogate's 400 ms APD90 check on the unseen slab")
+    ap.add_argument("--fp64-beat-ms", type=float, default=120.0,
+                    help="simulated ms of the FP64-tissue network run from rest against FP64 exact "
+                         "(0 skips it)")
     ap.add_argument("--batched-steps", type=int, default=600)
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -402,7 +407,40 @@ def mlp_roofline(prof):
 SURROGATE_CHECK = (10, 2.0, 1.0, 0.3, 0.5)   # window, dv_max, dvdt_max, dv_neighbour, rest_band
 
 
-def surrogate_form(w, K, W, preroll, ms64, ms32, act64, stream, torch, apd=True, apd64=None):
+def fp64_tissue_run(w, m, t_ms, W, stream, torch):
+    """FP64 exact against FP64 tissue with the network, both from rest over t_ms of the slab
+    (stimulus, upstroke and the plateau the network takes), graphs on, W untimed steps first:
+    ms per step of each, their ratio, the network's share of the node-windows and the activation
+    times' largest difference."""
+    from paper_2510_12011_b300 import tc
+    steps = int(round(t_ms / w.dt))
+    res = {}
+    for name, net in (("exact", False), ("network", True)):
+        sim = tc.from_workload(w, stream=stream.cuda_stream, precision=tc.TC_FP64)
+        if net:
+            sim.set_surrogate(m, *SURROGATE_CHECK)
+        sim.step(W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = sim.step(steps - W)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        u = sim.surrogate_usage() if net else None
+        res[name] = (e0.elapsed_time(e1) / (steps - W), sim.activation_times(), u, st["not_converged"])
+        sim.close()
+    (ms_e, act_e, _, nc_e), (ms_n, act_n, u, nc_n) = res["exact"], res["network"]
+    both = (act_e >= 0) & (act_n >= 0)
+    return {"simulated_ms": [0.0, t_ms], "timed_steps": steps - W, "ms_per_step_exact": ms_e,
+            "ms_per_step_network": ms_n, "speedup": ms_e / ms_n,
+            "network_share": u["surrogate"] / max(1, u["surrogate"] + u["exact"]),
+            "activated_both": int(both.sum()),
+            "act_err_ms_max": float(np.abs(act_n[both] - act_e[both]).max()) if both.any() else None,
+            "not_converged": nc_e + nc_n}
+
+
+def surrogate_form(w, K, W, preroll, ms64, ms32, act64, stream, torch, apd=True, apd64=None, beat_ms=0.0):
     """FP32 + the learned TP06 surrogate (the network stored with the package) on the same
     workload and the same timed window as the FP64 and FP32 runs (after the pre-roll, so that the
     wave is propagating and the network takes the plateau and recovery windows): node-steps/s,
@@ -448,6 +486,8 @@ def surrogate_form(w, K, W, preroll, ms64, ms32, act64, stream, torch, apd=True,
                    "act_err_ms_max": float(np.abs(act_d[both_d] - act64[both_d]).max()) if both_d.any() else None,
                    "kernels": {"ionic_ms": prof_d["ionic_ms"], "pcg_ms": prof_d["pcg_ms"],
                                "surrogate_ms": prof_d["surrogate_ms"], "mlp_ms": prof_d["mlp_ms"]}}
+    if beat_ms > 0:
+        fp64_tissue["from_rest"] = fp64_tissue_run(w, m, beat_ms, W, stream, torch)
     return {"value": n * K / (ms * 1e-3), "unit": "node-steps/s", "ms_per_step": ms / K,
             "speedup_vs_fp64": ms64 / ms, "speedup_vs_fp32": ms32 / ms if ms32 else None,
             "fp64_tissue": fp64_tissue,
@@ -868,7 +908,7 @@ def run_ours(args):
     sur = None
     if not args.no_surrogate and w.model == "tp06":
         sur = surrogate_form(w, K, W, P, ms, ms32 if fp32 else None, act64, stream, torch,
-                             apd=not args.no_surrogate_apd, apd64=apd64)
+                             apd=not args.no_surrogate_apd, apd64=apd64, beat_ms=args.fp64_beat_ms)
 
     prior = None
     if not args.no_prior_art and world == 1:
