@@ -1049,20 +1049,44 @@ __global__ void sur_features_kernel(int64_t n, const T* state, const T* V, const
     const int64_t s = i >> 5;
     const int beg = slice_ptr[s] + (int)(i & 31);
     const int w = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
+    // chunks of eight entries: the column indices first, then the gathers (two rounds of
+    // dependent loads for a 15-entry row instead of fifteen); the maximum is order-free
     float d = 0.f;
-    for (int j = 0; j < w; ++j) d = fmaxf(d, fabsf((float)V[col[beg + 32 * j]] - vi));
+    for (int j = 0; j < w; j += 8) {
+      int c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) c[u] = j + u < w ? __ldg(col + beg + 32 * (j + u)) : -1;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c[u] >= 0) d = fmaxf(d, fabsf((float)V[c[u]] - vi));
+    }
     cand = d <= dv_nbr;
   }
   if (i < n) flag[i] = 0;
+  // one atomic per block (256 threads): the warps' candidate counts are laid out in warp order
+  // behind the block's base
   const unsigned cm_ = __ballot_sync(0xffffffffu, cand);
   const unsigned rm = __ballot_sync(0xffffffffu, real && !cand);
-  const int lane = threadIdx.x & 31;
-  int base = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ int s_wc[8], s_rc[8], s_base;
   if (lane == 0) {
-    if (cm_) base = atomicAdd(count, __popc(cm_));
-    if (rm) atomicAdd(&counts[1], (unsigned long long)__popc(rm));
+    s_wc[warp] = __popc(cm_);
+    s_rc[warp] = __popc(rm);
   }
-  base = __shfl_sync(0xffffffffu, base, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0, rtot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const int c = s_wc[w];
+      s_wc[w] = tot;
+      tot += c;
+      rtot += s_rc[w];
+    }
+    s_base = tot ? atomicAdd(count, tot) : 0;
+    if (rtot) atomicAdd(&counts[1], (unsigned long long)rtot);
+  }
+  __syncthreads();
+  const int base = s_base + s_wc[warp];
   if (!cand) return;
   const int pos = base + __popc(cm_ & ((1u << lane) - 1u));
   idx[pos] = (int32_t)i;
@@ -1122,11 +1146,26 @@ __global__ void sur_commit_kernel(const int* count, int64_t n, const int32_t* id
       iion[i] = raw[19 * n + i] - dv / (float)(win * dt);
     }
   }
+  // one pair of atomics per block (256 threads)
   const unsigned okm = __ballot_sync(0xffffffffu, ok);
   const unsigned hm = __ballot_sync(0xffffffffu, have);
-  if ((threadIdx.x & 31) == 0 && hm) {
-    atomicAdd(&counts[0], (unsigned long long)__popc(okm));
-    atomicAdd(&counts[1], (unsigned long long)(__popc(hm) - __popc(okm)));
+  __shared__ int s_ok[8], s_have[8];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_ok[warp] = __popc(okm);
+    s_have[warp] = __popc(hm);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int o = 0, h = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      o += s_ok[w];
+      h += s_have[w];
+    }
+    if (h) {
+      atomicAdd(&counts[0], (unsigned long long)o);
+      atomicAdd(&counts[1], (unsigned long long)(h - o));
+    }
   }
 }
 
